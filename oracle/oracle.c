@@ -1,0 +1,794 @@
+/*
+ * CPU FP64 oracle for the reservoir linear-solve path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, sequential
+ * definition of what the CUDA library computes.  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark load it; the product
+ * path never links, calls or falls back to it.  It shares no code, header or
+ * constant with the CUDA sources.
+ *
+ * Every routine follows the paper's definitions (sections cited per routine):
+ *   - matrix/vector algebra, Section "Algebraic Operations" (y = aAx + by, <x,y>, ||x||);
+ *   - ILU, Section "Restricted Additive Schwarz Method" (LUx = b <=> Ly = b, Ux = y;
+ *     ILU(0) is the default local solver in the RAS parameter defaults);
+ *   - multigrid, Section "Algebraic Multigrid Methods" (R = P^T, A_{l+1} = R A P,
+ *     V-cycle algorithm with pre-smoother, restriction, recursion, prolongation,
+ *     post-smoother and exact coarsest solve; defaults 1 cycle, 6 levels, 2 sweeps);
+ *   - CPR, Section "CPR-like Preconditioners" (restriction Pi_r, prolongation Pi_p,
+ *     CPR-PF algorithm, quasi-IMPES decoupling named in the numerical experiments);
+ *   - Krylov solvers, Section "Solvers" (restarted GMRES(m), BiCGSTAB; SOLVER fields
+ *     rtol/atol/btol/maxit/restart).
+ * Where the paper is silent the readings used are stated beside the code.
+ * Parity of every routine is pinned by tests against closed forms, dense
+ * linear algebra and invariants.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_ENOMEM 2
+#define OR_ESINGULAR 5
+#define OR_EBREAKDOWN 6
+#define OR_ENOCONV 7
+#define OR_ENAN 9
+
+/* ------------------------------------------------------------------ BLAS-1 */
+
+/* alpha = <x, y>  (Algebraic Operations) */
+double or_dot(int64_t n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+}
+
+/* alpha = <x, x>^(1/2) */
+double or_norm2(int64_t n, const double *x) { return sqrt(or_dot(n, x, x)); }
+
+/* y = alpha x + beta y */
+static void axpby(int64_t n, double a, const double *x, double b, double *y) {
+    for (int64_t i = 0; i < n; ++i) y[i] = a * x[i] + b * y[i];
+}
+
+/* ------------------------------------------------------------- BSR SpMV */
+
+/* y = alpha A x + beta y for a 3x3-block BSR matrix (Algebraic Operations).
+ * Blocks are row-major; a row's blocks are summed in ascending column order. */
+int or_spmv(int nb, const int32_t *rp, const int32_t *ci, const double *v,
+            double alpha, const double *x, double beta, double *y) {
+    for (int r = 0; r < nb; ++r) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
+            const double *a = v + 9 * (int64_t)p;
+            const double *xc = x + 3 * (int64_t)ci[p];
+            for (int e = 0; e < 3; ++e)
+                for (int f = 0; f < 3; ++f) acc[e] += a[3 * e + f] * xc[f];
+        }
+        for (int e = 0; e < 3; ++e) {
+            double old = (beta == 0.0) ? 0.0 : beta * y[3 * (int64_t)r + e];
+            y[3 * (int64_t)r + e] = alpha * acc[e] + old;
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------ dense elimination */
+
+/* Solve A X = B (A n x n row-major, B n x nrhs row-major) by Gaussian
+ * elimination with partial pivoting.  A and B are overwritten; X lands in B.
+ * A pivot with |p| <= 1e-300 reports singularity. */
+static int gauss_solve(int n, double *A, double *B, int nrhs) {
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(A[(int64_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i) {
+            double t = fabs(A[(int64_t)i * n + k]);
+            if (t > best) { best = t; piv = i; }
+        }
+        if (!(best > 1e-300)) return OR_ESINGULAR;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(int64_t)k * n + j];
+                A[(int64_t)k * n + j] = A[(int64_t)piv * n + j];
+                A[(int64_t)piv * n + j] = t;
+            }
+            for (int j = 0; j < nrhs; ++j) {
+                double t = B[(int64_t)k * nrhs + j];
+                B[(int64_t)k * nrhs + j] = B[(int64_t)piv * nrhs + j];
+                B[(int64_t)piv * nrhs + j] = t;
+            }
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double l = A[(int64_t)i * n + k] / A[(int64_t)k * n + k];
+            if (l == 0.0) continue;
+            for (int j = k; j < n; ++j) A[(int64_t)i * n + j] -= l * A[(int64_t)k * n + j];
+            for (int j = 0; j < nrhs; ++j) B[(int64_t)i * nrhs + j] -= l * B[(int64_t)k * nrhs + j];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        for (int j = 0; j < nrhs; ++j) {
+            double s = B[(int64_t)k * nrhs + j];
+            for (int i = k + 1; i < n; ++i) s -= A[(int64_t)k * n + i] * B[(int64_t)i * nrhs + j];
+            B[(int64_t)k * nrhs + j] = s / A[(int64_t)k * n + k];
+        }
+    }
+    return OR_OK;
+}
+
+/* Dense solve A x = b (A row-major n x n, left untouched). */
+int or_dense_solve(int n, const double *A, const double *b, double *x) {
+    double *a = (double *)malloc(sizeof(double) * (size_t)n * n);
+    if (!a) return OR_ENOMEM;
+    memcpy(a, A, sizeof(double) * (size_t)n * n);
+    memcpy(x, b, sizeof(double) * (size_t)n);
+    int st = gauss_solve(n, a, x, 1);
+    free(a);
+    return st;
+}
+
+/* Inverse of one 3x3 block by elimination against the identity. */
+int or_inv3(const double *a, double *ainv) {
+    double m[9];
+    memcpy(m, a, sizeof m);
+    for (int i = 0; i < 9; ++i) ainv[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    return gauss_solve(3, m, ainv, 3);
+}
+
+static void mat3_vec(const double *a, const double *x, double *y) {
+    for (int e = 0; e < 3; ++e) y[e] = a[3 * e] * x[0] + a[3 * e + 1] * x[1] + a[3 * e + 2] * x[2];
+}
+
+static void mat3_mul(const double *a, const double *b, double *c) {
+    for (int e = 0; e < 3; ++e)
+        for (int f = 0; f < 3; ++f)
+            c[3 * e + f] = a[3 * e] * b[f] + a[3 * e + 1] * b[3 + f] + a[3 * e + 2] * b[6 + f];
+}
+
+static int32_t find_block(const int32_t *rp, const int32_t *ci, int r, int c) {
+    for (int32_t p = rp[r]; p < rp[r + 1]; ++p)
+        if (ci[p] == c) return p;
+    return -1;
+}
+
+/* ----------------------------------------------------------- block Jacobi */
+
+/* Setup: dinv_i = (A_ii)^{-1} for every block row. */
+int or_bj_setup(int nb, const int32_t *rp, const int32_t *ci, const double *v, double *dinv) {
+    for (int r = 0; r < nb; ++r) {
+        int32_t p = find_block(rp, ci, r, r);
+        if (p < 0) return OR_EINVAL;
+        if (or_inv3(v + 9 * (int64_t)p, dinv + 9 * (int64_t)r)) return OR_ESINGULAR;
+    }
+    return OR_OK;
+}
+
+/* Apply: z_i = dinv_i r_i. */
+void or_bj_apply(int nb, const double *dinv, const double *r, double *z) {
+    for (int i = 0; i < nb; ++i) mat3_vec(dinv + 9 * (int64_t)i, r + 3 * (int64_t)i, z + 3 * (int64_t)i);
+}
+
+/* ------------------------------------------------------- block ILU(0) */
+
+/* Block ILU(0) in natural row order, general form over the pattern of A:
+ *   for each row i, for each k < i in row i (ascending):
+ *       L_ik = A_ik U_kk^{-1};
+ *       for each j > k in row k: if (i,j) in pattern(A): A_ij -= L_ik A_kj.
+ * The factor overwrites a copy of the values: strict-lower blocks hold L
+ * (unit diagonal implied), the rest holds U.  udinv_i = U_ii^{-1}.
+ * *offdiag_updates counts updates that hit a block other than the diagonal
+ * (zero for the seven-point pattern, whose graph has no triangles). */
+int or_bilu0_setup(int nb, const int32_t *rp, const int32_t *ci, const double *v,
+                   double *lu, double *udinv, int64_t *offdiag_updates) {
+    memcpy(lu, v, sizeof(double) * 9 * (size_t)rp[nb]);
+    int64_t off = 0;
+    for (int i = 0; i < nb; ++i) {
+        for (int32_t pk = rp[i]; pk < rp[i + 1] && ci[pk] < i; ++pk) {
+            int k = ci[pk];
+            double lik[9];
+            mat3_mul(lu + 9 * (int64_t)pk, udinv + 9 * (int64_t)k, lik);
+            memcpy(lu + 9 * (int64_t)pk, lik, sizeof lik);
+            for (int32_t pj = rp[k]; pj < rp[k + 1]; ++pj) {
+                int j = ci[pj];
+                if (j <= k) continue;
+                int32_t pij = find_block(rp, ci, i, j);
+                if (pij < 0) continue;  /* no fill outside the pattern */
+                double t[9];
+                mat3_mul(lik, lu + 9 * (int64_t)pj, t);
+                for (int q = 0; q < 9; ++q) lu[9 * (int64_t)pij + q] -= t[q];
+                if (j != i) ++off;
+            }
+        }
+        int32_t pd = find_block(rp, ci, i, i);
+        if (pd < 0) return OR_EINVAL;
+        if (or_inv3(lu + 9 * (int64_t)pd, udinv + 9 * (int64_t)i)) return OR_ESINGULAR;
+    }
+    if (offdiag_updates) *offdiag_updates = off;
+    return OR_OK;
+}
+
+/* Apply z = (LU)^{-1} r: L y = r forward, then U z = y backward. */
+void or_bilu0_apply(int nb, const int32_t *rp, const int32_t *ci, const double *lu,
+                    const double *udinv, const double *r, double *z) {
+    double *y = z; /* y then z in place: row i of the backward sweep only reads rows > i */
+    for (int i = 0; i < nb; ++i) {
+        double s[3] = {r[3 * (int64_t)i], r[3 * (int64_t)i + 1], r[3 * (int64_t)i + 2]};
+        for (int32_t p = rp[i]; p < rp[i + 1] && ci[p] < i; ++p) {
+            double t[3];
+            mat3_vec(lu + 9 * (int64_t)p, y + 3 * (int64_t)ci[p], t);
+            for (int e = 0; e < 3; ++e) s[e] -= t[e];
+        }
+        for (int e = 0; e < 3; ++e) y[3 * (int64_t)i + e] = s[e];
+    }
+    for (int i = nb - 1; i >= 0; --i) {
+        double s[3] = {y[3 * (int64_t)i], y[3 * (int64_t)i + 1], y[3 * (int64_t)i + 2]};
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+            if (ci[p] <= i) continue;
+            double t[3];
+            mat3_vec(lu + 9 * (int64_t)p, z + 3 * (int64_t)ci[p], t);
+            for (int e = 0; e < 3; ++e) s[e] -= t[e];
+        }
+        mat3_vec(udinv + 9 * (int64_t)i, s, z + 3 * (int64_t)i);
+    }
+}
+
+/* ----------------------------------------------- quasi-IMPES and Pi_r / Pi_p */
+
+/* Seven-point scalar stencil storage used for the pressure system:
+ * a7[c*7 + s], s = 0:-z 1:-y 2:-x 3:centre 4:+x 5:+y 6:+z (0 where no face). */
+static const int SX[7] = {0, 0, -1, 0, 1, 0, 0};
+static const int SY[7] = {0, -1, 0, 0, 0, 1, 0};
+static const int SZ[7] = {-1, 0, 0, 0, 0, 0, 1};
+
+static int stencil_slot(int di, int dj, int dk) {
+    for (int s = 0; s < 7; ++s)
+        if (SX[s] == di && SY[s] == dj && SZ[s] == dk) return s;
+    return -1;
+}
+
+/* Quasi-IMPES weights (diagonal reading of the decoupling named in the
+ * experiments): with D = A_ii, w_i = (1, -D01/D11, -D02/D22).  The pressure
+ * matrix is the pressure column of the weighted block rows,
+ * (A_pp)_ij = sum_r w_i[r] A_ij[r][0], stored as a seven-point stencil. */
+int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v,
+                double *w, double *a7) {
+    int nb = nx * ny * nz;
+    memset(a7, 0, sizeof(double) * 7 * (size_t)nb);
+    for (int c = 0; c < nb; ++c) {
+        int32_t pd = find_block(rp, ci, c, c);
+        if (pd < 0) return OR_EINVAL;
+        const double *d = v + 9 * (int64_t)pd;
+        if (!(fabs(d[4]) > 1e-300) || !(fabs(d[8]) > 1e-300)) return OR_ESINGULAR;
+        double *wc = w + 3 * (int64_t)c;
+        wc[0] = 1.0;
+        wc[1] = -d[1] / d[4];
+        wc[2] = -d[2] / d[8];
+        int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        for (int32_t p = rp[c]; p < rp[c + 1]; ++p) {
+            int o = ci[p];
+            int oi = o % nx, oj = (o / nx) % ny, ok = o / (nx * ny);
+            int s = stencil_slot(oi - i, oj - j, ok - k);
+            if (s < 0) return OR_EINVAL;
+            const double *a = v + 9 * (int64_t)p;
+            a7[7 * (int64_t)c + s] = wc[0] * a[0] + wc[1] * a[3] + wc[2] * a[6];
+        }
+    }
+    return OR_OK;
+}
+
+/* Pi_r with the decoupling folded in: p_i = w_i . r_i. */
+void or_restrict_pressure(int nb, const double *w, const double *r, double *p) {
+    for (int i = 0; i < nb; ++i)
+        p[i] = w[3 * (int64_t)i] * r[3 * (int64_t)i] + w[3 * (int64_t)i + 1] * r[3 * (int64_t)i + 1] +
+               w[3 * (int64_t)i + 2] * r[3 * (int64_t)i + 2];
+}
+
+/* Pi_p: x_i = (p_i, 0, 0). */
+void or_prolong_pressure(int nb, const double *p, double *x) {
+    for (int i = 0; i < nb; ++i) {
+        x[3 * (int64_t)i] = p[i];
+        x[3 * (int64_t)i + 1] = 0.0;
+        x[3 * (int64_t)i + 2] = 0.0;
+    }
+}
+
+/* y = a7 x  for a seven-point stencil on an nx*ny*nz grid. */
+void or_stencil_apply(int nx, int ny, int nz, const double *a7, const double *x, double *y) {
+    int nb = nx * ny * nz;
+    for (int c = 0; c < nb; ++c) {
+        int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        double s = 0.0;
+        for (int q = 0; q < 7; ++q) {
+            int ii = i + SX[q], jj = j + SY[q], kk = k + SZ[q];
+            if (ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz) continue;
+            s += a7[7 * (int64_t)c + q] * x[(int64_t)nx * ny * kk + (int64_t)nx * jj + ii];
+        }
+        y[c] = s;
+    }
+}
+
+/* ------------------------------------------------------ geometric multigrid */
+
+/* Galerkin coarse operator A_c = P^T A P for piecewise-constant P on 2x2x2
+ * boxes (coarse cell (i/2, j/2, k/2); dims ceil(d/2)).  Entry (I,J) of the
+ * product is the sum of fine couplings A_ij with i in box I and j in box J;
+ * couplings inside one box add to the coarse centre. */
+void or_gmg_coarsen(int nx, int ny, int nz, const double *a7, double *ac7) {
+    int cx = (nx + 1) / 2, cy = (ny + 1) / 2, cz = (nz + 1) / 2;
+    memset(ac7, 0, sizeof(double) * 7 * (size_t)cx * cy * cz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t c = (int64_t)nx * ny * k + (int64_t)nx * j + i;
+                int64_t C = (int64_t)cx * cy * (k / 2) + (int64_t)cx * (j / 2) + i / 2;
+                for (int q = 0; q < 7; ++q) {
+                    int ii = i + SX[q], jj = j + SY[q], kk = k + SZ[q];
+                    if (ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz) continue;
+                    int s = stencil_slot(ii / 2 - i / 2, jj / 2 - j / 2, kk / 2 - k / 2);
+                    ac7[7 * C + s] += a7[7 * c + q];
+                }
+            }
+}
+
+/* One Gauss-Seidel sweep over the cells of one colour ((i+j+k) mod 2),
+ * visiting them in natural order. */
+void or_gs_colour(int nx, int ny, int nz, const double *a7, const double *b, double *x, int colour) {
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (((i + j + k) & 1) != colour) continue;
+                int64_t c = (int64_t)nx * ny * k + (int64_t)nx * j + i;
+                double s = b[c];
+                for (int q = 0; q < 7; ++q) {
+                    if (q == 3) continue;
+                    int ii = i + SX[q], jj = j + SY[q], kk = k + SZ[q];
+                    if (ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz) continue;
+                    s -= a7[7 * c + q] * x[(int64_t)nx * ny * kk + (int64_t)nx * jj + ii];
+                }
+                x[c] = s / a7[7 * c + 3];
+            }
+}
+
+#define OR_MAX_LEVELS 8
+typedef struct {
+    int nlev;
+    int nx[OR_MAX_LEVELS], ny[OR_MAX_LEVELS], nz[OR_MAX_LEVELS];
+    double *a7[OR_MAX_LEVELS];
+    double *x[OR_MAX_LEVELS], *b[OR_MAX_LEVELS], *r[OR_MAX_LEVELS];
+    double *coarse_dense; /* coarsest operator, dense row-major */
+    int sweeps;
+} or_gmg;
+
+/* Level count rule: halve (ceil) every dimension while the level has more than
+ * `max_coarse` cells, up to `max_levels` levels (paper default 6). */
+static int gmg_build(or_gmg *g, int nx, int ny, int nz, const double *a7, int max_levels,
+                     int max_coarse, int sweeps) {
+    memset(g, 0, sizeof *g);
+    if (max_levels > OR_MAX_LEVELS) max_levels = OR_MAX_LEVELS;
+    g->sweeps = sweeps;
+    g->nx[0] = nx; g->ny[0] = ny; g->nz[0] = nz;
+    int64_t n0 = (int64_t)nx * ny * nz;
+    g->a7[0] = (double *)malloc(sizeof(double) * 7 * n0);
+    memcpy(g->a7[0], a7, sizeof(double) * 7 * n0);
+    int l = 0;
+    while (l + 1 < max_levels && (int64_t)g->nx[l] * g->ny[l] * g->nz[l] > max_coarse) {
+        int cx = (g->nx[l] + 1) / 2, cy = (g->ny[l] + 1) / 2, cz = (g->nz[l] + 1) / 2;
+        g->nx[l + 1] = cx; g->ny[l + 1] = cy; g->nz[l + 1] = cz;
+        g->a7[l + 1] = (double *)malloc(sizeof(double) * 7 * (size_t)cx * cy * cz);
+        or_gmg_coarsen(g->nx[l], g->ny[l], g->nz[l], g->a7[l], g->a7[l + 1]);
+        ++l;
+    }
+    g->nlev = l + 1;
+    for (int q = 0; q < g->nlev; ++q) {
+        size_t n = (size_t)g->nx[q] * g->ny[q] * g->nz[q];
+        g->x[q] = (double *)calloc(n, sizeof(double));
+        g->b[q] = (double *)calloc(n, sizeof(double));
+        g->r[q] = (double *)calloc(n, sizeof(double));
+    }
+    int L = g->nlev - 1;
+    int nc = g->nx[L] * g->ny[L] * g->nz[L];
+    g->coarse_dense = (double *)calloc((size_t)nc * nc, sizeof(double));
+    for (int c = 0; c < nc; ++c) {
+        int i = c % g->nx[L], j = (c / g->nx[L]) % g->ny[L], k = c / (g->nx[L] * g->ny[L]);
+        for (int q = 0; q < 7; ++q) {
+            int ii = i + SX[q], jj = j + SY[q], kk = k + SZ[q];
+            if (ii < 0 || jj < 0 || kk < 0 || ii >= g->nx[L] || jj >= g->ny[L] || kk >= g->nz[L]) continue;
+            int o = g->nx[L] * g->ny[L] * kk + g->nx[L] * jj + ii;
+            g->coarse_dense[(size_t)c * nc + o] += g->a7[L][7 * (size_t)c + q];
+        }
+    }
+    return OR_OK;
+}
+
+static void gmg_free(or_gmg *g) {
+    for (int q = 0; q < g->nlev; ++q) { free(g->a7[q]); free(g->x[q]); free(g->b[q]); free(g->r[q]); }
+    free(g->coarse_dense);
+    memset(g, 0, sizeof *g);
+}
+
+/* V-cycle from a zero initial guess on level l (multigrid V-cycle algorithm):
+ * pre-smooth (red then black, `sweeps` times), residual, restrict with
+ * R = P^T (sum over each 2x2x2 box), recurse, prolong (inject) and add,
+ * post-smooth (black then red), exact dense solve on the coarsest level. */
+static int gmg_vcycle(or_gmg *g, int l) {
+    int nx = g->nx[l], ny = g->ny[l], nz = g->nz[l];
+    int64_t n = (int64_t)nx * ny * nz;
+    if (l == g->nlev - 1) {
+        return or_dense_solve((int)n, g->coarse_dense, g->b[l], g->x[l]);
+    }
+    memset(g->x[l], 0, sizeof(double) * n);
+    for (int s = 0; s < g->sweeps; ++s) {
+        or_gs_colour(nx, ny, nz, g->a7[l], g->b[l], g->x[l], 0);
+        or_gs_colour(nx, ny, nz, g->a7[l], g->b[l], g->x[l], 1);
+    }
+    or_stencil_apply(nx, ny, nz, g->a7[l], g->x[l], g->r[l]);
+    for (int64_t c = 0; c < n; ++c) g->r[l][c] = g->b[l][c] - g->r[l][c];
+    int cx = g->nx[l + 1], cy = g->ny[l + 1];
+    memset(g->b[l + 1], 0, sizeof(double) * (size_t)cx * cy * g->nz[l + 1]);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                g->b[l + 1][(int64_t)cx * cy * (k / 2) + (int64_t)cx * (j / 2) + i / 2] +=
+                    g->r[l][(int64_t)nx * ny * k + (int64_t)nx * j + i];
+    int st = gmg_vcycle(g, l + 1);
+    if (st) return st;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                g->x[l][(int64_t)nx * ny * k + (int64_t)nx * j + i] +=
+                    g->x[l + 1][(int64_t)cx * cy * (k / 2) + (int64_t)cx * (j / 2) + i / 2];
+    for (int s = 0; s < g->sweeps; ++s) {
+        or_gs_colour(nx, ny, nz, g->a7[l], g->b[l], g->x[l], 1);
+        or_gs_colour(nx, ny, nz, g->a7[l], g->b[l], g->x[l], 0);
+    }
+    return OR_OK;
+}
+
+/* Stand-alone V-cycle for tests: e = V(rhs) on the stencil hierarchy. */
+int or_gmg_vcycle(int nx, int ny, int nz, const double *a7, int max_levels, int max_coarse,
+                  int sweeps, const double *rhs, double *e, int *nlev_out) {
+    or_gmg g;
+    gmg_build(&g, nx, ny, nz, a7, max_levels, max_coarse, sweeps);
+    memcpy(g.b[0], rhs, sizeof(double) * (size_t)nx * ny * nz);
+    int st = gmg_vcycle(&g, 0);
+    memcpy(e, g.x[0], sizeof(double) * (size_t)nx * ny * nz);
+    if (nlev_out) *nlev_out = g.nlev;
+    gmg_free(&g);
+    return st;
+}
+
+/* ------------------------------------------------------------ system + PCs */
+
+enum { PC_NONE = 0, PC_BJACOBI = 1, PC_BILU0 = 2, PC_CPR = 3 };
+
+typedef struct {
+    int nx, ny, nz, nb;
+    const int32_t *rp, *ci;
+    double *v;        /* owned copy of the values (float-rounded when requested) */
+    int pc;
+    double *dinv;     /* block Jacobi */
+    double *lu, *udinv; /* block ILU(0) */
+    double *w, *a7;   /* quasi-IMPES weights, pressure stencil */
+    or_gmg gmg;
+    double *tmp_p, *tmp_x, *tmp_r;
+    int64_t pc_applies;
+} or_system;
+
+static double round_f32(double x) { return (double)(float)x; }
+
+/* Create a system; float_round != 0 rounds every matrix value to float
+ * (the FP32 copy used by the inner solves of iterative refinement). */
+or_system *or_create(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v,
+                     int float_round) {
+    or_system *s = (or_system *)calloc(1, sizeof(or_system));
+    if (!s) return NULL;
+    s->nx = nx; s->ny = ny; s->nz = nz; s->nb = nx * ny * nz;
+    s->rp = rp; s->ci = ci;
+    size_t nv = 9 * (size_t)rp[s->nb];
+    s->v = (double *)malloc(sizeof(double) * nv);
+    for (size_t q = 0; q < nv; ++q) s->v[q] = float_round ? round_f32(v[q]) : v[q];
+    return s;
+}
+
+void or_destroy(or_system *s) {
+    if (!s) return;
+    free(s->v); free(s->dinv); free(s->lu); free(s->udinv); free(s->w); free(s->a7);
+    free(s->tmp_p); free(s->tmp_x); free(s->tmp_r);
+    if (s->gmg.nlev) gmg_free(&s->gmg);
+    free(s);
+}
+
+/* Preconditioner setup.  pc: 0 none, 1 block Jacobi, 2 block ILU(0),
+ * 3 CPR (quasi-IMPES + GMG V-cycle pressure stage, then block ILU(0)).
+ * float_round != 0 rounds the stored factors to float after setup. */
+int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweeps, int float_round) {
+    int nb = s->nb;
+    s->pc = pc;
+    int st = OR_OK;
+    if (pc == PC_BJACOBI) {
+        s->dinv = (double *)malloc(sizeof(double) * 9 * (size_t)nb);
+        st = or_bj_setup(nb, s->rp, s->ci, s->v, s->dinv);
+        if (float_round)
+            for (size_t q = 0; q < 9 * (size_t)nb; ++q) s->dinv[q] = round_f32(s->dinv[q]);
+    }
+    if (pc == PC_BILU0 || pc == PC_CPR) {
+        s->lu = (double *)malloc(sizeof(double) * 9 * (size_t)s->rp[nb]);
+        s->udinv = (double *)malloc(sizeof(double) * 9 * (size_t)nb);
+        int64_t off = 0;
+        st = or_bilu0_setup(nb, s->rp, s->ci, s->v, s->lu, s->udinv, &off);
+        if (float_round) {
+            for (size_t q = 0; q < 9 * (size_t)s->rp[nb]; ++q) s->lu[q] = round_f32(s->lu[q]);
+            for (size_t q = 0; q < 9 * (size_t)nb; ++q) s->udinv[q] = round_f32(s->udinv[q]);
+        }
+    }
+    if (st) return st;
+    if (pc == PC_CPR) {
+        s->w = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
+        s->a7 = (double *)malloc(sizeof(double) * 7 * (size_t)nb);
+        st = or_qi_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, s->w, s->a7);
+        if (st) return st;
+        if (float_round) {
+            for (size_t q = 0; q < 3 * (size_t)nb; ++q) s->w[q] = round_f32(s->w[q]);
+            for (size_t q = 0; q < 7 * (size_t)nb; ++q) s->a7[q] = round_f32(s->a7[q]);
+        }
+        gmg_build(&s->gmg, s->nx, s->ny, s->nz, s->a7, gmg_levels, gmg_coarse, gmg_sweeps);
+        if (float_round)
+            for (int l = 1; l < s->gmg.nlev; ++l)
+                for (size_t q = 0; q < 7 * (size_t)s->gmg.nx[l] * s->gmg.ny[l] * s->gmg.nz[l]; ++q)
+                    s->gmg.a7[l][q] = round_f32(s->gmg.a7[l][q]);
+        s->tmp_p = (double *)malloc(sizeof(double) * (size_t)nb);
+        s->tmp_x = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
+        s->tmp_r = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
+    }
+    return st;
+}
+
+/* CPR-PF in its two-stage multiplicative form (the printed listing overwrites
+ * x and reuses f; the reading here is the standard one):
+ *   x = Pi_p M_g^{-1} Pi_r f;  r = f - A x;  x = x + ILU0^{-1} r. */
+static int cpr_apply(or_system *s, const double *f, double *x) {
+    int nb = s->nb;
+    or_restrict_pressure(nb, s->w, f, s->gmg.b[0]);
+    int st = gmg_vcycle(&s->gmg, 0);
+    if (st) return st;
+    or_prolong_pressure(nb, s->gmg.x[0], x);
+    memcpy(s->tmp_r, f, sizeof(double) * 3 * (size_t)nb);
+    or_spmv(nb, s->rp, s->ci, s->v, -1.0, x, 1.0, s->tmp_r);
+    or_bilu0_apply(nb, s->rp, s->ci, s->lu, s->udinv, s->tmp_r, s->tmp_x);
+    for (int64_t q = 0; q < 3 * (int64_t)nb; ++q) x[q] += s->tmp_x[q];
+    return OR_OK;
+}
+
+/* z = M^{-1} r for the configured preconditioner. */
+int or_pc_apply(or_system *s, const double *r, double *z) {
+    int64_t n = 3 * (int64_t)s->nb;
+    s->pc_applies++;
+    switch (s->pc) {
+    case PC_NONE: memcpy(z, r, sizeof(double) * n); return OR_OK;
+    case PC_BJACOBI: or_bj_apply(s->nb, s->dinv, r, z); return OR_OK;
+    case PC_BILU0: or_bilu0_apply(s->nb, s->rp, s->ci, s->lu, s->udinv, r, z); return OR_OK;
+    case PC_CPR: return cpr_apply(s, r, z);
+    }
+    return OR_EINVAL;
+}
+
+void or_get_factors(const or_system *s, double *udinv, double *w, double *a7) {
+    if (udinv && s->udinv) memcpy(udinv, s->udinv, sizeof(double) * 9 * (size_t)s->nb);
+    if (udinv && s->dinv) memcpy(udinv, s->dinv, sizeof(double) * 9 * (size_t)s->nb);
+    if (w && s->w) memcpy(w, s->w, sizeof(double) * 3 * (size_t)s->nb);
+    if (a7 && s->a7) memcpy(a7, s->a7, sizeof(double) * 7 * (size_t)s->nb);
+}
+
+int or_gmg_levels(const or_system *s) { return s->gmg.nlev; }
+
+/* ------------------------------------------------------------------ GMRES */
+
+/* Restarted, right-preconditioned GMRES(m) (Saad's form) with modified
+ * Gram-Schmidt Arnoldi and Givens rotations; flexible != 0 keeps
+ * z_j = M^{-1} v_j (FGMRES) and updates x += Z y, otherwise x += M^{-1}(V y).
+ * Convergence: |g_{j+1}| <= rtol ||b|| ends a cycle; the true residual
+ * ||b - A x|| is then recomputed and a new cycle starts unless it also meets
+ * the tolerance.  iters counts Arnoldi steps over all cycles.
+ * stats[0] = iterations, stats[1] = restarts (cycles), stats[2] = final true
+ * relative residual, stats[3] = preconditioner applications. */
+int or_gmres(or_system *s, const double *b, double *x, int m, double rtol, int maxit, int flexible,
+             double *stats) {
+    int64_t n = 3 * (int64_t)s->nb;
+    double *V = (double *)malloc(sizeof(double) * (size_t)(m + 1) * n);
+    double *Z = flexible ? (double *)malloc(sizeof(double) * (size_t)m * n) : NULL;
+    double *w = (double *)malloc(sizeof(double) * n);
+    double *t = (double *)malloc(sizeof(double) * n);
+    double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = (double *)calloc(m, sizeof(double)), *sn = (double *)calloc(m, sizeof(double));
+    double *g = (double *)calloc(m + 1, sizeof(double)), *y = (double *)calloc(m, sizeof(double));
+    double bnorm = or_norm2(n, b);
+    double tol = rtol * bnorm;
+    int iters = 0, cycles = 0, st = OR_ENOCONV;
+    s->pc_applies = 0;
+    for (;;) {
+        memcpy(w, b, sizeof(double) * n);
+        or_spmv(s->nb, s->rp, s->ci, s->v, -1.0, x, 1.0, w);
+        double beta = or_norm2(n, w);
+        if (!isfinite(beta)) { st = OR_ENAN; break; }
+        if (beta <= tol) { st = OR_OK; break; }
+        if (iters >= maxit) { st = OR_ENOCONV; break; }
+        ++cycles;
+        for (int64_t q = 0; q < n; ++q) V[q] = w[q] / beta;
+        memset(g, 0, sizeof(double) * (m + 1));
+        g[0] = beta;
+        int jend = 0;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (size_t)j * n;
+            double *zj = flexible ? Z + (size_t)j * n : t;
+            int ps = or_pc_apply(s, vj, zj);
+            if (ps) { st = ps; goto done; }
+            or_spmv(s->nb, s->rp, s->ci, s->v, 1.0, zj, 0.0, w);
+            ++iters;
+            for (int i = 0; i <= j; ++i) {
+                double h = or_dot(n, w, V + (size_t)i * n);
+                H[(size_t)i * m + j] = h;
+                axpby(n, -h, V + (size_t)i * n, 1.0, w);
+            }
+            double hn = or_norm2(n, w);
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            double rho = hypot(a, bb);
+            if (!(rho > 0.0) || !isfinite(rho)) { st = isfinite(rho) ? OR_EBREAKDOWN : OR_ENAN; goto done; }
+            cs[j] = a / rho;
+            sn[j] = bb / rho;
+            H[(size_t)j * m + j] = rho;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jend = j + 1;
+            int lucky = !(hn > 0.0);
+            if (!lucky)
+                for (int64_t q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+            if (fabs(g[j + 1]) <= tol || iters >= maxit || lucky) break;
+        }
+        for (int i = jend - 1; i >= 0; --i) {
+            double sacc = g[i];
+            for (int q = i + 1; q < jend; ++q) sacc -= H[(size_t)i * m + q] * y[q];
+            y[i] = sacc / H[(size_t)i * m + i];
+        }
+        if (flexible) {
+            for (int i = 0; i < jend; ++i) axpby(n, y[i], Z + (size_t)i * n, 1.0, x);
+        } else {
+            memset(w, 0, sizeof(double) * n);
+            for (int i = 0; i < jend; ++i) axpby(n, y[i], V + (size_t)i * n, 1.0, w);
+            int ps = or_pc_apply(s, w, t);
+            if (ps) { st = ps; goto done; }
+            axpby(n, 1.0, t, 1.0, x);
+        }
+    }
+done:
+    if (stats) {
+        memcpy(w, b, sizeof(double) * n);
+        or_spmv(s->nb, s->rp, s->ci, s->v, -1.0, x, 1.0, w);
+        stats[0] = iters;
+        stats[1] = cycles;
+        stats[2] = or_norm2(n, w) / (bnorm > 0 ? bnorm : 1.0);
+        stats[3] = (double)s->pc_applies;
+    }
+    free(V); free(Z); free(w); free(t); free(H); free(cs); free(sn); free(g); free(y);
+    return st;
+}
+
+/* --------------------------------------------------------------- BiCGSTAB */
+
+/* Right-preconditioned BiCGSTAB (van der Vorst):
+ *   r = b - A x, rh = r, rho = alpha = omega = 1, v = p = 0; loop:
+ *   rho' = <rh, r>; beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v);
+ *   ph = M^{-1} p; v = A ph; alpha = rho' / <rh, v>; s = r - alpha v;
+ *   if ||s|| <= tol: x += alpha ph, stop;
+ *   sh = M^{-1} s; t = A sh; omega = <t,s>/<t,t>; x += alpha ph + omega sh;
+ *   r = s - omega t; rho = rho'; stop if ||r|| <= tol.
+ * |rho'|, |<rh,v>| or |omega| at or below btol (relative to the norms
+ * involved) is a breakdown.  iters counts loop passes. */
+int or_bicgstab(or_system *s, const double *b, double *x, double rtol, double btol, int maxit,
+                double *stats) {
+    int64_t n = 3 * (int64_t)s->nb;
+    double *r = (double *)malloc(sizeof(double) * n), *rh = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)calloc(n, sizeof(double)), *v = (double *)calloc(n, sizeof(double));
+    double *ph = (double *)malloc(sizeof(double) * n), *sh = (double *)malloc(sizeof(double) * n);
+    double *sv = (double *)malloc(sizeof(double) * n), *t = (double *)malloc(sizeof(double) * n);
+    double bnorm = or_norm2(n, b), tol = rtol * bnorm;
+    memcpy(r, b, sizeof(double) * n);
+    or_spmv(s->nb, s->rp, s->ci, s->v, -1.0, x, 1.0, r);
+    memcpy(rh, r, sizeof(double) * n);
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    int it = 0, st = OR_ENOCONV;
+    s->pc_applies = 0;
+    double rn = or_norm2(n, r);
+    if (rn <= tol) st = OR_OK;
+    double rhn = rn;
+    while (st == OR_ENOCONV && it < maxit) {
+        ++it;
+        double rho1 = or_dot(n, rh, r);
+        if (!isfinite(rho1)) { st = OR_ENAN; break; }
+        if (fabs(rho1) <= btol * rhn * rn) { st = OR_EBREAKDOWN; break; }
+        double beta = (rho1 / rho) * (alpha / omega);
+        for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
+        int ps = or_pc_apply(s, p, ph);
+        if (ps) { st = ps; break; }
+        or_spmv(s->nb, s->rp, s->ci, s->v, 1.0, ph, 0.0, v);
+        double rv = or_dot(n, rh, v);
+        if (fabs(rv) <= btol * rhn * or_norm2(n, v)) { st = OR_EBREAKDOWN; break; }
+        alpha = rho1 / rv;
+        for (int64_t q = 0; q < n; ++q) sv[q] = r[q] - alpha * v[q];
+        double sn = or_norm2(n, sv);
+        if (sn <= tol) {
+            axpby(n, alpha, ph, 1.0, x);
+            st = OR_OK;
+            break;
+        }
+        ps = or_pc_apply(s, sv, sh);
+        if (ps) { st = ps; break; }
+        or_spmv(s->nb, s->rp, s->ci, s->v, 1.0, sh, 0.0, t);
+        double tt = or_dot(n, t, t);
+        double ts = or_dot(n, t, sv);
+        if (!(tt > 0.0)) { st = OR_EBREAKDOWN; break; }
+        omega = ts / tt;
+        if (fabs(omega) <= btol) { st = OR_EBREAKDOWN; break; }
+        for (int64_t q = 0; q < n; ++q) {
+            x[q] += alpha * ph[q] + omega * sh[q];
+            r[q] = sv[q] - omega * t[q];
+        }
+        rho = rho1;
+        rn = or_norm2(n, r);
+        if (!isfinite(rn)) { st = OR_ENAN; break; }
+        if (rn <= tol) st = OR_OK;
+    }
+    if (stats) {
+        memcpy(r, b, sizeof(double) * n);
+        or_spmv(s->nb, s->rp, s->ci, s->v, -1.0, x, 1.0, r);
+        stats[0] = it;
+        stats[1] = 0;
+        stats[2] = or_norm2(n, r) / (bnorm > 0 ? bnorm : 1.0);
+        stats[3] = (double)s->pc_applies;
+    }
+    free(r); free(rh); free(p); free(v); free(ph); free(sh); free(sv); free(t);
+    return st;
+}
+
+/* ----------------------------------------------------- iterative refinement */
+
+/* FP64 outer loop around inner solves on the float-rounded system `inner`:
+ *   r = b - A64 x;  stop if ||r|| <= rtol ||b||;  solve inner d ~ r to
+ *   inner_rtol (relative to ||r||) from d = 0;  x += d;  at most max_outer.
+ * solver: 0 GMRES(m), 1 BiCGSTAB.  stats[0] = inner iterations summed,
+ * stats[1] = outer steps, stats[2] = final true relative residual. */
+int or_refine(or_system *outer, or_system *inner, const double *b, double *x, int solver, int m,
+              double rtol, double inner_rtol, int max_outer, int maxit, double *stats) {
+    int64_t n = 3 * (int64_t)outer->nb;
+    double *r = (double *)malloc(sizeof(double) * n), *d = (double *)malloc(sizeof(double) * n);
+    double bnorm = or_norm2(n, b);
+    int outer_steps = 0, inner_total = 0, st = OR_ENOCONV;
+    double rel = 1.0;
+    for (;;) {
+        memcpy(r, b, sizeof(double) * n);
+        or_spmv(outer->nb, outer->rp, outer->ci, outer->v, -1.0, x, 1.0, r);
+        double rn = or_norm2(n, r);
+        rel = rn / (bnorm > 0 ? bnorm : 1.0);
+        if (!isfinite(rn)) { st = OR_ENAN; break; }
+        if (rn <= rtol * bnorm) { st = OR_OK; break; }
+        if (outer_steps >= max_outer || inner_total >= maxit) { st = OR_ENOCONV; break; }
+        ++outer_steps;
+        memset(d, 0, sizeof(double) * n);
+        double ist[4] = {0, 0, 0, 0};
+        int is = (solver == 0) ? or_gmres(inner, r, d, m, inner_rtol, maxit - inner_total, 0, ist)
+                               : or_bicgstab(inner, r, d, inner_rtol, 1e-30, maxit - inner_total, ist);
+        inner_total += (int)ist[0];
+        if (is != OR_OK && is != OR_ENOCONV) { st = is; break; }
+        axpby(n, 1.0, d, 1.0, x);
+    }
+    if (stats) { stats[0] = inner_total; stats[1] = outer_steps; stats[2] = rel; stats[3] = 0; }
+    free(r); free(d);
+    return st;
+}

@@ -1,0 +1,47 @@
+"""Small dense helpers shared by the tests (brute-force references)."""
+import numpy as np
+
+
+def bsr_to_dense(row_ptr, col_idx, vals):
+    nb = len(row_ptr) - 1
+    A = np.zeros((3 * nb, 3 * nb))
+    for r in range(nb):
+        for p in range(row_ptr[r], row_ptr[r + 1]):
+            c = col_idx[p]
+            A[3 * r:3 * r + 3, 3 * c:3 * c + 3] = vals[p]
+    return A
+
+
+def stencil_to_dense(nx, ny, nz, a7):
+    """Dense matrix of a seven-point stencil (slots -z,-y,-x,centre,+x,+y,+z)."""
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    offs = [(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    for c in range(n):
+        i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+        for s, (di, dj, dk) in enumerate(offs):
+            ii, jj, kk = i + di, j + dj, k + dk
+            if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                A[c, nx * ny * kk + nx * jj + ii] += a7[c, s]
+    return A
+
+
+def kron_bsr(nx, ny, nz, m_block, acc_block, trans=lambda c, o: 1.0):
+    """BSR matrix sum_faces T (e_i - e_j) e_i^T (x) M + I (x) acc on the seven-point pattern."""
+    import synth
+    rp, ci = synth.seven_point_pattern(nx, ny, nz)
+    nb = nx * ny * nz
+    vals = np.zeros((len(ci), 3, 3))
+    for r in range(nb):
+        diag = np.array(acc_block, dtype=float).copy()
+        dpos = None
+        for p in range(rp[r], rp[r + 1]):
+            c = ci[p]
+            if c == r:
+                dpos = p
+                continue
+            t = trans(r, c)
+            vals[p] = -t * np.asarray(m_block)
+            diag = diag + t * np.asarray(m_block)
+        vals[dpos] = diag
+    return rp, ci, vals
