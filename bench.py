@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark: time to solve A x = b to rtol 1e-8 on one GB300, plus BSR SpMV HBM GB/s.
+
+Workload: the 100x100x50 grid (500,000 cells, 1.5M unknowns) with layered
+permeability (seed 1), solved by GMRES(30) + block ILU(0) in wavefront order.
+One step = preconditioner setup + solve from x0 = 0 with the matrix and right-
+hand side already resident in HBM.  The matrix (249 MB of FP64 blocks) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
+instead, on a bounded sample of the same workload scaled to the full solve.
+Multi-GPU (torchrun): independent replicas, one per GPU, timed together; the
+solver has no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve time to rtol 1e-8 + SpMV HBM GB/s; mixed/learned vs plain FP64 on 1 GB300"
+WORKLOAD = "mid_100x100x50"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129e6
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if key in d and isinstance(d[key], (int, float)):
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def spmv_bytes(nb, nnzb, val_bytes=8):
+    """Algorithmic bytes of one SpMV: blocks + column indices + row pointers + x + y."""
+    return nnzb * (9 * val_bytes + 4) + (nb + 1) * 4 + 2 * nb * 3 * val_bytes
+
+
+def ilu_apply_bytes(nb, nnzb, val_bytes=8):
+    """Algorithmic bytes of one block ILU(0) apply: every off-diagonal block once (lower
+    blocks forward, upper backward), D^{-1} twice, r read, y written, y read, z written."""
+    return (nnzb - nb) * 9 * val_bytes + 2 * nb * 9 * val_bytes + 4 * nb * 3 * val_bytes
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def cpu_baseline(p, gpu_iters, sample_iters, solver="gmres", pc="bilu0"):
+    """Time the oracle (as it stands, one thread) on the first `sample_iters` Krylov
+    iterations of the workload and scale its solve time to `gpu_iters` iterations."""
+    import oracle
+    t0 = time.perf_counter()
+    s = oracle.System.from_problem(p, pc=pc)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, x, info = s.gmres(p.b, m=30, maxit=sample_iters) if solver == "gmres" else s.bicgstab(p.b, maxit=sample_iters)
+    t_solve = time.perf_counter() - t0
+    done = max(info["iters"], 1)
+    est_ms = 1e3 * (t_setup + t_solve * gpu_iters / done)
+    return {"value": round(est_ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"oracle setup + first {done} of {gpu_iters} GMRES(30)+BILU0 iterations on {WORKLOAD} "
+                      f"({t_setup + t_solve:.1f} s of CPU work), solve time scaled linearly to {gpu_iters} iterations"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return 0
+    import synth
+    p = synth.workload(WORKLOAD)
+    full_iters = 456  # oracle iteration count on this workload (tests/golden/oracle_solves.json)
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+    try:
+        full_iters = json.load(open(gold))[f"{WORKLOAD}/gmres/bilu0"]["iters"]
+    except (OSError, KeyError, ValueError):
+        pass
+    sample = max(5, args.ref_sample_iters)
+    for _ in range(args.warmup):
+        cpu_baseline(p, full_iters, 5)
+    vals = [cpu_baseline(p, full_iters, sample)["value"] for _ in range(args.steps)]
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "gmres(30)", "pc": "bilu0", "rtol": 1e-8},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} of {full_iters} iterations per step, scaled"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsv", choices=["rsv", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-iters", type=int, default=60)
+    ap.add_argument("--ref-sample-iters", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "rsv":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    rank, ws, local, dist = dist_init()
+    if args.impl == "reference":
+        rc = run_reference(args, rank, ws)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    import numpy as np
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = synth.workload(WORKLOAD)
+    A = rsv.Matrix(p.nx, p.ny, p.nz, stream=stream)
+    vals_d = torch.from_numpy(p.vals).to(dev)
+    A.set_values(vals_d)
+    b = torch.from_numpy(p.b).to(dev)
+    x = torch.zeros_like(b)
+    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=2000)
+
+    def step():
+        s.setup("bilu0")
+        x.zero_()
+        st, info = s.solve(b, x)
+        if st != rsv.RSV_OK:
+            raise RuntimeError(f"solve failed: {rsv.status_string(st)} {info}")
+        return info
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    l0 = rsv.rsv_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = rsv.rsv_kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clocks = sampler.stop()
+    info = infos[-1]
+
+    # ---- kernel microbenchmarks on the same stream (CUDA events)
+    peak, peak_src = hbm_peak()
+    xs = torch.randn(p.n, dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    for _ in range(5):
+        A.spmv(xs, ys)
+    reps = 50
+    e0.record(stream)
+    for _ in range(reps):
+        A.spmv(xs, ys)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    spmv_ms = e0.elapsed_time(e1) / reps
+    sb = spmv_bytes(p.nb, p.nnzb)
+    spmv_gbs = sb / (spmv_ms * 1e-3) / 1e9
+    zs = torch.empty_like(xs)
+    for _ in range(2):
+        s.apply(xs, zs)
+    reps_i = 10
+    e0.record(stream)
+    for _ in range(reps_i):
+        s.apply(xs, zs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ilu_ms = e0.elapsed_time(e1) / reps_i
+    ib = ilu_apply_bytes(p.nb, p.nnzb)
+    ilu_gbs = ib / (ilu_ms * 1e-3) / 1e9
+    # dominant kernel per Krylov iteration: one ILU apply vs one SpMV
+    if ilu_ms >= spmv_ms:
+        dom = {"kernel": "block ILU(0) apply (forward+backward wavefront sweeps)", "ms": ilu_ms, "bytes": ib,
+               "gbs": ilu_gbs}
+    else:
+        dom = {"kernel": "BSR SpMV", "ms": spmv_ms, "bytes": sb, "gbs": spmv_gbs}
+    roofline = {"bound": "hbm", "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(dom["gbs"] / peak, 4), "traffic": None, "kernel": dom["kernel"],
+                "algorithmic_bytes_per_launch": dom["bytes"], "avg_launch_ms": round(dom["ms"], 4),
+                "peak_source": peak_src}
+
+    # ---- end to end through the C ABI with host buffers
+    vals_h = torch.from_numpy(p.vals).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        A.set_values(vals_h.numpy())
+        s.setup("bilu0")
+        x_h.zero_()
+        st, einfo = s.solve(b_h.numpy(), x_h.numpy())
+        assert st == rsv.RSV_OK
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    wall_e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+    h2d = p.vals.nbytes + p.b.nbytes + p.b.nbytes
+    d2h = p.b.nbytes
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, info["iters"], args.cpu_sample_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [p.nx, p.ny, p.nz], "cells": p.nb, "unknowns": p.n,
+                       "nnzb": p.nnzb, "solver": "gmres(30)", "pc": "bilu0 (i+j+k wavefront)", "precision": "fp64",
+                       "rtol": 1e-8, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (FP64 blocks 249 MB > 129 MB), no flush"},
+            "iters": info["iters"], "true_relres": info["true_relres"], "ms_setup": round(info["ms_setup"], 3),
+            "ms_solve": round(info["ms_solve"], 3),
+            "spmv": {"gbs": round(spmv_gbs, 1), "frac_of_peak": round(spmv_gbs / peak, 4), "avg_launch_ms":
+                     round(spmv_ms, 4), "algorithmic_bytes": sb},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "wall_ms": round(wall_e2e_ms, 3),
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * rsv.h - C ABI of the GB300 reservoir linear-solver library (librsv.so).
+ *
+ * The library solves the Newton linear systems A x = b of a black-oil-like
+ * reservoir model on one GPU: A is the 3x3-block Jacobian of a cell-centred
+ * structured nx*ny*nz grid with a seven-point two-point-flux stencil.
+ * The calls follow the paper's problem statement: a structured grid
+ * (Section "Grid"), the map from cells to unknowns (Section "MAP"), a block
+ * matrix and vectors (Section "Distributed Matrices" and "Algebraic
+ * Operations"), a solver with rtol/atol/btol/maxit/restart (Section
+ * "Solvers", SOLVER structure) and a preconditioner with setup/apply/destroy
+ * (Section "Preconditioners", SOLVER_PC and PC_TYPE).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an rsv_status; no call aborts, traps or prints.  On an
+ *    error nothing is left half-allocated; output arguments are untouched.
+ *  - Handles are opaque and own the device memory they allocate.  Host
+ *    arrays passed in are copied before the call returns.
+ *  - Device pointers are plain CUDA global-memory addresses on the current
+ *    device (for example torch.Tensor.data_ptr()); the caller keeps them
+ *    alive for the duration of the call.
+ *  - A `stream` argument is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  All device work of a handle is issued on the stream it
+ *    was created with; calls that return results to the host synchronise it.
+ *  - Cell index c = nx*ny*k + nx*j + i (Section "Grid", default bottom-up
+ *    index); unknown 3c+e with e = 0 pressure and e = 1, 2 secondary
+ *    (point-interleaved: a permutation of the paper's field-major vector x).
+ *  - BSR layout: row_ptr int32[nb+1], col_idx int32[nnzb] ascending per row,
+ *    values float64[nnzb][3][3] row-major blocks.
+ */
+#ifndef RSV_H
+#define RSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RSV_API __attribute__((visibility("default")))
+#else
+#define RSV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RSV_OK = 0,
+    RSV_EINVAL = 1,      /* bad argument (null, size, range, wrong state) */
+    RSV_ENOMEM = 2,      /* device or host allocation failed */
+    RSV_ECUDA = 3,       /* a CUDA runtime call failed */
+    RSV_ENOTSUP = 4,     /* combination not supported */
+    RSV_ESINGULAR = 5,   /* a 3x3 pivot or coarse-grid pivot with |p| <= 1e-300 */
+    RSV_EBREAKDOWN = 6,  /* Krylov breakdown (rho, <rh,v>, omega or Givens radius vanished) */
+    RSV_ENOCONV = 7,     /* maxit reached; x holds the last iterate, info is filled */
+    RSV_ETIMEOUT = 8,    /* a bounded device-side wait ran out */
+    RSV_ENAN = 9         /* NaN or Inf met in a norm */
+} rsv_status;
+
+typedef enum { RSV_PC_NONE = 0, RSV_PC_BJACOBI = 1, RSV_PC_BILU0 = 2, RSV_PC_CPR = 3 } rsv_pc_type;
+typedef enum { RSV_GMRES = 0, RSV_BICGSTAB = 1, RSV_FGMRES = 2 } rsv_solver_type;
+typedef enum { RSV_PREC_FP64 = 0, RSV_PREC_MIXED = 1 } rsv_precision;
+
+typedef struct rsv_grid rsv_grid;
+typedef struct rsv_mat rsv_mat;
+typedef struct rsv_solver rsv_solver;
+
+/* Solver parameters (the paper's SOLVER fields rtol, atol, btol, maxit,
+ * restart; Section "Solvers").  Convergence: ||b - A x||_2 <=
+ * max(rtol ||b||_2, atol), always confirmed on the FP64 true residual.
+ * btol: breakdown threshold, relative to the norms involved. */
+typedef struct {
+    int solver;            /* rsv_solver_type */
+    int restart;           /* GMRES restart length m, 1..64 */
+    double rtol;
+    double atol;
+    double btol;
+    int maxit;             /* Krylov iterations (Arnoldi steps / BiCGSTAB passes), summed */
+    int precision;         /* rsv_precision: FP64, or FP32 inner solves + FP64 refinement */
+    double inner_rtol;     /* mixed: inner tolerance relative to the current outer residual */
+    int max_outer;         /* mixed: maximum refinement steps */
+    long long watchdog;    /* spin limit of every bounded device-side wait */
+} rsv_solver_params;
+
+/* Preconditioner parameters.  GMG defaults follow the paper's AMG defaults
+ * (one V-cycle, at most 6 levels, 2 relaxation sweeps; Section "Algebraic
+ * Multigrid Methods", default-parameter figure). */
+typedef struct {
+    int gmg_max_levels;    /* <= 8 */
+    int gmg_max_coarse;    /* stop coarsening at or below this many cells */
+    int gmg_sweeps;        /* red-black Gauss-Seidel sweeps before and after */
+} rsv_pc_params;
+
+/* Filled by rsv_solve. */
+typedef struct {
+    int iters;             /* Krylov iterations summed over restarts / outer steps */
+    int restarts;          /* GMRES cycles */
+    int outer_iters;       /* refinement steps (mixed precision), else 0 */
+    int status;            /* rsv_status of the solve */
+    double true_relres;    /* ||b - A x|| / ||b|| recomputed in FP64 on the device */
+    double ms_setup;       /* last rsv_precond_setup, CUDA-event time */
+    double ms_solve;       /* this solve, CUDA-event time */
+} rsv_solve_info;
+
+/* Defaults: GMRES, m = 30, rtol 1e-8, atol 0, btol 1e-30, maxit 2000, FP64,
+ * inner_rtol 1e-5, max_outer 10, watchdog 1<<26. */
+RSV_API void rsv_solver_params_default(rsv_solver_params *p);
+/* Defaults: 6 levels, 512 coarse cells, 2 sweeps. */
+RSV_API void rsv_pc_params_default(rsv_pc_params *p);
+RSV_API const char *rsv_status_string(rsv_status s);
+/* Text of the last CUDA runtime error seen by a call on this thread that
+ * returned RSV_ECUDA or RSV_ENOMEM ("no error" if none). */
+RSV_API const char *rsv_last_cuda_error(void);
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all handles); a diagnostic counter for benchmarks. */
+RSV_API uint64_t rsv_kernel_launches(void);
+
+/* ---- grid (Section "Grid": structured grid, default cell index) ---------
+ * nx, ny, nz >= 1 and nx*ny*nz*3 < 2^31.  The grid is host-only metadata. */
+RSV_API rsv_status rsv_grid_create(int nx, int ny, int nz, rsv_grid **out);
+RSV_API void rsv_grid_destroy(rsv_grid *g);
+
+/* ---- matrix (Sections "Distributed Matrices", "Algebraic Operations") ---
+ * Creates the seven-point 3x3-block BSR pattern of the grid on the device
+ * (rows ascending, columns ascending: -z, -y, -x, self, +x, +y, +z).
+ * Values start at zero.  The grid may be destroyed afterwards. */
+RSV_API rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out);
+RSV_API void rsv_mat_destroy(rsv_mat *A);
+/* Host views of the pattern, owned by the matrix (valid until destroy). */
+RSV_API rsv_status rsv_mat_get_pattern(const rsv_mat *A, const int32_t **row_ptr, const int32_t **col_idx,
+                               int64_t *nb, int64_t *nnzb);
+/* Copy nnzb*9 float64 block values (host or device pointer, on_device 0/1)
+ * into the matrix.  Invalidates any preconditioner built on it. */
+RSV_API rsv_status rsv_mat_set_values(rsv_mat *A, const double *vals, int on_device);
+
+/* y = alpha A x + beta y (Section "Algebraic Operations", first equation).
+ * x, y: device float64[3*nb]; x and y must not overlap. */
+RSV_API rsv_status rsv_spmv(const rsv_mat *A, double alpha, const double *x, double beta, double *y);
+/* Same in FP32: values rounded once to float at set_values time (the copy
+ * used by mixed-precision inner solves); x, y device float32[3*nb]. */
+RSV_API rsv_status rsv_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y);
+
+/* ---- vector algebra (Section "Algebraic Operations") --------------------
+ * Device float64 arrays of length n; the scalar result is returned on the
+ * host (the call synchronises the stream). */
+RSV_API rsv_status rsv_dot(void *stream, int64_t n, const double *x, const double *y, double *result);
+RSV_API rsv_status rsv_norm2(void *stream, int64_t n, const double *x, double *result);
+/* z = alpha x + beta y (z may alias x or y). */
+RSV_API rsv_status rsv_axpby(void *stream, int64_t n, double alpha, const double *x, double beta,
+                     const double *y, double *z);
+
+/* ---- solver + preconditioner (Sections "Solvers", "Preconditioners") ----
+ * The solver keeps a reference to A (A must outlive it) and allocates its
+ * Krylov workspace on A's stream. */
+RSV_API rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver **out);
+RSV_API void rsv_solver_destroy(rsv_solver *s);
+/* Build the preconditioner from A's current values:
+ *  NONE;  BJACOBI: inverted 3x3 diagonal blocks;
+ *  BILU0: block ILU(0) in natural order (Section "Restricted Additive Schwarz
+ *         Method": LU x = b <=> L y = b, U x = y; ILU(0) default), scheduled
+ *         along i+j+k wavefront hyperplanes;
+ *  CPR:   two-stage (Section "CPR-like Preconditioners", CPR-PF): quasi-IMPES
+ *         pressure restriction, geometric-multigrid V-cycle on the pressure
+ *         matrix (Section "Algebraic Multigrid Methods"), then block ILU(0).
+ * params may be NULL (defaults). */
+RSV_API rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params);
+/* z = M^{-1} r with the current preconditioner; device float64[3*nb]. */
+RSV_API rsv_status rsv_precond_apply(rsv_solver *s, const double *r, double *z);
+/* Copy the inverted diagonal blocks of the preconditioner (block Jacobi:
+ * A_ii^{-1}; block ILU(0): U_ii^{-1}) to host float64[nb][3][3]. */
+RSV_API rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host);
+/* Solve A x = b.  b, x: float64[3*nb], host (on_device = 0) or device
+ * (on_device = 1); x holds the initial guess on entry and the solution on
+ * return (also on ENOCONV).  info may be NULL. */
+RSV_API rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSV_H */

@@ -1,0 +1,232 @@
+"""Python binding of librsv, the GB300 reservoir linear-solver library.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+of ``librsv.so`` behind the C ABI declared in ``include/rsv.h``.  PyTorch
+supplies device memory (tensor ``data_ptr()``) and streams.  Importing this
+package loads the library and raises if it is missing; there is no CPU
+fallback.  Build it with ``paper_1602_05901_gb300._build.build()``.
+
+The module-level functions carry the C names (``rsv_grid_create`` ...) and
+return ``(status, outputs...)``; :class:`Matrix` and :class:`Solver` wrap
+the handles and raise :class:`RsvError` on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsv.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"librsv.so not built at {LIB_PATH}: run paper_1602_05901_gb300._build.build() "
+                      "(requires nvcc); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+RSV_OK, RSV_EINVAL, RSV_ENOMEM, RSV_ECUDA, RSV_ENOTSUP, RSV_ESINGULAR = 0, 1, 2, 3, 4, 5
+RSV_EBREAKDOWN, RSV_ENOCONV, RSV_ETIMEOUT, RSV_ENAN = 6, 7, 8, 9
+RSV_PC_NONE, RSV_PC_BJACOBI, RSV_PC_BILU0, RSV_PC_CPR = 0, 1, 2, 3
+RSV_GMRES, RSV_BICGSTAB, RSV_FGMRES = 0, 1, 2
+RSV_PREC_FP64, RSV_PREC_MIXED = 0, 1
+PC_TYPES = {"none": RSV_PC_NONE, "bjacobi": RSV_PC_BJACOBI, "bilu0": RSV_PC_BILU0, "cpr": RSV_PC_CPR}
+SOLVERS = {"gmres": RSV_GMRES, "bicgstab": RSV_BICGSTAB, "fgmres": RSV_FGMRES}
+
+
+class rsv_solver_params(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("restart", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("btol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("watchdog", ctypes.c_longlong)]
+
+
+class rsv_pc_params(ctypes.Structure):
+    _fields_ = [("gmg_max_levels", ctypes.c_int), ("gmg_max_coarse", ctypes.c_int), ("gmg_sweeps", ctypes.c_int)]
+
+
+class rsv_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("status", ctypes.c_int), ("true_relres", ctypes.c_double), ("ms_setup", ctypes.c_double),
+                ("ms_solve", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I, _D, _F, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.c_int64
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "rsv_solver_params_default": (None, [ctypes.POINTER(rsv_solver_params)]),
+    "rsv_pc_params_default": (None, [ctypes.POINTER(rsv_pc_params)]),
+    "rsv_status_string": (ctypes.c_char_p, [_I]),
+    "rsv_last_cuda_error": (ctypes.c_char_p, []),
+    "rsv_kernel_launches": (ctypes.c_uint64, []),
+    "rsv_grid_create": (_I, [_I, _I, _I, _PP]),
+    "rsv_grid_destroy": (None, [_P]),
+    "rsv_mat_create": (_I, [_P, _P, _PP]),
+    "rsv_mat_destroy": (None, [_P]),
+    "rsv_mat_get_pattern": (_I, [_P, _PP, _PP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "rsv_mat_set_values": (_I, [_P, _P, _I]),
+    "rsv_spmv": (_I, [_P, _D, _P, _D, _P]),
+    "rsv_spmv_f32": (_I, [_P, _F, _P, _F, _P]),
+    "rsv_dot": (_I, [_P, _I64, _P, _P, ctypes.POINTER(_D)]),
+    "rsv_norm2": (_I, [_P, _I64, _P, ctypes.POINTER(_D)]),
+    "rsv_axpby": (_I, [_P, _I64, _D, _P, _D, _P, _P]),
+    "rsv_solver_create": (_I, [_P, ctypes.POINTER(rsv_solver_params), _PP]),
+    "rsv_solver_destroy": (None, [_P]),
+    "rsv_precond_setup": (_I, [_P, _I, ctypes.POINTER(rsv_pc_params)]),
+    "rsv_precond_apply": (_I, [_P, _P, _P]),
+    "rsv_precond_get_dinv": (_I, [_P, _P]),
+    "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
+}
+EXPORTS = tuple(_SIGS)
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class RsvError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.rsv_status_string(status).decode()
+        if status in (RSV_ECUDA, RSV_ENOMEM):
+            msg += f" ({_lib.rsv_last_cuda_error().decode()})"
+        super().__init__(f"{where}: {msg} [{status}]")
+
+
+def check(status, where="rsv"):
+    if status != RSV_OK:
+        raise RsvError(status, where)
+    return status
+
+
+def status_string(status: int) -> str:
+    return _lib.rsv_status_string(status).decode()
+
+
+def _ptr(t):
+    """Raw address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(t, "data_ptr"):
+        assert t.is_contiguous()
+        return ctypes.c_void_p(t.data_ptr())
+    assert t.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def solver_params(solver="gmres", restart=30, rtol=1e-8, atol=0.0, btol=1e-30, maxit=2000, precision="fp64",
+                  inner_rtol=1e-5, max_outer=10, watchdog=None):
+    p = rsv_solver_params()
+    _lib.rsv_solver_params_default(ctypes.byref(p))
+    p.solver = SOLVERS[solver] if isinstance(solver, str) else solver
+    p.restart, p.rtol, p.atol, p.btol, p.maxit = restart, rtol, atol, btol, maxit
+    p.precision = {"fp64": RSV_PREC_FP64, "mixed": RSV_PREC_MIXED}[precision] if isinstance(precision, str) else precision
+    p.inner_rtol, p.max_outer = inner_rtol, max_outer
+    if watchdog is not None:
+        p.watchdog = watchdog
+    return p
+
+
+def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2):
+    p = rsv_pc_params()
+    _lib.rsv_pc_params_default(ctypes.byref(p))
+    p.gmg_max_levels, p.gmg_max_coarse, p.gmg_sweeps = gmg_max_levels, gmg_max_coarse, gmg_sweeps
+    return p
+
+
+class Matrix:
+    """Seven-point 3x3-block BSR matrix of an nx*ny*nz grid, resident on the GPU."""
+
+    def __init__(self, nx, ny, nz, stream=None):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.stream = _stream_ptr(stream)
+        g = ctypes.c_void_p()
+        check(_lib.rsv_grid_create(nx, ny, nz, ctypes.byref(g)), "rsv_grid_create")
+        h = ctypes.c_void_p()
+        try:
+            check(_lib.rsv_mat_create(g, self.stream, ctypes.byref(h)), "rsv_mat_create")
+        finally:
+            _lib.rsv_grid_destroy(g)
+        self.handle = h
+        rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+        nb, nnzb = _I64(), _I64()
+        check(_lib.rsv_mat_get_pattern(h, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(nb), ctypes.byref(nnzb)))
+        self.nb, self.nnzb = nb.value, nnzb.value
+        self.row_ptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int32)), (self.nb + 1,)).copy()
+        self.col_idx = np.ctypeslib.as_array(ctypes.cast(ci, ctypes.POINTER(ctypes.c_int32)), (self.nnzb,)).copy()
+
+    @property
+    def n(self):
+        return 3 * self.nb
+
+    def set_values(self, vals):
+        """vals: float64 [nnzb,3,3] as a numpy array (host) or CUDA torch tensor."""
+        on_dev = int(hasattr(vals, "is_cuda") and vals.is_cuda)
+        if not on_dev:
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        assert vals.size == 9 * self.nnzb if not on_dev else vals.numel() == 9 * self.nnzb
+        check(_lib.rsv_mat_set_values(self.handle, _ptr(vals), on_dev), "rsv_mat_set_values")
+
+    def spmv(self, x, y, alpha=1.0, beta=0.0):
+        if x.dtype.itemsize == 4:
+            check(_lib.rsv_spmv_f32(self.handle, alpha, _ptr(x), beta, _ptr(y)), "rsv_spmv_f32")
+        else:
+            check(_lib.rsv_spmv(self.handle, alpha, _ptr(x), beta, _ptr(y)), "rsv_spmv")
+        return y
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.rsv_mat_destroy(h)
+            self.handle = None
+
+
+class Solver:
+    """Krylov solver + preconditioner bound to a Matrix (which must outlive it)."""
+
+    def __init__(self, A: Matrix, **params):
+        self.A = A
+        self.params = solver_params(**params)
+        h = ctypes.c_void_p()
+        check(_lib.rsv_solver_create(A.handle, ctypes.byref(self.params), ctypes.byref(h)), "rsv_solver_create")
+        self.handle = h
+
+    def setup(self, pc="bilu0", **pcp):
+        st = _lib.rsv_precond_setup(self.handle, PC_TYPES[pc] if isinstance(pc, str) else pc,
+                                    ctypes.byref(pc_params(**pcp)))
+        check(st, "rsv_precond_setup")
+
+    def apply(self, r, z):
+        check(_lib.rsv_precond_apply(self.handle, _ptr(r), _ptr(z)), "rsv_precond_apply")
+        return z
+
+    def dinv(self):
+        out = np.zeros((self.A.nb, 3, 3))
+        check(_lib.rsv_precond_get_dinv(self.handle, _ptr(out)), "rsv_precond_get_dinv")
+        return out
+
+    def solve(self, b, x, raise_on_error=False):
+        """b, x: float64 [3*nb], both host numpy or both CUDA tensors. Returns (status, info dict)."""
+        on_dev = int(hasattr(b, "is_cuda") and b.is_cuda)
+        info = rsv_solve_info()
+        st = _lib.rsv_solve(self.handle, _ptr(b), _ptr(x), on_dev, ctypes.byref(info))
+        if raise_on_error:
+            check(st, "rsv_solve")
+        return st, info.as_dict()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.rsv_solver_destroy(h)
+            self.handle = None

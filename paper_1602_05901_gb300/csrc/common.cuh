@@ -1,0 +1,114 @@
+// Internal declarations shared by the CUDA translation units of librsv.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/rsv.h"
+
+#define RSV_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            rsv::set_last_cuda_error(e_);                    \
+            return RSV_ECUDA;                                \
+        }                                                    \
+    } while (0)
+
+#define RSV_TRY(expr)                                        \
+    do {                                                     \
+        rsv_status s_ = (expr);                              \
+        if (s_ != RSV_OK) return s_;                         \
+    } while (0)
+
+namespace rsv {
+
+constexpr int kMaxRestart = 64;
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs: grid of every reduction kernel
+constexpr int kRedThreads = 256;
+
+void set_last_cuda_error(cudaError_t e);
+// Process-wide count of kernel launches issued by the library.
+void count_launches(uint64_t n);
+
+// Solver scalars that live in device memory so that no Krylov step needs a
+// host round trip.  One instance per solver.
+struct DevState {
+    double H[(kMaxRestart + 1) * kMaxRestart];  // Hessenberg, row-major (m+1) x m, rotated in place
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double g[kMaxRestart + 1];
+    double y[kMaxRestart];
+    double h1[kMaxRestart + 1], h2[kMaxRestart + 1];  // CGS2 projection coefficients
+    double red[kMaxRestart + 1];                       // generic reduction outputs
+    double beta, hn, inv_hn, tol;
+    double rho, rho1, alpha, omega;
+    double bnorm;
+    int done;       // 1: stop this cycle / iteration loop
+    int status;     // rsv_status raised on the device (breakdown, nan, singular)
+    int iters;      // Krylov iterations so far (device count)
+    int jend;       // Arnoldi steps taken in the current cycle
+    int maxit;
+    unsigned counter[4];  // last-block tickets of the reduction kernels
+};
+
+struct Schedule {  // i+j+k wavefront hyperplanes
+    std::vector<int> plane_ptr;  // host, nplanes+1
+    int32_t *cells = nullptr;    // device, nb cell indices grouped by plane (ascending within)
+    int nplanes = 0;
+};
+
+}  // namespace rsv
+
+struct rsv_grid {
+    int nx, ny, nz;
+};
+
+struct rsv_mat {
+    int nx, ny, nz;
+    int64_t nb, nnzb;
+    cudaStream_t stream;
+    std::vector<int32_t> h_rp, h_ci;
+    int32_t *d_rp = nullptr, *d_ci = nullptr;
+    double *d_v = nullptr;   // nnzb*9 (+ tail pad)
+    float *d_v32 = nullptr;  // FP32 copy of the values
+    uint64_t version = 0;
+};
+
+namespace rsv {
+
+// ---- launchers implemented in spmv.cu
+cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
+                            const int *done);
+cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
+                            const int *done);
+cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b);
+
+// ---- launchers implemented in blas.cu
+// out[i] = <w, V_i> for i < k; V_i = V + i*ldv.  Deterministic two-level reduction.
+cudaError_t launch_mdot(cudaStream_t st, int64_t n, const double *w, const double *V, int64_t ldv, int k,
+                        double *partial, double *out, unsigned *counter, const int *done);
+// out = base + sgn * sum_i c[i] V_i; if nrm != nullptr, *nrm = ||out||_2.
+cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const double *base, const double *V, int64_t ldv,
+                         int k, const double *c, double sgn, double *out, double *partial, double *nrm,
+                         unsigned *counter, const int *done);
+// *out = ||x||_2 (sqrt_out=1) or <x,y>
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const double *x, const double *y, double *partial,
+                       double *out, unsigned *counter, int sqrt_out, const int *done);
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double *x, double b, const double *y,
+                         double *z);
+// x *= 1/(*s) (device scalar), skipping when *done
+cudaError_t launch_scale_inv(cudaStream_t st, int64_t n, double *x, const double *s, const int *done);
+
+// ---- launchers implemented in precond.cu
+cudaError_t build_schedule(const rsv_mat *A, Schedule *sch);
+void free_schedule(Schedule *sch);
+cudaError_t launch_bj_setup(const rsv_mat *A, double *dinv, int *status);
+cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const double *dinv, const double *r, double *z,
+                            const int *done);
+cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, double *dinv, int *status);
+cudaError_t launch_ilu_apply(const rsv_mat *A, const Schedule &sch, const double *dinv, const double *r,
+                             double *z, const int *done);
+
+}  // namespace rsv

@@ -1,0 +1,60 @@
+"""The C ABI library loads and exports every entry point the header declares (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rsv.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"RSV_API\s+[\w\s\*]*?\b(rsv_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1602_05901_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("rsv_grid_create", "rsv_mat_create", "rsv_mat_set_values", "rsv_spmv", "rsv_solver_create",
+                 "rsv_precond_setup", "rsv_solve"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L, path = lib
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s+(rsv_\w+)", out))
+    assert exported == set(declared_functions())
+
+
+def test_binding_covers_exports():
+    import paper_1602_05901_gb300 as rsv
+    assert set(rsv.EXPORTS) == set(declared_functions())
+
+
+def test_host_side_argument_checks_without_gpu():
+    import paper_1602_05901_gb300 as rsv
+    g = ctypes.c_void_p()
+    assert rsv.rsv_grid_create(0, 4, 4, ctypes.byref(g)) == rsv.RSV_EINVAL
+    assert rsv.rsv_grid_create(4, 4, 4, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_grid_create(2000, 2000, 2000, ctypes.byref(g)) == rsv.RSV_EINVAL
+    assert rsv.rsv_grid_create(3, 2, 1, ctypes.byref(g)) == rsv.RSV_OK
+    rsv.rsv_grid_destroy(g)
+    assert rsv.rsv_mat_create(None, None, ctypes.byref(g)) == rsv.RSV_EINVAL
+    assert rsv.rsv_solver_create(None, None, ctypes.byref(g)) == rsv.RSV_EINVAL
+    assert rsv.rsv_precond_setup(None, 1, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_solve(None, None, None, 0, None) == rsv.RSV_EINVAL
+    assert rsv.status_string(rsv.RSV_ENOCONV) == "not converged within maxit"
+    p = rsv.solver_params()
+    assert (p.restart, p.rtol, p.maxit, p.btol) == (30, 1e-8, 2000, 1e-30)

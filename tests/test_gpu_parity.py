@@ -1,0 +1,240 @@
+"""GPU path (through the C ABI) against the CPU oracle on the same seeded inputs."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solves.json")
+
+
+@pytest.fixture(scope="module")
+def rsv():
+    from paper_1602_05901_gb300 import _build
+    _build.build()
+    import paper_1602_05901_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def _mat(rsv, p):
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    assert np.array_equal(A.row_ptr, p.row_ptr) and np.array_equal(A.col_idx, p.col_idx)
+    A.set_values(p.vals)
+    return A
+
+
+def _row_scale(p, x):
+    """|A| |x| per scalar row: the scale of each SpMV entry's rounding error."""
+    return oracle.spmv(p.row_ptr, p.col_idx, np.abs(p.vals), np.abs(x))
+
+
+SPMV_DIMS = [(1, 1, 1), (2, 2, 1), (7, 5, 3), (20, 20, 10), (33, 17, 9), (100, 100, 50)]
+
+
+@pytest.mark.parametrize("dims", SPMV_DIMS)
+def test_spmv_fp64_per_entry(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=31)
+    A = _mat(rsv, p)
+    rng = np.random.default_rng(32)
+    x, y0 = rng.standard_normal(p.n), rng.standard_normal(p.n)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y0).cuda()
+    A.spmv(xd, yd, alpha=-0.75, beta=1.25)
+    torch.cuda.synchronize()
+    ref = oracle.spmv(p.row_ptr, p.col_idx, p.vals, x, alpha=-0.75, beta=1.25, y=y0)
+    scale = 0.75 * _row_scale(p, x) + 1.25 * np.abs(y0)
+    err = np.abs(yd.cpu().numpy() - ref)
+    assert np.all(err <= 1e-12 * scale), err.max()
+    # beta = 0 must not read y (NaN garbage in y stays out)
+    yd.fill_(float("nan"))
+    A.spmv(xd, yd)
+    ref0 = oracle.spmv(p.row_ptr, p.col_idx, p.vals, x)
+    assert np.all(np.abs(yd.cpu().numpy() - ref0) <= 1e-12 * _row_scale(p, x))
+
+
+@pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 9)])
+def test_spmv_fp32_per_entry(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=33)
+    A = _mat(rsv, p)
+    x = np.random.default_rng(34).standard_normal(p.n).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    A.spmv(xd, yd)
+    torch.cuda.synchronize()
+    v32 = p.vals.astype(np.float32).astype(np.float64)
+    ref = oracle.spmv(p.row_ptr, p.col_idx, v32, x.astype(np.float64))
+    scale = _row_scale(p, x.astype(np.float64))
+    assert np.all(np.abs(yd.cpu().numpy() - ref) <= 24 * 2.0 ** -24 * scale)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 3 * 33 * 17 * 9, 1_500_000])
+def test_blas1(rsv, torch, n):
+    import ctypes
+    rng = np.random.default_rng(n)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = ctypes.c_double()
+    s = torch.cuda.current_stream().cuda_stream
+    assert rsv.rsv_dot(s, n, xd.data_ptr(), yd.data_ptr(), ctypes.byref(out)) == 0
+    assert abs(out.value - oracle.dot(x, y)) <= 1e-13 * np.abs(x * y).sum()
+    assert rsv.rsv_norm2(s, n, xd.data_ptr(), ctypes.byref(out)) == 0
+    assert abs(out.value - oracle.norm2(x)) <= 1e-13 * oracle.norm2(x)
+    zd = torch.empty_like(xd)
+    assert rsv.rsv_axpby(s, n, 0.5, xd.data_ptr(), -2.0, yd.data_ptr(), zd.data_ptr()) == 0
+    torch.cuda.synchronize()
+    assert np.allclose(zd.cpu().numpy(), 0.5 * x - 2.0 * y, rtol=0, atol=1e-15 * (np.abs(x) + np.abs(y)).max())
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (9, 1, 1), (7, 5, 3), (20, 20, 10), (33, 17, 9)])
+@pytest.mark.parametrize("pc", ["bjacobi", "bilu0"])
+def test_preconditioner_factor_and_apply(rsv, torch, dims, pc):
+    p = synth.make_problem(*dims, seed=35)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A)
+    s.setup(pc)
+    o = oracle.System.from_problem(p, pc=pc)
+    assert o.setup_status == 0
+    d_or, _, _ = o.factors()
+    d_gpu = s.dinv()
+    assert np.all(np.abs(d_gpu - d_or) <= 1e-12 * np.abs(d_or).max(axis=(1, 2), keepdims=True))
+    r = np.random.default_rng(36).standard_normal(p.n)
+    rd = torch.from_numpy(r).cuda()
+    zd = torch.zeros_like(rd)
+    s.apply(rd, zd)
+    torch.cuda.synchronize()
+    _, z_or = o.pc_apply(r)
+    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-11 * np.linalg.norm(z_or)
+
+
+SOLVES = [("bicgstab", "bjacobi"), ("gmres", "bilu0"), ("fgmres", "bilu0"), ("bicgstab", "bilu0"),
+          ("gmres", "bjacobi"), ("gmres", "none")]
+
+
+def _oracle_solve(p, solver, pc, m=30, maxit=2000):
+    o = oracle.System.from_problem(p, pc=pc)
+    if solver == "bicgstab":
+        return o.bicgstab(p.b, maxit=maxit)
+    return o.gmres(p.b, m=m, flexible=(solver == "fgmres"), maxit=maxit)
+
+
+def _iters_close(a, b):
+    return abs(a - b) <= max(2, 0.10 * b)
+
+
+@pytest.mark.parametrize("solver,pc", SOLVES)
+@pytest.mark.parametrize("dims", [(20, 20, 10), (13, 7, 5)])
+def test_solve_tiny_matches_oracle(rsv, torch, solver, pc, dims):
+    p = synth.make_problem(*dims, seed=0 if dims == (20, 20, 10) else 37)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, solver=solver, restart=30, rtol=1e-8, maxit=4000)
+    s.setup(pc)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    ost, ox, oinfo = _oracle_solve(p, solver, pc, maxit=4000)
+    assert ost == 0 and st == rsv.RSV_OK, (st, info)
+    xh = x.cpu().numpy()
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, xh)) / np.linalg.norm(p.b)
+    assert relres <= 1e-8 and abs(relres - info["true_relres"]) <= 1e-12
+    assert _iters_close(info["iters"], oinfo["iters"]), (info, oinfo)
+
+
+def test_host_buffers_match_device_buffers(rsv, torch):
+    p = synth.make_problem(11, 9, 7, seed=38)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, solver="gmres")
+    s.setup("bilu0")
+    xh = np.zeros(p.n)
+    st, info = s.solve(p.b.copy(), xh)
+    b = torch.from_numpy(p.b).cuda()
+    xd = torch.zeros_like(b)
+    st2, info2 = s.solve(b, xd)
+    assert st == st2 == 0 and info["iters"] == info2["iters"]
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_maxit_reports_noconv_with_iterate(rsv, torch):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A = _mat(rsv, p)
+    for solver in ("gmres", "bicgstab"):
+        s = rsv.Solver(A, solver=solver, maxit=7)
+        s.setup("bjacobi")
+        x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        st, info = s.solve(torch.from_numpy(p.b).cuda(), x)
+        assert st == rsv.RSV_ENOCONV and info["status"] == rsv.RSV_ENOCONV
+        assert info["iters"] == 7 and 0 < info["true_relres"] < 1.0
+
+
+def test_zero_rhs_and_nonfinite_rhs(rsv, torch):
+    p = synth.make_problem(6, 5, 4, seed=39)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A)
+    s.setup("bilu0")
+    b = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == 0 and info["iters"] == 0 and float(x.abs().max()) == 0.0
+    b[5] = float("nan")
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_ENAN
+
+
+def test_singular_block_reported_at_setup(rsv, torch):
+    p = synth.make_problem(5, 4, 3, seed=40)
+    vals = p.vals.copy()
+    d = p.row_ptr[7] + [q for q in range(p.row_ptr[7], p.row_ptr[8]) if p.col_idx[q] == 7][0] - p.row_ptr[7]
+    vals[d] = np.array([[1.0, 2, 3], [2, 4, 6], [1, 1, 1]])  # rank 2
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(vals)
+    s = rsv.Solver(A)
+    with pytest.raises(rsv.RsvError) as e:
+        s.setup("bjacobi")
+    assert e.value.status == rsv.RSV_ESINGULAR
+
+
+def test_state_errors(rsv, torch):
+    p = synth.make_problem(4, 4, 4, seed=41)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, _ = s.solve(b, x)
+    assert st == rsv.RSV_EINVAL  # no preconditioner yet
+    s.setup("bilu0")
+    A.set_values(p.vals)  # new values invalidate the factor
+    st, _ = s.solve(b, x)
+    assert st == rsv.RSV_EINVAL
+    with pytest.raises(rsv.RsvError):
+        rsv.Solver(A, restart=0)
+
+
+def test_mid_gmres_bilu0_full_size(rsv, torch):
+    """100x100x50 (500k cells, 1.5M unknowns), layered permeability: the benchmark workload."""
+    gold = json.load(open(GOLDEN))["mid_100x100x50/gmres/bilu0"]
+    p = synth.workload("mid_100x100x50")
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=2000)
+    s.setup("bilu0")
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == 0, info
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
+    assert _iters_close(info["iters"], gold["iters"]), (info, gold)
+    # factor parity at full size on sampled cells
+    st_, lu, udinv, _ = oracle.bilu0_setup(p.row_ptr, p.col_idx, p.vals)
+    d = s.dinv()
+    idx = np.random.default_rng(42).choice(p.nb, 2000, replace=False)
+    assert np.all(np.abs(d[idx] - udinv[idx]) <= 1e-12 * np.abs(udinv[idx]).max(axis=(1, 2), keepdims=True))
