@@ -1,5 +1,18 @@
-"""Small dense helpers shared by the tests (brute-force references)."""
+"""Small dense helpers shared by the tests (brute-force references) and the library build hook."""
+import importlib.util
+import os
+
 import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def build_library():
+    """Build librsv.so (loads the build script by path: the package import needs the library)."""
+    spec = importlib.util.spec_from_file_location("rsv_build", os.path.join(ROOT, "paper_1602_05901_gb300", "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
 
 
 def bsr_to_dense(row_ptr, col_idx, vals):

@@ -17,8 +17,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1602_05901_gb300 import _build
-    path = _build.build()
+    from tests.helpers import build_library
+    path = build_library()
     return ctypes.CDLL(path), path
 
 
@@ -38,12 +38,12 @@ def test_every_declared_symbol_is_exported(lib):
     assert exported == set(declared_functions())
 
 
-def test_binding_covers_exports():
+def test_binding_covers_exports(lib):
     import paper_1602_05901_gb300 as rsv
     assert set(rsv.EXPORTS) == set(declared_functions())
 
 
-def test_host_side_argument_checks_without_gpu():
+def test_host_side_argument_checks_without_gpu(lib):
     import paper_1602_05901_gb300 as rsv
     g = ctypes.c_void_p()
     assert rsv.rsv_grid_create(0, 4, 4, ctypes.byref(g)) == rsv.RSV_EINVAL

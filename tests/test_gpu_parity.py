@@ -15,8 +15,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ora
 
 @pytest.fixture(scope="module")
 def rsv():
-    from paper_1602_05901_gb300 import _build
-    _build.build()
+    from tests.helpers import build_library
+    build_library()
     import paper_1602_05901_gb300 as m
     return m
 
