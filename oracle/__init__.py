@@ -29,10 +29,14 @@ PC = {"none": 0, "bjacobi": 1, "bilu0": 2, "cpr": 3}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, portable flags)."""
+    """Compile oracle.c into liboracle.so next to it.
+
+    -ffp-contract=off keeps every a*b+c as two rounded operations, so the oracle
+    rounds identically on x86-64 and AArch64 hosts.
+    """
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
