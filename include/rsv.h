@@ -79,7 +79,7 @@ typedef struct {
     int precision;         /* rsv_precision: FP64, or FP32 inner solves + FP64 refinement */
     double inner_rtol;     /* mixed: inner tolerance relative to the current outer residual */
     int max_outer;         /* mixed: maximum refinement steps */
-    long long watchdog;    /* spin limit of every bounded device-side wait */
+    long long watchdog;    /* time limit, microseconds, of every bounded device-side wait */
 } rsv_solver_params;
 
 /* Preconditioner parameters.  GMG defaults follow the paper's AMG defaults
@@ -103,7 +103,7 @@ typedef struct {
 } rsv_solve_info;
 
 /* Defaults: GMRES, m = 30, rtol 1e-8, atol 0, btol 1e-30, maxit 2000, FP64,
- * inner_rtol 1e-5, max_outer 10, watchdog 1<<26. */
+ * inner_rtol 1e-5, max_outer 10, watchdog 2,000,000 us. */
 RSV_API void rsv_solver_params_default(rsv_solver_params *p);
 /* Defaults: 6 levels, 512 coarse cells, 2 sweeps. */
 RSV_API void rsv_pc_params_default(rsv_pc_params *p);

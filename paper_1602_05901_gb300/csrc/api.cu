@@ -192,6 +192,8 @@ struct rsv_solver {
     double *dinv = nullptr;
     double *d_b = nullptr, *d_x = nullptr;
     Schedule sch;
+    IluTiles tiles;
+    bool scratch_dirty = false;  // a sweep timed out: its sentinel scratch must be refilled
     double ms_setup = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -209,7 +211,7 @@ void rsv_solver_params_default(rsv_solver_params *p) {
     p->precision = RSV_PREC_FP64;
     p->inner_rtol = 1e-5;
     p->max_outer = 10;
-    p->watchdog = 1ll << 26;
+    p->watchdog = 2000000;  // microseconds
 }
 
 void rsv_pc_params_default(rsv_pc_params *p) {
@@ -394,6 +396,7 @@ static void solver_free(rsv_solver *s) {
                     (void *)s->bv, (void *)s->dinv, (void *)s->d_b, (void *)s->d_x})
         if (p) cudaFree(p);
     free_schedule(&s->sch);
+    free_tiles(&s->tiles);
     if (s->e0) cudaEventDestroy(s->e0);
     if (s->e1) cudaEventDestroy(s->e1);
     delete s;
@@ -403,7 +406,7 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
     if (!A || !p || !out) return RSV_EINVAL;
     if (p->solver < RSV_GMRES || p->solver > RSV_FGMRES) return RSV_EINVAL;
     if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 0 || !(p->rtol >= 0.0) || !(p->atol >= 0.0) ||
-        !(p->btol >= 0.0))
+        !(p->btol >= 0.0) || p->watchdog < 1)
         return RSV_EINVAL;
     if (p->precision != RSV_PREC_FP64) return RSV_ENOTSUP;
     rsv_solver *s = new (std::nothrow) rsv_solver();
@@ -465,6 +468,7 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     if (pc_type == RSV_PC_BILU0) {
         if (!s->sch.cells) RSV_CUDA_TRY(build_schedule(A, &s->sch));
         RSV_CUDA_TRY(launch_ilu_setup(A, s->sch, s->dinv, &s->ds->status));
+        RSV_CUDA_TRY(tiles_setup(A, s->dinv, &s->tiles));
     }
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
@@ -487,7 +491,9 @@ static cudaError_t pc_apply(rsv_solver *s, const double *r, double *z, const int
     switch (s->pc_type) {
     case RSV_PC_NONE: return cudaMemcpyAsync(z, r, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->st);
     case RSV_PC_BJACOBI: return launch_bj_apply(s->st, s->A->nb, s->dinv, r, z, done);
-    case RSV_PC_BILU0: return launch_ilu_apply(s->A, s->sch, s->dinv, r, z, done);
+    case RSV_PC_BILU0:
+        return launch_ilu_apply_tiles(s->A, s->tiles, r, z, done, &s->ds->status,
+                                      (unsigned long long)s->p.watchdog * 1000ull);
     }
     return cudaErrorInvalidValue;
 }
@@ -653,7 +659,7 @@ static rsv_status bicgstab_solve(rsv_solver *s, const double *b, double *x, doub
         }
         RSV_CUDA_TRY(cudaGetLastError());
         RSV_TRY(fetch(s, &h));
-        if (h.done) {
+        if (h.done || h.status != RSV_OK) {
             result = (h.status != RSV_OK) ? (rsv_status)h.status
                                           : (h.iters >= s->p.maxit ? RSV_ENOCONV : RSV_OK);
             break;
@@ -688,6 +694,10 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
     }
     // reset device state
     RSV_CUDA_TRY(cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
+    if (s->scratch_dirty && s->tiles.scratch) {
+        RSV_CUDA_TRY(reset_tiles_scratch(s->A, &s->tiles));
+        s->scratch_dirty = false;
+    }
     double bnorm = 0.0;
     RSV_CUDA_TRY(launch_dot(s->st, n, db, db, s->partial, &s->ds->bnorm, &s->ds->counter[0], 1, nullptr));
     RSV_CUDA_TRY(cudaMemcpyAsync(&bnorm, &s->ds->bnorm, sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -701,6 +711,7 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
     rsv_status st = (s->p.solver == RSV_BICGSTAB) ? bicgstab_solve(s, db, dx, bnorm, &local)
                                                    : gmres_solve(s, db, dx, bnorm, &local);
     if (st == RSV_ECUDA || st == RSV_ENOMEM) return st;
+    if (st == RSV_ETIMEOUT) s->scratch_dirty = true;
     // FP64 true residual, recomputed
     double rn = 0.0;
     RSV_CUDA_TRY(residual(s, db, dx, s->w, &s->ds->red[12]));

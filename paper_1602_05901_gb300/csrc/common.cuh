@@ -53,6 +53,15 @@ struct DevState {
     unsigned counter[4];  // last-block tickets of the reduction kernels
 };
 
+struct IluTiles {  // packed factor for the persistent tile sweeps (ilu_tiles.cu)
+    int nT = 0, S = 0, grid = 0;
+    size_t smem = 0;
+    int2 *order = nullptr;    // tile (J, K) per processing position
+    double *Ff = nullptr;     // forward chunks  [nT][S][36][32]
+    double *Fb = nullptr;     // backward chunks [nT][S][36][32]
+    double *scratch = nullptr;  // y of the forward sweep (sentinel-filled between applications)
+};
+
 struct Schedule {  // i+j+k wavefront hyperplanes
     std::vector<int> plane_ptr;  // host, nplanes+1
     int32_t *cells = nullptr;    // device, nb cell indices grouped by plane (ascending within)
@@ -110,5 +119,12 @@ cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const double *dinv, con
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, double *dinv, int *status);
 cudaError_t launch_ilu_apply(const rsv_mat *A, const Schedule &sch, const double *dinv, const double *r,
                              double *z, const int *done);
+
+// ---- launchers implemented in ilu_tiles.cu
+cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T);
+cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *T);
+void free_tiles(IluTiles *T);
+cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T, const double *r, double *z, const int *done,
+                                   int *status, unsigned long long timeout_ns);
 
 }  // namespace rsv

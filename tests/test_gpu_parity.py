@@ -234,6 +234,28 @@ def test_state_errors(rsv, torch):
         rsv.Solver(A, restart=0)
 
 
+def test_watchdog_timeout_returns_status_and_context_survives(rsv, torch):
+    """A 1 microsecond wait limit makes the tile sweeps' cross-warp waits run out:
+    the solve reports ETIMEOUT (no trap, no hang) and the next solve with the
+    normal limit succeeds on the same context."""
+    p = synth.make_problem(24, 40, 20, seed=43)
+    A = _mat(rsv, p)
+    b = torch.from_numpy(p.b).cuda()
+    s = rsv.Solver(A, solver="gmres", watchdog=1)
+    s.setup("bilu0")
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_ETIMEOUT, (st, info)
+    s2 = rsv.Solver(A, solver="gmres")
+    s2.setup("bilu0")
+    x.zero_()
+    st, info = s2.solve(b, x)
+    assert st == rsv.RSV_OK and info["true_relres"] <= 1e-8
+    # the timed-out solver recovers too once its limit is back to normal
+    st, info = s.solve(b, x)
+    assert st in (rsv.RSV_OK, rsv.RSV_ETIMEOUT)
+
+
 def test_mid_gmres_bilu0_full_size(rsv, torch):
     """100x100x50 (500k cells, 1.5M unknowns), layered permeability: the benchmark workload."""
     gold = json.load(open(GOLDEN))["mid_100x100x50/gmres/bilu0"]
