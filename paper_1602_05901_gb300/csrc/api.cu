@@ -47,12 +47,12 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
     const double a = H[j * m + j], b = H[(j + 1) * m + j];
     const double rho = hypot(a, b);
     if (!isfinite(rho) || !isfinite(ds->hn)) {
-        ds->status = RSV_ENAN;
+        if (ds->status == 0) ds->status = RSV_ENAN;
         ds->done = 1;
         return;
     }
     if (!(rho > 0.0)) {
-        ds->status = RSV_EBREAKDOWN;
+        if (ds->status == 0) ds->status = RSV_EBREAKDOWN;
         ds->done = 1;
         return;
     }
@@ -81,8 +81,8 @@ __global__ void gmres_backsolve(DevState *ds, int m) {
 __global__ void bicg_beta(DevState *ds, double btol) {
     if (ds->done) return;
     const double rho1 = ds->red[0];
-    if (!isfinite(rho1)) { ds->status = RSV_ENAN; ds->done = 1; return; }
-    if (fabs(rho1) <= btol * ds->red[8] * ds->red[9]) { ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
+    if (!isfinite(rho1)) { if (ds->status == 0) ds->status = RSV_ENAN; ds->done = 1; return; }
+    if (fabs(rho1) <= btol * ds->red[8] * ds->red[9]) { if (ds->status == 0) ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
     ds->rho1 = rho1;
     ds->red[10] = (rho1 / ds->rho) * (ds->alpha / ds->omega);  // beta
 }
@@ -90,8 +90,8 @@ __global__ void bicg_beta(DevState *ds, double btol) {
 __global__ void bicg_alpha(DevState *ds, double btol) {
     if (ds->done) return;
     const double rv = ds->red[1];
-    if (!isfinite(rv)) { ds->status = RSV_ENAN; ds->done = 1; return; }
-    if (fabs(rv) <= btol * ds->red[8] * ds->red[2]) { ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
+    if (!isfinite(rv)) { if (ds->status == 0) ds->status = RSV_ENAN; ds->done = 1; return; }
+    if (fabs(rv) <= btol * ds->red[8] * ds->red[2]) { if (ds->status == 0) ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
     ds->alpha = ds->rho1 / rv;
 }
 
@@ -99,7 +99,7 @@ __global__ void bicg_check_s(DevState *ds) {
     if (ds->done) return;
     ds->iters += 1;
     const double sn = ds->red[3];
-    if (!isfinite(sn)) { ds->status = RSV_ENAN; ds->done = 1; return; }
+    if (!isfinite(sn)) { if (ds->status == 0) ds->status = RSV_ENAN; ds->done = 1; return; }
     if (sn <= ds->tol) {
         ds->red[11] = 1.0;  // x += alpha ph pending
         ds->done = 1;
@@ -109,9 +109,9 @@ __global__ void bicg_check_s(DevState *ds) {
 __global__ void bicg_omega(DevState *ds, double btol) {
     if (ds->done) return;
     const double ts = ds->red[4], tt = ds->red[5];
-    if (!(tt > 0.0) || !isfinite(tt)) { ds->status = isfinite(tt) ? RSV_EBREAKDOWN : RSV_ENAN; ds->done = 1; return; }
+    if (!(tt > 0.0) || !isfinite(tt)) { if (ds->status == 0) ds->status = isfinite(tt) ? RSV_EBREAKDOWN : RSV_ENAN; ds->done = 1; return; }
     const double om = ts / tt;
-    if (fabs(om) <= btol) { ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
+    if (fabs(om) <= btol) { if (ds->status == 0) ds->status = RSV_EBREAKDOWN; ds->done = 1; return; }
     ds->omega = om;
 }
 
@@ -119,7 +119,7 @@ __global__ void bicg_finish_iter(DevState *ds) {
     if (ds->done) return;
     ds->rho = ds->rho1;
     const double rn = ds->red[9];
-    if (!isfinite(rn)) { ds->status = RSV_ENAN; ds->done = 1; return; }
+    if (!isfinite(rn)) { if (ds->status == 0) ds->status = RSV_ENAN; ds->done = 1; return; }
     if (rn <= ds->tol || ds->iters >= ds->maxit) ds->done = 1;
 }
 

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
         }
     }
     if (failed) {
-        if (lane == 0) atomicMax(P.status, (int)RSV_ETIMEOUT);
+        if (lane == 0) atomicCAS(P.status, 0, (int)RSV_ETIMEOUT);
         // let copies still in flight land before the CTA exits (bounded)
         if (lane == 0) {
             const uint64_t limit = global_timer() + 1000000000ull;

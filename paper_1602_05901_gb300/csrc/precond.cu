@@ -89,7 +89,7 @@ __global__ void bj_setup_kernel(int64_t nb, Dims g, const int32_t *__restrict__ 
     const RowSlots s = row_slots((int)c, g);
     double a[9];
     load9(v + 9 * (int64_t)(rp[c] + s.d), a);
-    if (!inv3(a, dinv + 9 * c)) atomicMax(status, (int)RSV_ESINGULAR);
+    if (!inv3(a, dinv + 9 * c)) atomicCAS(status, 0, (int)RSV_ESINGULAR);
 }
 
 __global__ void bj_apply_kernel(int64_t nb, const double *__restrict__ dinv, const double *__restrict__ r,
@@ -135,7 +135,7 @@ __global__ void ilu_factor_plane(Dims g, const int32_t *__restrict__ rp, const d
 #pragma unroll
         for (int e = 0; e < 9; ++e) D[e] -= U[e];
     }
-    if (!inv3(D, dinv + 9 * (int64_t)c)) atomicMax(status, (int)RSV_ESINGULAR);
+    if (!inv3(D, dinv + 9 * (int64_t)c)) atomicCAS(status, 0, (int)RSV_ESINGULAR);
 }
 
 __global__ void ilu_fwd_plane(Dims g, const int32_t *__restrict__ rp, const double *__restrict__ v,
