@@ -2,10 +2,13 @@
 """Benchmark: time to solve A x = b to rtol 1e-8 on one GB300, plus BSR SpMV HBM GB/s.
 
 Workload: the 100x100x50 grid (500,000 cells, 1.5M unknowns) with layered
-permeability (seed 1), solved by GMRES(30) + block ILU(0) in wavefront order.
-One step = preconditioner setup + solve from x0 = 0 with the matrix and right-
-hand side already resident in HBM.  The matrix (249 MB of FP64 blocks) is
-larger than the 129 MB L2, so no flush is needed between steps.
+permeability (seed 1), solved by GMRES(30) + block ILU(0) in wavefront order
+to a true FP64 relative residual of 1e-8.  One step = preconditioner setup +
+solve from x0 = 0 with the matrix and right-hand side already resident in
+HBM, in the mixed-precision form (FP32 inner solves under FP64 iterative
+refinement); the plain FP64 solve of the same system is timed the same way
+and reported beside it.  The matrix (249 MB of FP64 blocks) is larger than
+the 129 MB L2, so no flush is needed between steps.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
 instead, on a bounded sample of the same workload scaled to the full solve.
@@ -47,6 +50,19 @@ def hbm_peak():
 def spmv_bytes(nb, nnzb, val_bytes=8):
     """Algorithmic bytes of one SpMV: blocks + column indices + row pointers + x + y."""
     return nnzb * (9 * val_bytes + 4) + (nb + 1) * 4 + 2 * nb * 3 * val_bytes
+
+
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA cores) from the pool's nominal table
+
+
+def ilu_apply_flops(nb, nnzb):
+    """FP64/FP32 flops of one block ILU(0) apply: a 3x3 block-vector product (9 FMA) per
+    off-diagonal block and two D^{-1} products per cell."""
+    return 2 * 9 * ((nnzb - nb) + 2 * nb)
+
+
+def spmv_flops(nnzb):
+    return 2 * 9 * nnzb
 
 
 def ilu_apply_bytes(nb, nnzb, val_bytes=8):
@@ -194,74 +210,79 @@ def main():
     A.set_values(vals_d)
     b = torch.from_numpy(p.b).to(dev)
     x = torch.zeros_like(b)
-    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=2000)
+    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision="mixed")
+    s64 = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision="fp64")
 
-    def step():
-        s.setup("bilu0")
+    def step(solver):
+        solver.setup("bilu0")
         x.zero_()
-        st, info = s.solve(b, x)
+        st, info = solver.solve(b, x)
         if st != rsv.RSV_OK:
             raise RuntimeError(f"solve failed: {rsv.status_string(st)} {info}")
         return info
 
+    def timed(solver, steps):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = rsv.rsv_kernel_launches()
+        e0.record(stream)
+        infos = [step(solver) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_ = e0.elapsed_time(e1) / steps
+        if dist is not None:
+            t = torch.tensor([ms_], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_ = float(t.item())
+            dist.barrier()
+        return ms_, infos[-1], rsv.rsv_kernel_launches() - l0
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
-        info = step()
+        step(s)
+        step(s64)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(local)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    l0 = rsv.rsv_kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    infos = []
-    for _ in range(args.steps):
-        infos.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    launches = rsv.rsv_kernel_launches() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms, info, launches = timed(s, args.steps)
+    ms64, info64, _ = timed(s64, max(1, args.steps))
     clocks = sampler.stop()
-    info = infos[-1]
 
     # ---- kernel microbenchmarks on the same stream (CUDA events)
     peak, peak_src = hbm_peak()
+
+    def event_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
     xs = torch.randn(p.n, dtype=torch.float64, device=dev)
     ys = torch.empty_like(xs)
-    for _ in range(5):
-        A.spmv(xs, ys)
-    reps = 50
-    e0.record(stream)
-    for _ in range(reps):
-        A.spmv(xs, ys)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    spmv_ms = e0.elapsed_time(e1) / reps
-    sb = spmv_bytes(p.nb, p.nnzb)
-    spmv_gbs = sb / (spmv_ms * 1e-3) / 1e9
+    xs32, ys32 = xs.float(), torch.empty(p.n, dtype=torch.float32, device=dev)
+    spmv_ms = event_ms(lambda: A.spmv(xs, ys), 50)
+    spmv32_ms = event_ms(lambda: A.spmv(xs32, ys32), 50)
+    sb, sb32 = spmv_bytes(p.nb, p.nnzb), spmv_bytes(p.nb, p.nnzb, 4)
+    spmv_gbs, spmv32_gbs = sb / (spmv_ms * 1e-3) / 1e9, sb32 / (spmv32_ms * 1e-3) / 1e9
+    s.setup("bilu0")
+    s64.setup("bilu0")
+    zs32 = torch.empty_like(xs32)
+    ilu32_ms = event_ms(lambda: s.apply(xs32, zs32), 20)
     zs = torch.empty_like(xs)
-    for _ in range(2):
-        s.apply(xs, zs)
-    reps_i = 10
-    e0.record(stream)
-    for _ in range(reps_i):
-        s.apply(xs, zs)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ilu_ms = e0.elapsed_time(e1) / reps_i
-    ib = ilu_apply_bytes(p.nb, p.nnzb)
-    ilu_gbs = ib / (ilu_ms * 1e-3) / 1e9
-    # dominant kernel per Krylov iteration: one ILU apply vs one SpMV
-    if ilu_ms >= spmv_ms:
-        dom = {"kernel": "block ILU(0) apply (forward+backward wavefront sweeps)", "ms": ilu_ms, "bytes": ib,
-               "gbs": ilu_gbs}
+    ilu_ms = event_ms(lambda: s64.apply(xs, zs), 10)
+    ib32 = ilu_apply_bytes(p.nb, p.nnzb, 4)
+    ilu32_gbs = ib32 / (ilu32_ms * 1e-3) / 1e9
+    ilu_gflops = ilu_apply_flops(p.nb, p.nnzb) / (ilu_ms * 1e-3) / 1e9
+    # dominant kernel of the timed (mixed) path per inner iteration: FP32 ILU apply vs FP32 SpMV
+    if ilu32_ms >= spmv32_ms:
+        dom = {"kernel": "block ILU(0) apply, FP32 (forward+backward tile sweeps)", "ms": ilu32_ms, "bytes": ib32,
+               "gbs": ilu32_gbs}
     else:
-        dom = {"kernel": "BSR SpMV", "ms": spmv_ms, "bytes": sb, "gbs": spmv_gbs}
+        dom = {"kernel": "BSR SpMV FP32", "ms": spmv32_ms, "bytes": sb32, "gbs": spmv32_gbs}
     roofline = {"bound": "hbm", "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom["gbs"] / peak, 4), "traffic": None, "kernel": dom["kernel"],
                 "algorithmic_bytes_per_launch": dom["bytes"], "avg_launch_ms": round(dom["ms"], 4),
@@ -279,7 +300,7 @@ def main():
         s.setup("bilu0")
         x_h.zero_()
         st, einfo = s.solve(b_h.numpy(), x_h.numpy())
-        assert st == rsv.RSV_OK
+        assert st == rsv.RSV_OK, rsv.status_string(st)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
@@ -289,21 +310,29 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, info["iters"], args.cpu_sample_iters)
+        cpu = cpu_baseline(p, info64["iters"], args.cpu_sample_iters)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [p.nx, p.ny, p.nz], "cells": p.nb, "unknowns": p.n,
-                       "nnzb": p.nnzb, "solver": "gmres(30)", "pc": "bilu0 (i+j+k wavefront)", "precision": "fp64",
+                       "nnzb": p.nnzb, "solver": "gmres(30)", "pc": "bilu0 (i+j+k wavefront tiles)",
+                       "precision": "mixed: FP32 inner (inner rtol 1e-5) + FP64 refinement",
                        "rtol": 1e-8, "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (FP64 blocks 249 MB > 129 MB), no flush"},
-            "iters": info["iters"], "true_relres": info["true_relres"], "ms_setup": round(info["ms_setup"], 3),
-            "ms_solve": round(info["ms_solve"], 3),
+            "iters": info["iters"], "outer_iters": info["outer_iters"], "true_relres": info["true_relres"],
+            "ms_setup": round(info["ms_setup"], 3), "ms_solve": round(info["ms_solve"], 3),
+            "fp64": {"ms_per_step": round(ms64, 3), "iters": info64["iters"], "true_relres": info64["true_relres"],
+                     "speedup_mixed_over_fp64": round(ms64 / ms, 3),
+                     "ilu_apply_ms": round(ilu_ms, 4), "ilu_apply_gflops": round(ilu_gflops, 1),
+                     "ilu_frac_of_fp64_peak": round(ilu_gflops / (FP64_PEAK_TFLOPS * 1e3), 4)},
             "spmv": {"gbs": round(spmv_gbs, 1), "frac_of_peak": round(spmv_gbs / peak, 4), "avg_launch_ms":
-                     round(spmv_ms, 4), "algorithmic_bytes": sb},
+                     round(spmv_ms, 4), "algorithmic_bytes": sb,
+                     "gflops_fp64": round(spmv_flops(p.nnzb) / (spmv_ms * 1e-3) / 1e9, 1),
+                     "fp32_gbs": round(spmv32_gbs, 1), "fp32_frac_of_peak": round(spmv32_gbs / peak, 4),
+                     "fp32_avg_launch_ms": round(spmv32_ms, 4)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "wall_ms": round(wall_e2e_ms, 3),

@@ -164,8 +164,13 @@ RSV_API void rsv_solver_destroy(rsv_solver *s);
  *         matrix (Section "Algebraic Multigrid Methods"), then block ILU(0).
  * params may be NULL (defaults). */
 RSV_API rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params);
-/* z = M^{-1} r with the current preconditioner; device float64[3*nb]. */
+/* z = M^{-1} r with the current preconditioner of an FP64 solver; device
+ * float64[3*nb]; r and z must not overlap.  Returns before the GPU work ends
+ * (stream-ordered); a device-side failure surfaces at the next rsv_solve. */
 RSV_API rsv_status rsv_precond_apply(rsv_solver *s, const double *r, double *z);
+/* Same in FP32 for a mixed-precision solver (its preconditioner is built on
+ * the FP32-rounded matrix and stores FP32 factors); device float32[3*nb]. */
+RSV_API rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z);
 /* Copy the inverted diagonal blocks of the preconditioner (block Jacobi:
  * A_ii^{-1}; block ILU(0): U_ii^{-1}) to host float64[nb][3][3]. */
 RSV_API rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host);

@@ -78,6 +78,7 @@ _SIGS = {
     "rsv_solver_destroy": (None, [_P]),
     "rsv_precond_setup": (_I, [_P, _I, ctypes.POINTER(rsv_pc_params)]),
     "rsv_precond_apply": (_I, [_P, _P, _P]),
+    "rsv_precond_apply_f32": (_I, [_P, _P, _P]),
     "rsv_precond_get_dinv": (_I, [_P, _P]),
     "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
 }
@@ -208,7 +209,10 @@ class Solver:
         check(st, "rsv_precond_setup")
 
     def apply(self, r, z):
-        check(_lib.rsv_precond_apply(self.handle, _ptr(r), _ptr(z)), "rsv_precond_apply")
+        if r.dtype.itemsize == 4:
+            check(_lib.rsv_precond_apply_f32(self.handle, _ptr(r), _ptr(z)), "rsv_precond_apply_f32")
+        else:
+            check(_lib.rsv_precond_apply(self.handle, _ptr(r), _ptr(z)), "rsv_precond_apply")
         return z
 
     def dinv(self):

@@ -30,6 +30,7 @@ constexpr int kRedBlocks = 304;   // 2 x 152 SMs: grid of every reduction kernel
 constexpr int kRedThreads = 256;
 
 void set_last_cuda_error(cudaError_t e);
+rsv_status cuda_status(cudaError_t e);
 // Process-wide count of kernel launches issued by the library.
 void count_launches(uint64_t n);
 
@@ -54,12 +55,12 @@ struct DevState {
 };
 
 struct IluTiles {  // packed factor for the persistent tile sweeps (ilu_tiles.cu)
-    int nT = 0, S = 0, grid = 0;
+    int nT = 0, S = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
     size_t smem = 0;
     int2 *order = nullptr;    // tile (J, K) per processing position
-    double *Ff = nullptr;     // forward chunks  [nT][S][36][32]
-    double *Fb = nullptr;     // backward chunks [nT][S][36][32]
-    double *scratch = nullptr;  // y of the forward sweep (sentinel-filled between applications)
+    void *Ff = nullptr;       // forward chunks  [nT][S][36][32]
+    void *Fb = nullptr;       // backward chunks [nT][S][36][32]
+    void *scratch = nullptr;  // y of the forward sweep (sentinel-filled between applications)
 };
 
 struct Schedule {  // i+j+k wavefront hyperplanes
@@ -94,37 +95,44 @@ cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float
                             const int *done);
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b);
 
-// ---- launchers implemented in blas.cu
+// ---- launchers implemented in blas.cu (T = double or float; reductions in FP64)
 // out[i] = <w, V_i> for i < k; V_i = V + i*ldv.  Deterministic two-level reduction.
-cudaError_t launch_mdot(cudaStream_t st, int64_t n, const double *w, const double *V, int64_t ldv, int k,
-                        double *partial, double *out, unsigned *counter, const int *done);
-// out = base + sgn * sum_i c[i] V_i; if nrm != nullptr, *nrm = ||out||_2.
-cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const double *base, const double *V, int64_t ldv,
-                         int k, const double *c, double sgn, double *out, double *partial, double *nrm,
-                         unsigned *counter, const int *done);
+template <typename T>
+cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int64_t ldv, int k, double *partial,
+                        double *out, unsigned *counter, const int *done);
+// out = base + sgn * sum_i c[i] V_i (base may be null); if nrm != nullptr, *nrm = ||out||_2.
+template <typename T>
+cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
+                         double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done);
 // *out = ||x||_2 (sqrt_out=1) or <x,y>
-cudaError_t launch_dot(cudaStream_t st, int64_t n, const double *x, const double *y, double *partial,
-                       double *out, unsigned *counter, int sqrt_out, const int *done);
-cudaError_t launch_axpby(cudaStream_t st, int64_t n, double a, const double *x, double b, const double *y,
-                         double *z);
+template <typename T>
+cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,
+                       unsigned *counter, int sqrt_out, const int *done);
+template <typename T>
+cudaError_t launch_axpby(cudaStream_t st, int64_t n, T a, const T *x, T b, const T *y, T *z);
 // x *= 1/(*s) (device scalar), skipping when *done
-cudaError_t launch_scale_inv(cudaStream_t st, int64_t n, double *x, const double *s, const int *done);
+template <typename T>
+cudaError_t launch_scale_inv(cudaStream_t st, int64_t n, T *x, const double *s, const int *done);
+// xf = (float)(x / *s);  x += (*s) * df
+cudaError_t launch_to_f32_scaled(cudaStream_t st, int64_t n, const double *x, const double *s, float *xf);
+cudaError_t launch_add_f32_scaled(cudaStream_t st, int64_t n, const float *df, const double *s, double *x);
 
 // ---- launchers implemented in precond.cu
 cudaError_t build_schedule(const rsv_mat *A, Schedule *sch);
 void free_schedule(Schedule *sch);
-cudaError_t launch_bj_setup(const rsv_mat *A, double *dinv, int *status);
-cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const double *dinv, const double *r, double *z,
-                            const int *done);
-cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, double *dinv, int *status);
-cudaError_t launch_ilu_apply(const rsv_mat *A, const Schedule &sch, const double *dinv, const double *r,
-                             double *z, const int *done);
+// from_f32: factor the FP32-rounded values (mixed precision) instead of the FP64 ones.
+cudaError_t launch_bj_setup(const rsv_mat *A, bool from_f32, double *dinv, float *dinv32, int *status);
+template <typename T>
+cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const T *dinv, const T *r, T *z, const int *done);
+cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status);
 
 // ---- launchers implemented in ilu_tiles.cu
-cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T);
-cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *T);
-void free_tiles(IluTiles *T);
-cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T, const double *r, double *z, const int *done,
+template <typename T>
+cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_);
+cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *T_);
+void free_tiles(IluTiles *T_);
+template <typename T>
+cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T_, const T *r, T *z, const int *done,
                                    int *status, unsigned long long timeout_ns);
 
 }  // namespace rsv

@@ -39,9 +39,18 @@ namespace {
 constexpr int TJ = 8, TK = 4;
 constexpr int NQ = 36;               // 27 off-diagonal block entries + 9 of D^{-1}
 constexpr int NS = 4;                // shared-memory ring stages = prefetch distance
-constexpr int CHUNK = NQ * 32;       // doubles per warp step
-constexpr unsigned CHUNK_BYTES = CHUNK * 8;
-constexpr unsigned long long SENT = 0xFFF4C0DE5A17E7A1ull;  // signalling NaN
+constexpr int CHUNK = NQ * 32;       // values per warp step
+
+// Signalling NaNs: no arithmetic result has these bit patterns.
+template <typename T> struct Bits;
+template <> struct Bits<double> {
+    using U = unsigned long long;
+    static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;
+};
+template <> struct Bits<float> {
+    using U = unsigned int;
+    static constexpr U SENT = 0x7FA5C0DEu;
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -83,32 +92,41 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const double *p) {
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-
-__device__ __forceinline__ void st_relaxed(double *p, double v) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+__device__ __forceinline__ unsigned ld_relaxed(const float *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
-
-__device__ __forceinline__ void st_sentinel(double *p) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(SENT) : "memory");
+__device__ __forceinline__ void st_relaxed_bits(double *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed_bits(float *p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long to_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned to_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ double from_bits(unsigned long long v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ float from_bits(unsigned v) { return __uint_as_float(v); }
 
+template <typename T>
 struct SweepArgs {
     int nx, ny, nz, nT, S;
     const int2 *order;         // tile (J, K) per position
-    const double *F;           // packed factor chunks [nT][S][36][32]
-    const double *in;          // forward: r; backward: y
-    double *out;               // forward: y; backward: z
-    double *reset;             // forward: z (gets the sentinel); backward: y (gets the sentinel)
+    const T *F;                // packed factor chunks [nT][S][36][32]
+    const T *in;               // forward: r; backward: y
+    T *out;                    // forward: y; backward: z
+    T *reset;                  // forward: z (gets the sentinel); backward: y (gets the sentinel)
     const int *done;
     int *status;
     unsigned long long timeout_ns;
 };
 
 // Wait until the three components at p are published (not the sentinel).
-__device__ __forceinline__ bool poll3(const double *p, unsigned long long v[3], uint64_t deadline) {
+template <typename T>
+__device__ __forceinline__ bool poll3(const T *p, typename Bits<T>::U v[3], uint64_t deadline) {
     for (int e = 0; e < 3; ++e) {
         unsigned spins = 0;
-        while (v[e] == SENT) {
+        while (v[e] == Bits<T>::SENT) {
             v[e] = ld_relaxed(p + e);
             if ((++spins & 255u) == 0 && global_timer() > deadline) return false;
         }
@@ -116,11 +134,13 @@ __device__ __forceinline__ bool poll3(const double *p, unsigned long long v[3], 
     return true;
 }
 
-template <bool FWD>
-__global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
+    using U = typename Bits<T>::U;
+    constexpr unsigned CHUNK_BYTES = CHUNK * sizeof(T);
     if (P.done && *(volatile const int *)P.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    double *ring = reinterpret_cast<double *>(smem);
+    T *ring = reinterpret_cast<T *>(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * CHUNK_BYTES);
     const int lane = threadIdx.x;
     const int a = lane & 7, b = lane >> 3;
@@ -142,7 +162,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
         const int2 JK = P.order[tt];
         const int j = JK.x * TJ + a, k = JK.y * TK + b;
         const bool jk_ok = (j < ny) && (k < nz);
-        const double *Ft = P.F + (size_t)tt * P.S * CHUNK;
+        const T *Ft = P.F + (size_t)tt * P.S * CHUNK;
         const int S = P.S;
         // direction-dependent geometry
         const int aoff = FWD ? a : (TJ - 1 - a);
@@ -171,20 +191,20 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
                 pending |= 1u << q;
             }
         }
-        double vin[NS][3];
-        unsigned long long rj[NS][3], rk[NS][3];
+        T vin[NS][3];
+        U rj[NS][3], rk[NS][3];
 #pragma unroll
         for (int u = 0; u < NS; ++u) {
             const bool v = u < S && cell_valid(u);
             const int64_t c = v ? cell_of(u) : 0;
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                vin[u][e] = v ? P.in[3 * c + e] : 0.0;
-                rj[u][e] = (v && edge_j && has_j) ? ld_relaxed(P.out + 3 * (c + dj) + e) : 0ull;
-                rk[u][e] = (v && edge_k && has_k) ? ld_relaxed(P.out + 3 * (c + dk) + e) : 0ull;
+                vin[u][e] = v ? P.in[3 * c + e] : T(0);
+                rj[u][e] = (v && edge_j && has_j) ? ld_relaxed(P.out + 3 * (c + dj) + e) : U(0);
+                rk[u][e] = (v && edge_k && has_k) ? ld_relaxed(P.out + 3 * (c + dk) + e) : U(0);
             }
         }
-        double prev[3] = {0.0, 0.0, 0.0};
+        T prev[3] = {T(0), T(0), T(0)};
 
         for (int s0 = 0; s0 < S; s0 += NS) {
 #pragma unroll
@@ -201,23 +221,23 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
                 const bool valid = cell_valid(s);
                 const int64_t c = valid ? cell_of(s) : 0;
                 // neighbours: shuffles of the previous step's results
-                double nj[3], nk[3];
+                T nj[3], nk[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    const double sjv = __shfl_sync(0xffffffffu, prev[e], lane_j & 31);
-                    const double skv = __shfl_sync(0xffffffffu, prev[e], lane_k & 31);
-                    nj[e] = has_j ? sjv : 0.0;
-                    nk[e] = has_k ? skv : 0.0;
+                    const T sjv = __shfl_sync(0xffffffffu, prev[e], lane_j & 31);
+                    const T skv = __shfl_sync(0xffffffffu, prev[e], lane_k & 31);
+                    nj[e] = has_j ? sjv : T(0);
+                    nk[e] = has_k ? skv : T(0);
                 }
                 if (valid && edge_j && has_j) {
                     if (!poll3(P.out + 3 * (c + dj), rj[u], deadline)) failed = true;
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) nj[e] = __longlong_as_double(rj[u][e]);
+                    for (int e = 0; e < 3; ++e) nj[e] = from_bits(rj[u][e]);
                 }
                 if (valid && edge_k && has_k) {
                     if (!poll3(P.out + 3 * (c + dk), rk[u], deadline)) failed = true;
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) nk[e] = __longlong_as_double(rk[u][e]);
+                    for (int e = 0; e < 3; ++e) nk[e] = from_bits(rk[u][e]);
                 }
                 // factor chunk of this step
                 {
@@ -235,18 +255,18 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
                         pending &= ~(1u << u);
                     }
                 }
-                const double *Fs = ring + u * CHUNK + lane;
+                const T *Fs = ring + u * CHUNK + lane;
                 const bool has_i = FWD ? (cell_i(s) > 0) : (cell_i(s) < nx - 1);
-                double own[3];
+                T own[3];
 #pragma unroll
-                for (int e = 0; e < 3; ++e) own[e] = has_i ? prev[e] : 0.0;
+                for (int e = 0; e < 3; ++e) own[e] = has_i ? prev[e] : T(0);
                 // slots: FWD  [0] -z  [1] -y  [2] -x ;  BWD  [0] +x  [1] +y  [2] +z
-                const double *xs0 = FWD ? nk : own;
-                const double *xs2 = FWD ? own : nk;
-                double acc[3];
+                const T *xs0 = FWD ? nk : own;
+                const T *xs2 = FWD ? own : nk;
+                T acc[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    double sum = 0.0;
+                    T sum = T(0);
 #pragma unroll
                     for (int f = 0; f < 3; ++f) {
                         sum = fma(Fs[(0 * 9 + 3 * e + f) * 32], xs0[f], sum);
@@ -255,22 +275,22 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
                     }
                     acc[e] = FWD ? (vin[u][e] - sum) : sum;
                 }
-                double res[3];
+                T res[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    const double d = Fs[(27 + 3 * e) * 32] * acc[0] + Fs[(28 + 3 * e) * 32] * acc[1] +
-                                     Fs[(29 + 3 * e) * 32] * acc[2];
+                    const T d = Fs[(27 + 3 * e) * 32] * acc[0] + Fs[(28 + 3 * e) * 32] * acc[1] +
+                                Fs[(29 + 3 * e) * 32] * acc[2];
                     res[e] = FWD ? d : (vin[u][e] - d);
                 }
                 if (valid) {
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        st_relaxed(P.out + 3 * c + e, res[e]);
-                        st_sentinel(P.reset + 3 * c + e);
+                        st_relaxed_bits(P.out + 3 * c + e, to_bits(res[e]));
+                        st_relaxed_bits(P.reset + 3 * c + e, Bits<T>::SENT);
                     }
                 }
 #pragma unroll
-                for (int e = 0; e < 3; ++e) prev[e] = valid ? res[e] : 0.0;
+                for (int e = 0; e < 3; ++e) prev[e] = valid ? res[e] : T(0);
                 // prefetch the vectors of step s + NS into this slot
                 {
                     const int sn = s + NS;
@@ -278,9 +298,9 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
                     const int64_t cn = vn ? cell_of(sn) : 0;
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        vin[u][e] = vn ? P.in[3 * cn + e] : 0.0;
-                        rj[u][e] = (vn && edge_j && has_j) ? ld_relaxed(P.out + 3 * (cn + dj) + e) : 0ull;
-                        rk[u][e] = (vn && edge_k && has_k) ? ld_relaxed(P.out + 3 * (cn + dk) + e) : 0ull;
+                        vin[u][e] = vn ? P.in[3 * cn + e] : T(0);
+                        rj[u][e] = (vn && edge_j && has_j) ? ld_relaxed(P.out + 3 * (cn + dj) + e) : U(0);
+                        rk[u][e] = (vn && edge_k && has_k) ? ld_relaxed(P.out + 3 * (cn + dk) + e) : U(0);
                     }
                 }
                 __syncwarp();
@@ -306,9 +326,12 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs P) {
 }
 
 // Pack the factor into warp-step chunks.  One thread per (tile, step, lane).
+// Block values come from `v` (FP64, or the FP32 copy for mixed precision);
+// D^{-1} from the FP64 factor; both are stored as T.
+template <typename T, typename Tv>
 __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__restrict__ order,
-                           const int32_t *__restrict__ rp, const double *__restrict__ v,
-                           const double *__restrict__ dinv, double *__restrict__ Ff, double *__restrict__ Fb) {
+                           const int32_t *__restrict__ rp, const Tv *__restrict__ v,
+                           const double *__restrict__ dinv, T *__restrict__ Ff, T *__restrict__ Fb) {
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)nT * S * 32;
     if (gid >= total) return;
@@ -321,10 +344,10 @@ __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__
     for (int dir = 0; dir < 2; ++dir) {
         const bool fwd = dir == 0;
         const int i = fwd ? (s - a - b) : (nx - 1 - (s - (TJ - 1 - a) - (TK - 1 - b)));
-        double *out = (fwd ? Ff : Fb) + ((size_t)t * S + s) * CHUNK + lane;
+        T *out = (fwd ? Ff : Fb) + ((size_t)t * S + s) * CHUNK + lane;
         const bool valid = j < ny && k < nz && i >= 0 && i < nx;
         if (!valid) {
-            for (int q = 0; q < NQ; ++q) out[q * 32] = 0.0;
+            for (int q = 0; q < NQ; ++q) out[q * 32] = T(0);
             continue;
         }
         const int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
@@ -340,26 +363,31 @@ __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__
         const int sl[3] = {fwd ? mz : px, fwd ? my : py, fwd ? mx : pz};
         for (int blk = 0; blk < 3; ++blk)
             for (int e = 0; e < 9; ++e)
-                out[(blk * 9 + e) * 32] = sl[blk] >= 0 ? v[9 * ((int64_t)rp[c] + sl[blk]) + e] : 0.0;
-        for (int e = 0; e < 9; ++e) out[(27 + e) * 32] = dinv[9 * c + e];
+                out[(blk * 9 + e) * 32] = sl[blk] >= 0 ? (T)v[9 * ((int64_t)rp[c] + sl[blk]) + e] : T(0);
+        for (int e = 0; e < 9; ++e) out[(27 + e) * 32] = (T)dinv[9 * c + e];
     }
 }
 
-__global__ void fill_sentinel(int64_t n, double *p) {
+template <typename T>
+__global__ void fill_sentinel(int64_t n, T *p) {
+    using U = typename Bits<T>::U;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        reinterpret_cast<unsigned long long *>(p)[i] = SENT;
+        reinterpret_cast<U *>(p)[i] = Bits<T>::SENT;
 }
 
 }  // namespace
 
-cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T) {
+template <typename T>
+cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_) {
+    IluTiles *Tl = T_;
     const int nx = A->nx, ny = A->ny, nz = A->nz;
     const int nTJ = (ny + TJ - 1) / TJ, nTK = (nz + TK - 1) / TK;
     const int nT = nTJ * nTK;
     const int S = nx + TJ + TK - 2;
+    const size_t chunk_bytes = CHUNK * sizeof(T);
     cudaError_t e = cudaSuccess;
-    if (!T->Ff || T->nT != nT || T->S != S) {
-        free_tiles(T);
+    if (!Tl->Ff || Tl->nT != nT || Tl->S != S || Tl->elem != (int)sizeof(T)) {
+        free_tiles(Tl);
         std::vector<int2> order;
         order.reserve(nT);
         for (int d = 0; d <= nTJ + nTK - 2; ++d)
@@ -367,73 +395,89 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T) {
                 const int K = d - J;
                 if (K >= 0 && K < nTK) order.push_back(make_int2(J, K));
             }
-        T->nT = nT;
-        T->S = S;
-        const size_t fbytes = (size_t)nT * S * CHUNK_BYTES;
-        if ((e = cudaMalloc((void **)&T->Ff, fbytes)) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void **)&T->Fb, fbytes)) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void **)&T->order, sizeof(int2) * nT)) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void **)&T->scratch, sizeof(double) * 3 * std::max<int64_t>(A->nb, 1))) != cudaSuccess)
-            return e;
-        if ((e = cudaMemcpyAsync(T->order, order.data(), sizeof(int2) * nT, cudaMemcpyHostToDevice, A->stream)) !=
+        Tl->nT = nT;
+        Tl->S = S;
+        Tl->elem = (int)sizeof(T);
+        const size_t fbytes = (size_t)nT * S * chunk_bytes;
+        if ((e = cudaMalloc(&Tl->Ff, fbytes)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&Tl->Fb, fbytes)) != cudaSuccess) return e;
+        if ((e = cudaMalloc((void **)&Tl->order, sizeof(int2) * nT)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&Tl->scratch, sizeof(T) * 3 * std::max<int64_t>(A->nb, 1))) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(Tl->order, order.data(), sizeof(int2) * nT, cudaMemcpyHostToDevice, A->stream)) !=
             cudaSuccess)
             return e;
         if ((e = cudaStreamSynchronize(A->stream)) != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
+        int dev = 0, sms = 0, per_f = 0, per_b = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = NS * CHUNK_BYTES + NS * sizeof(uint64_t);
-        for (int fwd = 0; fwd < 2; ++fwd) {
-            const void *fn = fwd ? (const void *)ilu_sweep_tiles<true> : (const void *)ilu_sweep_tiles<false>;
-            if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-                return e;
-        }
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ilu_sweep_tiles<true>, 32, smem)) !=
-            cudaSuccess)
+        const size_t smem = NS * chunk_bytes + NS * sizeof(uint64_t);
+        if ((e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
-        int per_sm_b = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, ilu_sweep_tiles<false>, 32, smem)) !=
-            cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, ilu_sweep_tiles<T, true>, 32, smem)) !=
+                cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, ilu_sweep_tiles<T, false>, 32, smem)) !=
+                cudaSuccess)
             return e;
-        T->grid = std::max(1, std::min(nT, sms * std::min(per_sm, per_sm_b)));
-        T->smem = smem;
+        Tl->grid = std::max(1, std::min(nT, sms * std::min(per_f, per_b)));
+        Tl->smem = smem;
     }
     const int64_t total = (int64_t)nT * S * 32;
+    const unsigned g = (unsigned)((total + 255) / 256);
     rsv::count_launches(1);
-    pack_tiles<<<(unsigned)((total + 255) / 256), 256, 0, A->stream>>>(nx, ny, nz, nT, S, T->order, A->d_rp, A->d_v,
-                                                                        dinv, T->Ff, T->Fb);
+    if (sizeof(T) == 8)
+        pack_tiles<T, double><<<g, 256, 0, A->stream>>>(nx, ny, nz, nT, S, Tl->order, A->d_rp, A->d_v, dinv,
+                                                        (T *)Tl->Ff, (T *)Tl->Fb);
+    else
+        pack_tiles<T, float><<<g, 256, 0, A->stream>>>(nx, ny, nz, nT, S, Tl->order, A->d_rp, A->d_v32, dinv,
+                                                       (T *)Tl->Ff, (T *)Tl->Fb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return reset_tiles_scratch(A, T);
+    return reset_tiles_scratch(A, Tl);
 }
 
-cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *T) {
+cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *Tl) {
     const int64_t n = 3 * A->nb;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
     rsv::count_launches(1);
-    fill_sentinel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, A->stream>>>(
-        n, T->scratch);
+    if (Tl->elem == 8)
+        fill_sentinel<double><<<g, 256, 0, A->stream>>>(n, (double *)Tl->scratch);
+    else
+        fill_sentinel<float><<<g, 256, 0, A->stream>>>(n, (float *)Tl->scratch);
     return cudaGetLastError();
 }
 
-void free_tiles(IluTiles *T) {
-    if (T->Ff) cudaFree(T->Ff);
-    if (T->Fb) cudaFree(T->Fb);
-    if (T->order) cudaFree(T->order);
-    if (T->scratch) cudaFree(T->scratch);
-    *T = IluTiles();
+void free_tiles(IluTiles *Tl) {
+    if (Tl->Ff) cudaFree(Tl->Ff);
+    if (Tl->Fb) cudaFree(Tl->Fb);
+    if (Tl->order) cudaFree(Tl->order);
+    if (Tl->scratch) cudaFree(Tl->scratch);
+    *Tl = IluTiles();
 }
 
-cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T, const double *r, double *z, const int *done,
+template <typename T>
+cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &Tl, const T *r, T *z, const int *done,
                                    int *status, unsigned long long timeout_ns) {
-    SweepArgs f{A->nx, A->ny, A->nz, T.nT, T.S, T.order, T.Ff, r, T.scratch, z, done, status, timeout_ns};
-    SweepArgs bw{A->nx, A->ny, A->nz, T.nT, T.S, T.order, T.Fb, T.scratch, z, T.scratch, done, status, timeout_ns};
+    SweepArgs<T> f{A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, (const T *)Tl.Ff, r, (T *)Tl.scratch, z,
+                   done, status, timeout_ns};
+    SweepArgs<T> bw{A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, (const T *)Tl.Fb, (const T *)Tl.scratch, z,
+                    (T *)Tl.scratch, done, status, timeout_ns};
     void *fa[] = {&f};
     void *ba[] = {&bw};
     rsv::count_launches(2);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<true>, dim3(T.grid), dim3(32), fa,
-                                                T.smem, A->stream);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<T, true>, dim3(Tl.grid), dim3(32), fa,
+                                                Tl.smem, A->stream);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<false>, dim3(T.grid), dim3(32), ba, T.smem,
+    return cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<T, false>, dim3(Tl.grid), dim3(32), ba, Tl.smem,
                                        A->stream);
 }
+
+template cudaError_t tiles_setup<double>(const rsv_mat *, const double *, IluTiles *);
+template cudaError_t tiles_setup<float>(const rsv_mat *, const double *, IluTiles *);
+template cudaError_t launch_ilu_apply_tiles<double>(const rsv_mat *, const IluTiles &, const double *, double *,
+                                                    const int *, int *, unsigned long long);
+template cudaError_t launch_ilu_apply_tiles<float>(const rsv_mat *, const IluTiles &, const float *, float *,
+                                                   const int *, int *, unsigned long long);
 
 }  // namespace rsv

@@ -1,0 +1,640 @@
+// C ABI of librsv, part 2: the solver handle, preconditioner setup/apply and
+// the Krylov drivers.
+//
+// Krylov solvers (Section "Solvers": restarted GMRES(m) and BiCGSTAB with the
+// SOLVER fields rtol, atol, btol, maxit, restart).  All vector work and every
+// solver scalar stay on the device; the host only launches kernels and reads
+// a few status words once per GMRES cycle or every few BiCGSTAB iterations.
+// Kernels of a step that follows convergence see the device `done` flag and
+// return at once.
+//
+// Arnoldi orthogonalisation is classical Gram-Schmidt applied twice (two
+// passes of "all projections, then one multi-vector update"); the Hessenberg
+// columns, Givens rotations and the residual estimate are FP64 scalars kept
+// in device memory.
+//
+// Mixed precision (precision = RSV_PREC_MIXED): an FP64 iterative-refinement
+// loop r = b - A x (FP64 SpMV, FP64 norm), inner solve A d = r / ||r|| with
+// FP32 matrix values, FP32 preconditioner factors and an FP32 Krylov basis
+// (dot products still accumulate in FP64), then x += ||r|| d.
+#include <cmath>
+#include <new>
+
+#include "common.cuh"
+
+namespace rsv {
+namespace {
+
+// ------------------------------------------------------------- tiny kernels
+
+__global__ void gmres_cycle_init(DevState *ds) {
+    ds->g[0] = ds->beta;
+    for (int i = 1; i <= kMaxRestart; ++i) ds->g[i] = 0.0;
+    ds->jend = 0;
+    ds->done = 0;
+}
+
+__device__ __forceinline__ void raise_status(DevState *ds, int code) {
+    if (ds->status == 0) ds->status = code;
+    ds->done = 1;
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
+// previous Givens rotations, a new rotation and the residual estimate |g_{j+1}|.
+__global__ void gmres_givens(DevState *ds, int j, int m) {
+    if (ds->done) return;
+    double *H = ds->H;
+    for (int i = 0; i <= j; ++i) H[i * m + j] = ds->h1[i] + ds->h2[i];
+    H[(j + 1) * m + j] = ds->hn;
+    for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], b = H[(i + 1) * m + j];
+        H[i * m + j] = ds->cs[i] * a + ds->sn[i] * b;
+        H[(i + 1) * m + j] = -ds->sn[i] * a + ds->cs[i] * b;
+    }
+    const double a = H[j * m + j], b = H[(j + 1) * m + j];
+    const double rho = hypot(a, b);
+    if (!isfinite(rho) || !isfinite(ds->hn)) return raise_status(ds, RSV_ENAN);
+    if (!(rho > 0.0)) return raise_status(ds, RSV_EBREAKDOWN);
+    ds->cs[j] = a / rho;
+    ds->sn[j] = b / rho;
+    H[j * m + j] = rho;
+    H[(j + 1) * m + j] = 0.0;
+    ds->g[j + 1] = -ds->sn[j] * ds->g[j];
+    ds->g[j] = ds->cs[j] * ds->g[j];
+    ds->jend = j + 1;
+    ds->iters += 1;
+    const bool lucky = !(ds->hn > 0.0);
+    if (fabs(ds->g[j + 1]) <= ds->tol || ds->iters >= ds->maxit || lucky || j + 1 == m) ds->done = 1;
+}
+
+__global__ void gmres_backsolve(DevState *ds, int m) {
+    const int n = ds->jend;
+    for (int i = n - 1; i >= 0; --i) {
+        double s = ds->g[i];
+        for (int q = i + 1; q < n; ++q) s -= ds->H[i * m + q] * ds->y[q];
+        ds->y[i] = s / ds->H[i * m + i];
+    }
+}
+
+// BiCGSTAB scalar steps (single thread).  red[]: 0 <rh,r>, 1 <rh,v>, 2 ||v||,
+// 3 ||s||, 4 <t,s>, 5 <t,t>, 8 ||rh||, 9 ||r||, 10 beta, 11 half-step flag.
+__global__ void bicg_beta(DevState *ds, double btol) {
+    if (ds->done) return;
+    const double rho1 = ds->red[0];
+    if (!isfinite(rho1)) return raise_status(ds, RSV_ENAN);
+    if (fabs(rho1) <= btol * ds->red[8] * ds->red[9]) return raise_status(ds, RSV_EBREAKDOWN);
+    ds->rho1 = rho1;
+    ds->red[10] = (rho1 / ds->rho) * (ds->alpha / ds->omega);
+}
+
+__global__ void bicg_alpha(DevState *ds, double btol) {
+    if (ds->done) return;
+    const double rv = ds->red[1];
+    if (!isfinite(rv)) return raise_status(ds, RSV_ENAN);
+    if (fabs(rv) <= btol * ds->red[8] * ds->red[2]) return raise_status(ds, RSV_EBREAKDOWN);
+    ds->alpha = ds->rho1 / rv;
+}
+
+__global__ void bicg_check_s(DevState *ds) {
+    if (ds->done) return;
+    ds->iters += 1;
+    const double sn = ds->red[3];
+    if (!isfinite(sn)) return raise_status(ds, RSV_ENAN);
+    if (sn <= ds->tol) {
+        ds->red[11] = 1.0;  // x += alpha ph pending
+        ds->done = 1;
+    }
+}
+
+__global__ void bicg_omega(DevState *ds, double btol) {
+    if (ds->done) return;
+    const double ts = ds->red[4], tt = ds->red[5];
+    if (!isfinite(tt)) return raise_status(ds, RSV_ENAN);
+    if (!(tt > 0.0)) return raise_status(ds, RSV_EBREAKDOWN);
+    const double om = ts / tt;
+    if (fabs(om) <= btol) return raise_status(ds, RSV_EBREAKDOWN);
+    ds->omega = om;
+}
+
+__global__ void bicg_finish_iter(DevState *ds) {
+    if (ds->done) return;
+    ds->rho = ds->rho1;
+    const double rn = ds->red[9];
+    if (!isfinite(rn)) return raise_status(ds, RSV_ENAN);
+    if (rn <= ds->tol || ds->iters >= ds->maxit) ds->done = 1;
+}
+
+__global__ void bicg_init(DevState *ds) {
+    ds->rho = ds->alpha = ds->omega = 1.0;
+    ds->red[8] = ds->red[9];
+    ds->red[11] = 0.0;
+    ds->done = 0;
+}
+
+// p = r + beta (p - omega v)
+template <typename T>
+__global__ void bicg_update_p(int64_t n, const DevState *ds, const T *r, const T *v, T *p) {
+    if (ds->done) return;
+    const T beta = (T)ds->red[10], om = (T)ds->omega;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        p[i] = r[i] + beta * (p[i] - om * v[i]);
+}
+
+// s = r - alpha v
+template <typename T>
+__global__ void bicg_update_s(int64_t n, const DevState *ds, const T *r, const T *v, T *s) {
+    if (ds->done) return;
+    const T al = (T)ds->alpha;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) s[i] = r[i] - al * v[i];
+}
+
+// x += alpha ph when the half step converged
+template <typename T>
+__global__ void bicg_half_x(int64_t n, DevState *ds, const T *ph, T *x) {
+    if (ds->red[11] != 1.0) return;
+    const T al = (T)ds->alpha;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) x[i] += al * ph[i];
+}
+
+__global__ void bicg_consume_half(DevState *ds) {
+    if (ds->red[11] == 1.0) ds->red[11] = 2.0;
+}
+
+// x += alpha ph + omega sh; r = s - omega t
+template <typename T>
+__global__ void bicg_update_xr(int64_t n, const DevState *ds, const T *ph, const T *sh, const T *s, const T *t,
+                               T *x, T *r) {
+    if (ds->done) return;
+    const T al = (T)ds->alpha, om = (T)ds->omega;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        x[i] += al * ph[i] + om * sh[i];
+        r[i] = s[i] - om * t[i];
+    }
+}
+
+int egrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
+}  // namespace
+}  // namespace rsv
+
+using namespace rsv;
+
+// Krylov workspace of one vector precision.
+struct KrylovWork {
+    void *V = nullptr;   // (m+1) basis vectors (GMRES) or 8 vectors (BiCGSTAB)
+    void *Z = nullptr;   // m preconditioned vectors (FGMRES)
+    void *w = nullptr;   // scratch
+    void *t = nullptr;   // scratch
+};
+
+struct rsv_solver {
+    rsv_mat *A = nullptr;
+    rsv_solver_params p{};
+    cudaStream_t st = nullptr;
+    int64_t n = 0;
+    int pc_type = -1;
+    rsv_pc_params pcp{};
+    uint64_t pc_version = ~0ull;
+    bool mixed = false;
+    DevState *ds = nullptr;
+    double *partial = nullptr;
+    KrylovWork kw;               // FP64 work (FP64 solves) or FP32 work (mixed inner solves)
+    double *r64 = nullptr;       // FP64 residual (true residual / refinement)
+    double *d_b = nullptr, *d_x = nullptr;  // staging for host buffers
+    float *rf = nullptr, *df = nullptr;     // mixed: scaled inner right-hand side and correction
+    double *dinv = nullptr;      // FP64 inverted diagonal blocks (Jacobi: A_ii^-1, ILU: D_i^-1)
+    float *dinv32 = nullptr;     // FP32 copy for mixed block Jacobi
+    Schedule sch;
+    IluTiles tiles;
+    bool scratch_dirty = false;  // a sweep timed out: its sentinel scratch must be refilled
+    double ms_setup = 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t spmv(rsv_solver *s, T alpha, const T *x, T beta, T *y, const int *done);
+template <>
+cudaError_t spmv<double>(rsv_solver *s, double alpha, const double *x, double beta, double *y, const int *done) {
+    return launch_spmv_f64(s->A, alpha, x, beta, y, done);
+}
+template <>
+cudaError_t spmv<float>(rsv_solver *s, float alpha, const float *x, float beta, float *y, const int *done) {
+    return launch_spmv_f32(s->A, alpha, x, beta, y, done);
+}
+
+// z = M^{-1} r on the solver stream in precision T; `done` gates the kernels.
+template <typename T>
+cudaError_t pc_apply(rsv_solver *s, const T *r, T *z, const int *done) {
+    switch (s->pc_type) {
+    case RSV_PC_NONE: return cudaMemcpyAsync(z, r, sizeof(T) * s->n, cudaMemcpyDeviceToDevice, s->st);
+    case RSV_PC_BJACOBI:
+        if (sizeof(T) == 8) return launch_bj_apply<T>(s->st, s->A->nb, (const T *)s->dinv, r, z, done);
+        return launch_bj_apply<T>(s->st, s->A->nb, (const T *)s->dinv32, r, z, done);
+    case RSV_PC_BILU0:
+        return launch_ilu_apply_tiles<T>(s->A, s->tiles, r, z, done, &s->ds->status,
+                                         (unsigned long long)s->p.watchdog * 1000ull);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// r = b - A x and ||r|| into *nrm (device)
+template <typename T>
+cudaError_t residual(rsv_solver *s, const T *b, const T *x, T *r, double *nrm) {
+    cudaError_t e = cudaMemcpyAsync(r, b, sizeof(T) * s->n, cudaMemcpyDeviceToDevice, s->st);
+    if (e == cudaSuccess) e = spmv<T>(s, T(-1), x, T(1), r, nullptr);
+    if (e == cudaSuccess) e = launch_dot<T>(s->st, s->n, r, r, s->partial, nrm, &s->ds->counter[0], 1, nullptr);
+    return e;
+}
+
+struct HostState {
+    double beta;
+    int done, status, iters, jend;
+};
+
+rsv_status fetch(rsv_solver *s, HostState *h) {
+    DevState *ds = s->ds;
+    RSV_CUDA_TRY(cudaMemcpyAsync(&h->beta, &ds->beta, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&h->done, &ds->done, 4 * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    return RSV_OK;
+}
+
+rsv_status set_tol(rsv_solver *s, double tol) {
+    RSV_CUDA_TRY(cudaMemcpyAsync(&s->ds->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s->st));
+    return RSV_OK;
+}
+
+// Restarted GMRES(m) / FGMRES on A x = b in precision T, from the x given,
+// until ||b - A x|| <= tol (confirmed on the residual recomputed in T) or the
+// device iteration counter reaches p.maxit.  Counts cycles into *cycles.
+template <typename T>
+rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles) {
+    const int64_t n = s->n;
+    const int m = s->p.restart;
+    const bool flex = s->p.solver == RSV_FGMRES;
+    DevState *ds = s->ds;
+    T *V = (T *)s->kw.V, *Z = (T *)s->kw.Z, *w = (T *)s->kw.w, *t = (T *)s->kw.t;
+    HostState h{};
+    RSV_TRY(set_tol(s, tol));
+    for (;;) {
+        RSV_CUDA_TRY(residual<T>(s, b, x, V, &ds->beta));
+        RSV_TRY(fetch(s, &h));
+        if (h.status != RSV_OK) return (rsv_status)h.status;
+        if (!std::isfinite(h.beta)) return RSV_ENAN;
+        if (h.beta <= tol) return RSV_OK;
+        if (h.iters >= s->p.maxit) return RSV_ENOCONV;
+        ++*cycles;
+        rsv::count_launches(1);
+        gmres_cycle_init<<<1, 1, 0, s->st>>>(ds);
+        RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, V, &ds->beta, nullptr));
+        for (int j = 0; j < m; ++j) {
+            T *vj = V + (size_t)j * n;
+            T *wj = V + (size_t)(j + 1) * n;
+            T *z = flex ? Z + (size_t)j * n : t;
+            RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
+            RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
+            // classical Gram-Schmidt, two passes (re-orthogonalised)
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, n, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done));
+            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, n, j + 1, ds->h1, -1.0, wj, s->partial, nullptr,
+                                         &ds->counter[1], &ds->done));
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, n, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done));
+            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, n, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
+                                         &ds->counter[1], &ds->done));
+            rsv::count_launches(1);
+            gmres_givens<<<1, 1, 0, s->st>>>(ds, j, m);
+            RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, wj, &ds->hn, &ds->done));
+        }
+        RSV_TRY(fetch(s, &h));
+        if (h.status != RSV_OK && h.status != RSV_EBREAKDOWN) return (rsv_status)h.status;
+        if (h.jend > 0) {
+            rsv::count_launches(1);
+            gmres_backsolve<<<1, 1, 0, s->st>>>(ds, m);
+            if (flex) {
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, x, Z, n, h.jend, ds->y, 1.0, x, s->partial, nullptr,
+                                             &ds->counter[1], nullptr));
+            } else {
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, (const T *)nullptr, V, n, h.jend, ds->y, 1.0, w, s->partial,
+                                             nullptr, &ds->counter[1], nullptr));
+                RSV_CUDA_TRY(pc_apply<T>(s, w, t, nullptr));
+                RSV_CUDA_TRY(launch_axpby<T>(s->st, n, T(1), t, T(1), x, x));
+            }
+        }
+        if (h.status == RSV_EBREAKDOWN) return RSV_EBREAKDOWN;
+    }
+}
+
+// Right-preconditioned BiCGSTAB in precision T from the x given.
+template <typename T>
+rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
+    const int64_t n = s->n;
+    DevState *ds = s->ds;
+    T *r = (T *)s->kw.V, *rh = r + n, *p = r + 2 * n, *v = r + 3 * n, *ph = r + 4 * n, *sh = r + 5 * n,
+      *sv = r + 6 * n, *t = r + 7 * n;  // s (sv) and t adjacent: one two-column dot
+    const double btol = s->p.btol;
+    RSV_TRY(set_tol(s, tol));
+    RSV_CUDA_TRY(residual<T>(s, b, x, r, &ds->red[9]));
+    RSV_CUDA_TRY(cudaMemcpyAsync(rh, r, sizeof(T) * n, cudaMemcpyDeviceToDevice, s->st));
+    RSV_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(T) * n, s->st));
+    RSV_CUDA_TRY(cudaMemsetAsync(v, 0, sizeof(T) * n, s->st));
+    rsv::count_launches(1);
+    bicg_init<<<1, 1, 0, s->st>>>(ds);
+    double rn0 = 0.0;
+    RSV_CUDA_TRY(cudaMemcpyAsync(&rn0, &ds->red[9], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (!std::isfinite(rn0)) return RSV_ENAN;
+    if (rn0 <= tol) return RSV_OK;
+    const int g = egrid(n);
+    const int kBatch = 8;
+    HostState h{};
+    for (;;) {
+        for (int it = 0; it < kBatch; ++it) {
+            const int *done = &ds->done;
+            RSV_CUDA_TRY(launch_dot<T>(s->st, n, rh, r, s->partial, &ds->red[0], &ds->counter[0], 0, done));
+            rsv::count_launches(2);
+            bicg_beta<<<1, 1, 0, s->st>>>(ds, btol);
+            bicg_update_p<T><<<g, 256, 0, s->st>>>(n, ds, r, v, p);
+            RSV_CUDA_TRY(pc_apply<T>(s, p, ph, done));
+            RSV_CUDA_TRY(spmv<T>(s, T(1), ph, T(0), v, done));
+            RSV_CUDA_TRY(launch_dot<T>(s->st, n, rh, v, s->partial, &ds->red[1], &ds->counter[0], 0, done));
+            RSV_CUDA_TRY(launch_dot<T>(s->st, n, v, v, s->partial, &ds->red[2], &ds->counter[0], 1, done));
+            rsv::count_launches(2);
+            bicg_alpha<<<1, 1, 0, s->st>>>(ds, btol);
+            bicg_update_s<T><<<g, 256, 0, s->st>>>(n, ds, r, v, sv);
+            RSV_CUDA_TRY(launch_dot<T>(s->st, n, sv, sv, s->partial, &ds->red[3], &ds->counter[0], 1, done));
+            rsv::count_launches(3);
+            bicg_check_s<<<1, 1, 0, s->st>>>(ds);
+            bicg_half_x<T><<<g, 256, 0, s->st>>>(n, ds, ph, x);
+            bicg_consume_half<<<1, 1, 0, s->st>>>(ds);
+            RSV_CUDA_TRY(pc_apply<T>(s, sv, sh, done));
+            RSV_CUDA_TRY(spmv<T>(s, T(1), sh, T(0), t, done));
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, t, sv, n, 2, s->partial, &ds->red[4], &ds->counter[0], done));
+            rsv::count_launches(2);
+            bicg_omega<<<1, 1, 0, s->st>>>(ds, btol);
+            bicg_update_xr<T><<<g, 256, 0, s->st>>>(n, ds, ph, sh, sv, t, x, r);
+            RSV_CUDA_TRY(launch_dot<T>(s->st, n, r, r, s->partial, &ds->red[9], &ds->counter[0], 1, done));
+            rsv::count_launches(1);
+            bicg_finish_iter<<<1, 1, 0, s->st>>>(ds);
+        }
+        RSV_CUDA_TRY(cudaGetLastError());
+        RSV_TRY(fetch(s, &h));
+        if (h.done || h.status != RSV_OK) break;
+    }
+    if (h.status != RSV_OK) return (rsv_status)h.status;
+    double rn = 0.0, half = 0.0;
+    RSV_CUDA_TRY(cudaMemcpyAsync(&rn, &ds->red[9], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&half, &ds->red[11], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (half != 0.0 || rn <= tol) return RSV_OK;
+    return RSV_ENOCONV;
+}
+
+// FP64 solve: the Krylov method runs directly on the FP64 system.
+rsv_status solve_fp64(rsv_solver *s, const double *b, double *x, double tol, rsv_solve_info *info) {
+    int cycles = 0;
+    rsv_status st = (s->p.solver == RSV_BICGSTAB) ? bicgstab_run<double>(s, b, x, tol)
+                                                   : gmres_run<double>(s, b, x, tol, &cycles);
+    info->restarts = cycles;
+    return st;
+}
+
+// Mixed precision: FP64 iterative refinement around FP32 inner solves.
+rsv_status solve_mixed(rsv_solver *s, const double *b, double *x, double tol, rsv_solve_info *info) {
+    const int64_t n = s->n;
+    DevState *ds = s->ds;
+    int cycles = 0, outer = 0;
+    rsv_status result = RSV_ENOCONV;
+    for (;;) {
+        RSV_CUDA_TRY(residual<double>(s, b, x, s->r64, &ds->red[13]));
+        double rn = 0.0;
+        int iters = 0, status = 0;
+        RSV_CUDA_TRY(cudaMemcpyAsync(&rn, &ds->red[13], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        RSV_CUDA_TRY(cudaMemcpyAsync(&status, &ds->status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+        RSV_CUDA_TRY(cudaMemcpyAsync(&iters, &ds->iters, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+        RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+        if (status != RSV_OK) { result = (rsv_status)status; break; }
+        if (!std::isfinite(rn)) { result = RSV_ENAN; break; }
+        if (rn <= tol) { result = RSV_OK; break; }
+        if (outer >= s->p.max_outer || iters >= s->p.maxit) { result = RSV_ENOCONV; break; }
+        ++outer;
+        RSV_CUDA_TRY(launch_to_f32_scaled(s->st, n, s->r64, &ds->red[13], s->rf));
+        RSV_CUDA_TRY(cudaMemsetAsync(s->df, 0, sizeof(float) * n, s->st));
+        rsv_status ist = (s->p.solver == RSV_BICGSTAB) ? bicgstab_run<float>(s, s->rf, s->df, s->p.inner_rtol)
+                                                        : gmres_run<float>(s, s->rf, s->df, s->p.inner_rtol, &cycles);
+        if (ist != RSV_OK && ist != RSV_ENOCONV && ist != RSV_EBREAKDOWN) { result = ist; break; }
+        if (ist == RSV_EBREAKDOWN) {
+            // a breakdown of the inner solve still leaves a usable correction;
+            // clear the device flag so that the outer loop can continue
+            RSV_CUDA_TRY(cudaMemsetAsync(&ds->status, 0, sizeof(int), s->st));
+        }
+        RSV_CUDA_TRY(launch_add_f32_scaled(s->st, n, s->df, &ds->red[13], x));
+    }
+    info->restarts = cycles;
+    info->outer_iters = outer;
+    return result;
+}
+
+void solver_free(rsv_solver *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->st);
+    for (void *p : {(void *)s->ds, (void *)s->partial, s->kw.V, s->kw.Z, s->kw.w, s->kw.t, (void *)s->r64,
+                    (void *)s->d_b, (void *)s->d_x, (void *)s->rf, (void *)s->df, (void *)s->dinv,
+                    (void *)s->dinv32})
+        if (p) cudaFree(p);
+    free_schedule(&s->sch);
+    free_tiles(&s->tiles);
+    if (s->e0) cudaEventDestroy(s->e0);
+    if (s->e1) cudaEventDestroy(s->e1);
+    delete s;
+}
+
+rsv_status read_status(rsv_solver *s, int *status) {
+    RSV_CUDA_TRY(cudaMemcpyAsync(status, &s->ds->status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    return RSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver **out) {
+    if (!A || !p || !out) return RSV_EINVAL;
+    if (p->solver < RSV_GMRES || p->solver > RSV_FGMRES) return RSV_EINVAL;
+    if (p->restart < 1 || p->restart > kMaxRestart || p->maxit < 0 || !(p->rtol >= 0.0) || !(p->atol >= 0.0) ||
+        !(p->btol >= 0.0) || p->watchdog < 1)
+        return RSV_EINVAL;
+    if (p->precision != RSV_PREC_FP64 && p->precision != RSV_PREC_MIXED) return RSV_EINVAL;
+    if (p->precision == RSV_PREC_MIXED && (!(p->inner_rtol > 0.0) || !(p->inner_rtol < 1.0) || p->max_outer < 1))
+        return RSV_EINVAL;
+    rsv_solver *s = new (std::nothrow) rsv_solver();
+    if (!s) return RSV_ENOMEM;
+    s->A = A;
+    s->p = *p;
+    s->st = A->stream;
+    s->n = 3 * A->nb;
+    s->mixed = p->precision == RSV_PREC_MIXED;
+    const int64_t n = std::max<int64_t>(s->n, 1);
+    const int m = p->restart;
+    const size_t es = s->mixed ? sizeof(float) : sizeof(double);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    };
+    alloc((void **)&s->ds, sizeof(DevState));
+    alloc((void **)&s->partial, sizeof(double) * (kMaxRestart + 1) * kRedBlocks);
+    if (p->solver == RSV_BICGSTAB) {
+        alloc(&s->kw.V, 8 * n * es);
+    } else {
+        alloc(&s->kw.V, (size_t)(m + 1) * n * es);
+        if (p->solver == RSV_FGMRES) alloc(&s->kw.Z, (size_t)m * n * es);
+    }
+    alloc(&s->kw.w, n * es);
+    alloc(&s->kw.t, n * es);
+    alloc((void **)&s->r64, n * sizeof(double));
+    alloc((void **)&s->d_b, n * sizeof(double));
+    alloc((void **)&s->d_x, n * sizeof(double));
+    if (s->mixed) {
+        alloc((void **)&s->rf, n * sizeof(float));
+        alloc((void **)&s->df, n * sizeof(float));
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) {
+        solver_free(s);
+        return cuda_status(e);
+    }
+    *out = s;
+    return RSV_OK;
+}
+
+void rsv_solver_destroy(rsv_solver *s) { solver_free(s); }
+
+rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params) {
+    if (!s || pc_type < RSV_PC_NONE || pc_type > RSV_PC_CPR) return RSV_EINVAL;
+    rsv_pc_params pcp;
+    rsv_pc_params_default(&pcp);
+    if (params) pcp = *params;
+    if (pc_type == RSV_PC_CPR) return RSV_ENOTSUP;
+    rsv_mat *A = s->A;
+    s->pc_type = -1;
+    RSV_CUDA_TRY(cudaEventRecord(s->e0, s->st));
+    RSV_CUDA_TRY(cudaMemsetAsync(&s->ds->status, 0, sizeof(int), s->st));
+    if ((pc_type == RSV_PC_BJACOBI || pc_type == RSV_PC_BILU0) && !s->dinv)
+        RSV_CUDA_TRY(cudaMalloc((void **)&s->dinv, sizeof(double) * 9 * std::max<int64_t>(A->nb, 1)));
+    if (pc_type == RSV_PC_BJACOBI) {
+        if (s->mixed && !s->dinv32)
+            RSV_CUDA_TRY(cudaMalloc((void **)&s->dinv32, sizeof(float) * 9 * std::max<int64_t>(A->nb, 1)));
+        RSV_CUDA_TRY(launch_bj_setup(A, s->mixed, s->dinv, s->mixed ? s->dinv32 : nullptr, &s->ds->status));
+    }
+    if (pc_type == RSV_PC_BILU0) {
+        if (!s->sch.cells) RSV_CUDA_TRY(build_schedule(A, &s->sch));
+        RSV_CUDA_TRY(launch_ilu_setup(A, s->sch, s->mixed, s->dinv, &s->ds->status));
+        if (s->mixed)
+            RSV_CUDA_TRY(tiles_setup<float>(A, s->dinv, &s->tiles));
+        else
+            RSV_CUDA_TRY(tiles_setup<double>(A, s->dinv, &s->tiles));
+        s->scratch_dirty = false;
+    }
+    RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
+    int status = 0;
+    RSV_TRY(read_status(s, &status));
+    float ms = 0.f;
+    RSV_CUDA_TRY(cudaEventElapsedTime(&ms, s->e0, s->e1));
+    s->ms_setup = ms;
+    if (status != RSV_OK) return (rsv_status)status;
+    s->pc_type = pc_type;
+    s->pcp = pcp;
+    s->pc_version = A->version;
+    return RSV_OK;
+}
+
+static rsv_status pc_check(rsv_solver *s, const void *r, const void *z) {
+    if (!s || !r || !z || r == z) return RSV_EINVAL;
+    if (s->pc_type < 0 || s->pc_version != s->A->version) return RSV_EINVAL;
+    return RSV_OK;
+}
+
+rsv_status rsv_precond_apply(rsv_solver *s, const double *r, double *z) {
+    RSV_TRY(pc_check(s, r, z));
+    if (s->mixed) return RSV_EINVAL;
+    RSV_CUDA_TRY(pc_apply<double>(s, r, z, nullptr));
+    return RSV_OK;
+}
+
+rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z) {
+    RSV_TRY(pc_check(s, r, z));
+    if (!s->mixed) return RSV_EINVAL;
+    RSV_CUDA_TRY(pc_apply<float>(s, r, z, nullptr));
+    return RSV_OK;
+}
+
+rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host) {
+    if (!s || !dinv_host || !s->dinv || (s->pc_type != RSV_PC_BJACOBI && s->pc_type != RSV_PC_BILU0))
+        return RSV_EINVAL;
+    RSV_CUDA_TRY(cudaMemcpyAsync(dinv_host, s->dinv, sizeof(double) * 9 * s->A->nb, cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    return RSV_OK;
+}
+
+rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info) {
+    if (!s || !b || !x) return RSV_EINVAL;
+    if (s->pc_type < 0 || s->pc_version != s->A->version) return RSV_EINVAL;
+    const int64_t n = s->n;
+    const double *db = b;
+    double *dx = x;
+    RSV_CUDA_TRY(cudaEventRecord(s->e0, s->st));
+    if (!on_device) {
+        RSV_CUDA_TRY(cudaMemcpyAsync(s->d_b, b, sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
+        RSV_CUDA_TRY(cudaMemcpyAsync(s->d_x, x, sizeof(double) * n, cudaMemcpyHostToDevice, s->st));
+        db = s->d_b;
+        dx = s->d_x;
+    }
+    RSV_CUDA_TRY(cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
+    if (s->scratch_dirty && s->tiles.scratch) {
+        RSV_CUDA_TRY(reset_tiles_scratch(s->A, &s->tiles));
+        s->scratch_dirty = false;
+    }
+    double bnorm = 0.0;
+    RSV_CUDA_TRY(launch_dot<double>(s->st, n, db, db, s->partial, &s->ds->bnorm, &s->ds->counter[0], 1, nullptr));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&bnorm, &s->ds->bnorm, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (!std::isfinite(bnorm)) return RSV_ENAN;
+    const double tol = std::max(s->p.rtol * bnorm, s->p.atol);
+    const int maxit = s->p.maxit;
+    RSV_CUDA_TRY(cudaMemcpyAsync(&s->ds->maxit, &maxit, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    rsv_solve_info local{};
+    rsv_status st = s->mixed ? solve_mixed(s, db, dx, tol, &local) : solve_fp64(s, db, dx, tol, &local);
+    if (st == RSV_ECUDA || st == RSV_ENOMEM) return st;
+    if (st == RSV_ETIMEOUT) s->scratch_dirty = true;
+    // FP64 true residual, recomputed; the iteration count from the device
+    double rn = 0.0;
+    int iters = 0;
+    RSV_CUDA_TRY(residual<double>(s, db, dx, s->r64, &s->ds->red[12]));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&rn, &s->ds->red[12], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&iters, &s->ds->iters, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    if (!on_device) RSV_CUDA_TRY(cudaMemcpyAsync(x, s->d_x, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    float ms = 0.f;
+    RSV_CUDA_TRY(cudaEventElapsedTime(&ms, s->e0, s->e1));
+    if (info) {
+        info->iters = iters;
+        info->restarts = local.restarts;
+        info->outer_iters = local.outer_iters;
+        info->status = st;
+        info->true_relres = bnorm > 0 ? rn / bnorm : rn;
+        info->ms_setup = s->ms_setup;
+        info->ms_solve = ms;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -234,6 +234,55 @@ def test_state_errors(rsv, torch):
         rsv.Solver(A, restart=0)
 
 
+@pytest.mark.parametrize("dims", [(7, 5, 3), (20, 20, 10), (33, 17, 9)])
+@pytest.mark.parametrize("pc", ["bjacobi", "bilu0"])
+def test_mixed_preconditioner_fp32(rsv, torch, dims, pc):
+    """Mixed precision: the factor is computed in FP64 from the FP32-rounded matrix
+    (compared with the oracle on the same rounded values to 1e-12) and applied in
+    FP32 (compared with the oracle's FP64 application of the FP32-rounded factor)."""
+    p = synth.make_problem(*dims, seed=44)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, precision="mixed")
+    s.setup(pc)
+    v32 = p.vals.astype(np.float32).astype(np.float64)
+    o = oracle.System(p.nx, p.ny, p.nz, p.row_ptr, p.col_idx, v32, pc=pc)
+    d_or, _, _ = o.factors()
+    d_gpu = s.dinv()
+    assert np.all(np.abs(d_gpu - d_or) <= 1e-12 * np.abs(d_or).max(axis=(1, 2), keepdims=True))
+    of = oracle.System.from_problem(p, pc=pc, float_round=True)
+    r = np.random.default_rng(45).standard_normal(p.n).astype(np.float32)
+    rd = torch.from_numpy(r).cuda()
+    zd = torch.zeros_like(rd)
+    s.apply(rd, zd)
+    torch.cuda.synchronize()
+    _, z_or = of.pc_apply(r.astype(np.float64))
+    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("solver,pc", [("gmres", "bilu0"), ("bicgstab", "bilu0"), ("gmres", "bjacobi"),
+                                       ("fgmres", "bilu0")])
+def test_mixed_solve_reaches_fp64_tolerance(rsv, torch, solver, pc):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, solver=solver, precision="mixed", rtol=1e-8, inner_rtol=1e-5, maxit=6000, max_outer=10)
+    s.setup(pc)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_OK, (st, info)
+    xh = x.cpu().numpy()
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, xh)) / np.linalg.norm(p.b)
+    assert relres <= 1e-8 and abs(relres - info["true_relres"]) <= 1e-12
+    assert info["outer_iters"] >= 2
+    outer = oracle.System.from_problem(p, pc="none")
+    inner = oracle.System.from_problem(p, pc=pc, float_round=True)
+    ost, _, oinfo = oracle.refine(outer, inner, p.b, solver="bicgstab" if solver == "bicgstab" else "gmres",
+                                  maxit=6000)
+    assert ost == 0
+    assert 0.5 * oinfo["iters"] - 5 <= info["iters"] <= 1.5 * oinfo["iters"] + 5, (info, oinfo)
+
+
 def test_watchdog_timeout_returns_status_and_context_survives(rsv, torch):
     """A 1 microsecond wait limit makes the tile sweeps' cross-warp waits run out:
     the solve reports ETIMEOUT (no trap, no hang) and the next solve with the
@@ -254,6 +303,19 @@ def test_watchdog_timeout_returns_status_and_context_survives(rsv, torch):
     # the timed-out solver recovers too once its limit is back to normal
     st, info = s.solve(b, x)
     assert st in (rsv.RSV_OK, rsv.RSV_ETIMEOUT)
+
+
+def test_mid_mixed_gmres_bilu0_full_size(rsv, torch):
+    p = synth.workload("mid_100x100x50")
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision="mixed")
+    s.setup("bilu0")
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == 0, info
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
 
 
 def test_mid_gmres_bilu0_full_size(rsv, torch):
