@@ -50,6 +50,7 @@ struct DevState {
     int status;     // rsv_status raised on the device (breakdown, nan, singular)
     int iters;      // Krylov iterations so far (device count)
     int jend;       // Arnoldi steps taken in the current cycle
+    int conv;       // the current cycle met the tolerance on its residual estimate
     int maxit;
     unsigned counter[4];  // last-block tickets of the reduction kernels
 };
