@@ -55,13 +55,17 @@ struct DevState {
     unsigned counter[4];  // last-block tickets of the reduction kernels
 };
 
-struct IluTiles {  // packed factor for the persistent tile sweeps (ilu_tiles.cu)
-    int nT = 0, S = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
+struct IluTiles {  // packed factor and buffers of the persistent tile sweeps (ilu_tiles.cu)
+    int nT = 0, nTK = 0, S = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
     size_t smem = 0;
     int2 *order = nullptr;    // tile (J, K) per processing position
-    void *Ff = nullptr;       // forward chunks  [nT][S][36][32]
-    void *Fb = nullptr;       // backward chunks [nT][S][36][32]
-    void *scratch = nullptr;  // y of the forward sweep (sentinel-filled between applications)
+    int *pos_of = nullptr;    // J * nTK + K -> position
+    void *Ff = nullptr;       // forward factor rows  [nT][S][32][NQP]
+    void *Fb = nullptr;       // backward factor rows [nT][S][32][NQP]
+    void *Vf = nullptr;       // forward input in tile order [nT][S][32][4]
+    void *Vb = nullptr;       // backward input (y) in tile order [nT][S][32][4]
+    void *EJf = nullptr, *EKf = nullptr;  // forward edge hand-off buffers
+    void *EJb = nullptr, *EKb = nullptr;  // backward edge hand-off buffers
 };
 
 struct Schedule {  // i+j+k wavefront hyperplanes
@@ -130,7 +134,6 @@ cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f3
 // ---- launchers implemented in ilu_tiles.cu
 template <typename T>
 cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_);
-cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *T_);
 void free_tiles(IluTiles *T_);
 template <typename T>
 cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T_, const T *r, T *z, const int *done,

@@ -8,27 +8,31 @@
 // (i = s - a - b, j0 + a, k0 + b) at step s, so the cell's -y and -z
 // neighbours inside the tile were computed by lanes (a-1, b) and (a, b-1) one
 // step earlier and arrive by warp shuffle; the -x neighbour is the lane's own
-// previous result.  Only tile-edge lanes read neighbours owned by other
-// warps.  Those values are published by plain stores into an output buffer
-// that was pre-filled with a signalling-NaN sentinel: a value is ready when
-// it is no longer the sentinel (arithmetic never produces a signalling NaN),
-// so no flags or fences are needed.  Edge values are prefetched D steps
-// ahead and re-polled (with a time limit) only if still absent.
+// previous result.
 //
-// Each warp's factor data (the three lower or upper blocks and D^{-1} of
-// every cell it visits) is packed at setup in exactly the order the warp
-// reads it: step-major chunks of 36 x 32 doubles (9216 B).  A TMA bulk copy
-// (cp.async.bulk + mbarrier) streams chunk s + NS - 1 into a shared-memory
-// ring while step s computes.
+// Everything else a step needs arrives through one shared-memory ring filled
+// by TMA bulk copies (cp.async.bulk + mbarrier) NS - 1 steps ahead:
+//   * the factor row of each lane (three off-diagonal blocks and D^{-1}, 36
+//     values, packed at setup in exactly the order the warp reads them);
+//   * the input vector, gathered into the same tile order before the sweep;
+//   * the values of neighbouring tiles' edge cells.  A tile publishes the
+//     results of its last j-row and last k-layer into small per-tile edge
+//     buffers indexed by the step at which the neighbour will need them.  The
+//     buffers hold a signalling-NaN sentinel until written (arithmetic never
+//     produces one), so a consumer that finds the sentinel in its staged copy
+//     re-reads the value from global memory until it appears (bounded by a
+//     time limit that ends the sweep with RSV_ETIMEOUT).
 //
 // The backward sweep z_c = y_c - D_c^{-1} (A_{c,+x} z_{+x} + A_{c,+y} z_{+y} +
 // A_{c,+z} z_{+z}) is the mirror image (lane (a, b) visits
-// i = nx-1 - (s - (7-a) - (3-b))).  The forward sweep writes the sentinel
-// into the output z as it goes and the backward sweep writes it back into
-// the scratch y, so both buffers are ready for the next application without
-// a separate fill.  Tiles are processed in order of J+K; all warps are
-// co-resident (cooperative launch), and a warp only ever waits for tiles
-// earlier in that order, so the waits cannot form a cycle.
+// i = nx-1 - (s - (7-a) - (3-b))).  The forward sweep writes y straight into
+// the tile order the backward sweep reads (at forward step s every lane's
+// cell is visited at backward step S-1-s), so y never exists in natural
+// order; the backward sweep writes z in natural order.
+//
+// Tiles are processed in order of J+K (backward: reverse order); all warps
+// are co-resident (cooperative launch), and a warp only ever waits for tiles
+// earlier in its order, so the waits cannot form a cycle.
 #include <algorithm>
 
 #include "common.cuh"
@@ -37,19 +41,28 @@ namespace rsv {
 namespace {
 
 constexpr int TJ = 8, TK = 4;
-constexpr int NQ = 36;               // 27 off-diagonal block entries + 9 of D^{-1}
-constexpr int NS = 4;                // shared-memory ring stages = prefetch distance
-constexpr int CHUNK = NQ * 32;       // values per warp step
+constexpr int NS = 4;  // ring stages; copies run NS - 1 steps ahead
 
-// Signalling NaNs: no arithmetic result has these bit patterns.
 template <typename T> struct Bits;
 template <> struct Bits<double> {
     using U = unsigned long long;
-    static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;
+    static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;  // signalling NaN
+    static constexpr int NQP = 38;                    // padded factor row: conflict-free 16-byte reads
 };
 template <> struct Bits<float> {
     using U = unsigned int;
     static constexpr U SENT = 0x7FA5C0DEu;
+    static constexpr int NQP = 36;
+};
+
+// Stage layout (in elements of T): factor [32][NQP] | vector [32][4] | edge j [4][4] | edge k [8][4]
+template <typename T> struct Stage {
+    static constexpr int F = 32 * Bits<T>::NQP;
+    static constexpr int V = 32 * 4;
+    static constexpr int EJ = TK * 4;
+    static constexpr int EK = TJ * 4;
+    static constexpr int SIZE = F + V + EJ + EK;
+    static constexpr unsigned FB = F * sizeof(T), VB = V * sizeof(T), EJB = EJ * sizeof(T), EKB = EK * sizeof(T);
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -57,20 +70,17 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)_
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -80,7 +90,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-
 __device__ __forceinline__ uint64_t global_timer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -97,112 +106,118 @@ __device__ __forceinline__ unsigned ld_relaxed(const float *p) {
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_relaxed_bits(double *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(double *p, double v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
 }
-__device__ __forceinline__ void st_relaxed_bits(float *p, unsigned v) {
-    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(float *p, float v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
 }
-__device__ __forceinline__ unsigned long long to_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
-__device__ __forceinline__ unsigned to_bits(float v) { return __float_as_uint(v); }
-__device__ __forceinline__ double from_bits(unsigned long long v) { return __longlong_as_double((long long)v); }
-__device__ __forceinline__ float from_bits(unsigned v) { return __uint_as_float(v); }
+__device__ __forceinline__ unsigned long long bits_of(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned bits_of(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ double value_of(unsigned long long v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ float value_of(unsigned v) { return __uint_as_float(v); }
 
 template <typename T>
 struct SweepArgs {
-    int nx, ny, nz, nT, S;
-    const int2 *order;         // tile (J, K) per position
-    const T *F;                // packed factor chunks [nT][S][36][32]
-    const T *in;               // forward: r; backward: y
-    T *out;                    // forward: y; backward: z
-    T *reset;                  // forward: z (gets the sentinel); backward: y (gets the sentinel)
+    int nx, ny, nz, nT, nTK, S;
+    const int2 *order;   // position -> tile (J, K)
+    const int *pos_of;   // J * nTK + K -> position
+    const T *F;          // factor rows [nT][S][32][NQP]
+    const T *V;          // input vector in tile order [nT][S][32][4]
+    T *Vnext;            // forward: y in backward tile order [nT][S][32][4]; backward: null
+    T *z;                // backward: output in natural order; forward: null
+    T *EJ, *EK;          // edge buffers this sweep publishes [nT][S][TK][4], [nT][S][TJ][4]
+    T *EJnext, *EKnext;  // forward: the backward sweep's edge buffers (reset to the sentinel)
     const int *done;
     int *status;
     unsigned long long timeout_ns;
 };
 
-// Wait until the three components at p are published (not the sentinel).
+// Re-read a staged neighbour value that was still the sentinel.
 template <typename T>
-__device__ __forceinline__ bool poll3(const T *p, typename Bits<T>::U v[3], uint64_t deadline) {
-    for (int e = 0; e < 3; ++e) {
-        unsigned spins = 0;
-        while (v[e] == Bits<T>::SENT) {
-            v[e] = ld_relaxed(p + e);
-            if ((++spins & 255u) == 0 && global_timer() > deadline) return false;
-        }
+__device__ __forceinline__ bool poll3(const T *g, T v[3], uint64_t deadline) {
+    using U = typename Bits<T>::U;
+    unsigned spins = 0;
+    for (;;) {
+        U b0 = bits_of(v[0]), b1 = bits_of(v[1]), b2 = bits_of(v[2]);
+        if (b0 != Bits<T>::SENT && b1 != Bits<T>::SENT && b2 != Bits<T>::SENT) return true;
+        b0 = ld_relaxed(g);
+        b1 = ld_relaxed(g + 1);
+        b2 = ld_relaxed(g + 2);
+        v[0] = value_of(b0);
+        v[1] = value_of(b1);
+        v[2] = value_of(b2);
+        if ((++spins & 63u) == 0 && global_timer() > deadline) return false;
     }
-    return true;
 }
 
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
-    using U = typename Bits<T>::U;
-    constexpr unsigned CHUNK_BYTES = CHUNK * sizeof(T);
+    using St = Stage<T>;
+    constexpr int NQP = Bits<T>::NQP;
     if (P.done && *(volatile const int *)P.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     T *ring = reinterpret_cast<T *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * CHUNK_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * St::SIZE * sizeof(T));
     const int lane = threadIdx.x;
     const int a = lane & 7, b = lane >> 3;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const int64_t sj = nx, sk = (int64_t)nx * ny;
+    const int nx = P.nx, ny = P.ny, nz = P.nz, S = P.S;
     if (lane == 0) {
         for (int q = 0; q < NS; ++q) mbar_init(&bars[q], 1);
         fence_barrier_init();
     }
     __syncwarp();
-    unsigned phase = 0;  // parity bit per ring stage
+    unsigned phase = 0, pending = 0;
     const uint64_t deadline = global_timer() + P.timeout_ns;
     bool failed = false;
+    const int nTJ = (ny + TJ - 1) / TJ;
 
-    unsigned pending = 0;  // ring stages with a bulk copy in flight (tracked by lane 0)
     for (int t = blockIdx.x; t < P.nT && !failed; t += gridDim.x) {
-        // forward: tiles in increasing J+K; backward: decreasing (a tile only waits for earlier ones)
         const int tt = FWD ? t : (P.nT - 1 - t);
         const int2 JK = P.order[tt];
+        // producers of this tile's edge inputs
+        const int pj = FWD ? (JK.x > 0 ? P.pos_of[(JK.x - 1) * P.nTK + JK.y] : -1)
+                           : (JK.x + 1 < nTJ ? P.pos_of[(JK.x + 1) * P.nTK + JK.y] : -1);
+        const int pk = FWD ? (JK.y > 0 ? P.pos_of[JK.x * P.nTK + JK.y - 1] : -1)
+                           : (JK.y + 1 < P.nTK ? P.pos_of[JK.x * P.nTK + JK.y + 1] : -1);
         const int j = JK.x * TJ + a, k = JK.y * TK + b;
         const bool jk_ok = (j < ny) && (k < nz);
-        const T *Ft = P.F + (size_t)tt * P.S * CHUNK;
-        const int S = P.S;
-        // direction-dependent geometry
-        const int aoff = FWD ? a : (TJ - 1 - a);
-        const int boff = FWD ? b : (TK - 1 - b);
-        // in-tile neighbour lanes and whether this lane's neighbour lies in another tile
-        const int lane_j = FWD ? lane - 1 : lane + 1;      // j -/+ 1
-        const int lane_k = FWD ? lane - 8 : lane + 8;      // k -/+ 1
-        const bool edge_j = FWD ? (a == 0) : (a == TJ - 1);
-        const bool edge_k = FWD ? (b == 0) : (b == TK - 1);
         const bool has_j = FWD ? (j > 0) : (j + 1 < ny);
         const bool has_k = FWD ? (k > 0) : (k + 1 < nz);
-        const int64_t dj = FWD ? -sj : sj, dk = FWD ? -sk : sk;
-
-        auto cell_i = [&](int s) { return FWD ? (s - aoff - boff) : (nx - 1 - (s - aoff - boff)); };
-        auto cell_valid = [&](int s) {
-            const int i = cell_i(s);
-            return jk_ok && i >= 0 && i < nx;
+        const bool edge_j = FWD ? (a == 0) : (a == TJ - 1);
+        const bool edge_k = FWD ? (b == 0) : (b == TK - 1);
+        const bool pub_j = FWD ? (a == TJ - 1) : (a == 0);  // this lane's results feed the next tile in j
+        const bool pub_k = FWD ? (b == TK - 1) : (b == 0);
+        const int lane_j = (FWD ? lane - 1 : lane + 1) & 31;
+        const int lane_k = (FWD ? lane - 8 : lane + 8) & 31;
+        const int off = FWD ? (a + b) : ((TJ - 1 - a) + (TK - 1 - b));
+        const int64_t base = (int64_t)k * nx * ny + (int64_t)j * nx;
+        const size_t tile0 = (size_t)tt * S;
+        const T *Ft = P.F + tile0 * St::F;
+        const T *Vt = P.V + tile0 * St::V;
+        const T *EJsrc = pj >= 0 ? P.EJ + (size_t)pj * S * St::EJ : nullptr;
+        const T *EKsrc = pk >= 0 ? P.EK + (size_t)pk * S * St::EK : nullptr;
+        if (FWD) {
+            // this tile's backward-sweep edge buffers start at the sentinel
+            using U = typename Bits<T>::U;
+            U *ej = reinterpret_cast<U *>(P.EJnext + tile0 * St::EJ);
+            U *ek = reinterpret_cast<U *>(P.EKnext + tile0 * St::EK);
+            for (int q = lane; q < S * St::EJ; q += 32) ej[q] = Bits<T>::SENT;
+            for (int q = lane; q < S * St::EK; q += 32) ek[q] = Bits<T>::SENT;
+        }
+        const unsigned stage_bytes = St::FB + St::VB + (pj >= 0 ? St::EJB : 0u) + (pk >= 0 ? St::EKB : 0u);
+        auto issue = [&](int s, int st) {
+            T *dst = ring + st * St::SIZE;
+            mbar_expect(&bars[st], stage_bytes);
+            tma_load_1d(dst, Ft + (size_t)s * St::F, St::FB, &bars[st]);
+            tma_load_1d(dst + St::F, Vt + (size_t)s * St::V, St::VB, &bars[st]);
+            if (pj >= 0) tma_load_1d(dst + St::F + St::V, EJsrc + (size_t)s * St::EJ, St::EJB, &bars[st]);
+            if (pk >= 0) tma_load_1d(dst + St::F + St::V + St::EJ, EKsrc + (size_t)s * St::EK, St::EKB, &bars[st]);
+            pending |= 1u << st;
         };
-        auto cell_of = [&](int s) { return (int64_t)k * sk + (int64_t)j * sj + cell_i(s); };
-
-        // prologue: factor chunks 0..NS-2, vector prefetch for steps 0..NS-1
         if (lane == 0) {
             fence_proxy_async();
-            for (int q = 0; q < NS - 1 && q < S; ++q) {
-                tma_load_1d(ring + q * CHUNK, Ft + (size_t)q * CHUNK, CHUNK_BYTES, &bars[q]);
-                pending |= 1u << q;
-            }
-        }
-        T vin[NS][3];
-        U rj[NS][3], rk[NS][3];
-#pragma unroll
-        for (int u = 0; u < NS; ++u) {
-            const bool v = u < S && cell_valid(u);
-            const int64_t c = v ? cell_of(u) : 0;
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                vin[u][e] = v ? P.in[3 * c + e] : T(0);
-                rj[u][e] = (v && edge_j && has_j) ? ld_relaxed(P.out + 3 * (c + dj) + e) : U(0);
-                rk[u][e] = (v && edge_k && has_k) ? ld_relaxed(P.out + 3 * (c + dk) + e) : U(0);
-            }
+            for (int q = 0; q < NS - 1 && q < S; ++q) issue(q, q);
         }
         T prev[3] = {T(0), T(0), T(0)};
 
@@ -211,35 +226,24 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
             for (int u = 0; u < NS; ++u) {
                 const int s = s0 + u;
                 if (s >= S) break;
-                // refill the stage freed by step s-1
                 if (lane == 0 && s + NS - 1 < S) {
-                    const int st = (u + NS - 1) % NS;
                     fence_proxy_async();
-                    tma_load_1d(ring + st * CHUNK, Ft + (size_t)(s + NS - 1) * CHUNK, CHUNK_BYTES, &bars[st]);
-                    pending |= 1u << st;
+                    issue(s + NS - 1, (u + NS - 1) % NS);
                 }
-                const bool valid = cell_valid(s);
-                const int64_t c = valid ? cell_of(s) : 0;
-                // neighbours: shuffles of the previous step's results
-                T nj[3], nk[3];
+                const int i = FWD ? (s - off) : (nx - 1 - (s - off));
+                const bool valid = jk_ok && i >= 0 && i < nx;
+                const bool has_i = FWD ? (i > 0) : (i < nx - 1);
+                // in-tile neighbours: previous step's results of the adjacent lanes
+                T nj[3], nk[3], own[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    const T sjv = __shfl_sync(0xffffffffu, prev[e], lane_j & 31);
-                    const T skv = __shfl_sync(0xffffffffu, prev[e], lane_k & 31);
-                    nj[e] = has_j ? sjv : T(0);
-                    nk[e] = has_k ? skv : T(0);
+                    const T vj = __shfl_sync(0xffffffffu, prev[e], lane_j);
+                    const T vk = __shfl_sync(0xffffffffu, prev[e], lane_k);
+                    nj[e] = has_j ? vj : T(0);
+                    nk[e] = has_k ? vk : T(0);
+                    own[e] = has_i ? prev[e] : T(0);
                 }
-                if (valid && edge_j && has_j) {
-                    if (!poll3(P.out + 3 * (c + dj), rj[u], deadline)) failed = true;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) nj[e] = from_bits(rj[u][e]);
-                }
-                if (valid && edge_k && has_k) {
-                    if (!poll3(P.out + 3 * (c + dk), rk[u], deadline)) failed = true;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) nk[e] = from_bits(rk[u][e]);
-                }
-                // factor chunk of this step
+                // wait for this step's stage
                 {
                     unsigned spins = 0;
                     bool landed = true;
@@ -255,54 +259,104 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                         pending &= ~(1u << u);
                     }
                 }
-                const T *Fs = ring + u * CHUNK + lane;
-                const bool has_i = FWD ? (cell_i(s) > 0) : (cell_i(s) < nx - 1);
-                T own[3];
+                const T *stg = ring + u * St::SIZE;
+                if (valid && edge_j && has_j) {
+                    const T *e4 = stg + St::F + St::V + b * 4;
+                    T v3[3] = {e4[0], e4[1], e4[2]};
+                    if (!poll3(P.EJ + ((size_t)pj * S + s) * St::EJ + b * 4, v3, deadline)) failed = true;
+                    nj[0] = v3[0];
+                    nj[1] = v3[1];
+                    nj[2] = v3[2];
+                }
+                if (valid && edge_k && has_k) {
+                    const T *e4 = stg + St::F + St::V + St::EJ + a * 4;
+                    T v3[3] = {e4[0], e4[1], e4[2]};
+                    if (!poll3(P.EK + ((size_t)pk * S + s) * St::EK + a * 4, v3, deadline)) failed = true;
+                    nk[0] = v3[0];
+                    nk[1] = v3[1];
+                    nk[2] = v3[2];
+                }
+                // factor row and input of this lane
+                T f[NQP];
+                {
+                    const T *row = stg + lane * NQP;
+                    if (sizeof(T) == 4) {
 #pragma unroll
-                for (int e = 0; e < 3; ++e) own[e] = has_i ? prev[e] : T(0);
-                // slots: FWD  [0] -z  [1] -y  [2] -x ;  BWD  [0] +x  [1] +y  [2] +z
-                const T *xs0 = FWD ? nk : own;
-                const T *xs2 = FWD ? own : nk;
+                        for (int q = 0; q < 9; ++q) {
+                            const float4 v4 = reinterpret_cast<const float4 *>(row)[q];
+                            f[4 * q] = v4.x;
+                            f[4 * q + 1] = v4.y;
+                            f[4 * q + 2] = v4.z;
+                            f[4 * q + 3] = v4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 18; ++q) {
+                            const double2 v2 = reinterpret_cast<const double2 *>(row)[q];
+                            f[2 * q] = v2.x;
+                            f[2 * q + 1] = v2.y;
+                        }
+                    }
+                }
+                T vin[3];
+                {
+                    const T *v4 = stg + St::F + lane * 4;
+                    vin[0] = v4[0];
+                    vin[1] = v4[1];
+                    vin[2] = v4[2];
+                }
+                // slots: forward [0] -z [1] -y [2] -x ; backward [0] +x [1] +y [2] +z
+                const T *x0 = FWD ? nk : own;
+                const T *x2 = FWD ? own : nk;
                 T acc[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    T sum = T(0);
-#pragma unroll
-                    for (int f = 0; f < 3; ++f) {
-                        sum = fma(Fs[(0 * 9 + 3 * e + f) * 32], xs0[f], sum);
-                        sum = fma(Fs[(1 * 9 + 3 * e + f) * 32], nj[f], sum);
-                        sum = fma(Fs[(2 * 9 + 3 * e + f) * 32], xs2[f], sum);
-                    }
-                    acc[e] = FWD ? (vin[u][e] - sum) : sum;
+                    T p0 = f[3 * e] * x0[0];
+                    T p1 = f[9 + 3 * e] * nj[0];
+                    T p2 = f[18 + 3 * e] * x2[0];
+                    p0 = fma(f[3 * e + 1], x0[1], p0);
+                    p1 = fma(f[9 + 3 * e + 1], nj[1], p1);
+                    p2 = fma(f[18 + 3 * e + 1], x2[1], p2);
+                    p0 = fma(f[3 * e + 2], x0[2], p0);
+                    p1 = fma(f[9 + 3 * e + 2], nj[2], p1);
+                    p2 = fma(f[18 + 3 * e + 2], x2[2], p2);
+                    const T sum = (p0 + p1) + p2;
+                    acc[e] = FWD ? (vin[e] - sum) : sum;
                 }
                 T res[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    const T d = Fs[(27 + 3 * e) * 32] * acc[0] + Fs[(28 + 3 * e) * 32] * acc[1] +
-                                Fs[(29 + 3 * e) * 32] * acc[2];
-                    res[e] = FWD ? d : (vin[u][e] - d);
+                    const T d = fma(f[27 + 3 * e + 2], acc[2], fma(f[27 + 3 * e + 1], acc[1], f[27 + 3 * e] * acc[0]));
+                    res[e] = FWD ? d : (vin[e] - d);
                 }
                 if (valid) {
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        st_relaxed_bits(P.out + 3 * c + e, to_bits(res[e]));
-                        st_relaxed_bits(P.reset + 3 * c + e, Bits<T>::SENT);
+                    if (FWD) {
+                        T *o = P.Vnext + ((tile0 + (S - 1 - s)) * 32 + lane) * 4;
+                        o[0] = res[0];
+                        o[1] = res[1];
+                        o[2] = res[2];
+                    } else {
+                        T *o = P.z + 3 * (base + i);
+                        o[0] = res[0];
+                        o[1] = res[1];
+                        o[2] = res[2];
+                    }
+                    const int sj = s - (TJ - 1), sk = s - (TK - 1);
+                    if (pub_j && sj >= 0) {
+                        T *o = P.EJ + ((tile0 + sj) * TK + b) * 4;
+                        st_relaxed(o, res[0]);
+                        st_relaxed(o + 1, res[1]);
+                        st_relaxed(o + 2, res[2]);
+                    }
+                    if (pub_k && sk >= 0) {
+                        T *o = P.EK + ((tile0 + sk) * TJ + a) * 4;
+                        st_relaxed(o, res[0]);
+                        st_relaxed(o + 1, res[1]);
+                        st_relaxed(o + 2, res[2]);
                     }
                 }
 #pragma unroll
                 for (int e = 0; e < 3; ++e) prev[e] = valid ? res[e] : T(0);
-                // prefetch the vectors of step s + NS into this slot
-                {
-                    const int sn = s + NS;
-                    const bool vn = sn < S && cell_valid(sn);
-                    const int64_t cn = vn ? cell_of(sn) : 0;
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        vin[u][e] = vn ? P.in[3 * cn + e] : T(0);
-                        rj[u][e] = (vn && edge_j && has_j) ? ld_relaxed(P.out + 3 * (cn + dj) + e) : U(0);
-                        rk[u][e] = (vn && edge_k && has_k) ? ld_relaxed(P.out + 3 * (cn + dk) + e) : U(0);
-                    }
-                }
                 __syncwarp();
             }
             if (__any_sync(0xffffffffu, failed)) {
@@ -312,9 +366,9 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         }
     }
     if (failed) {
-        if (lane == 0) atomicCAS(P.status, 0, (int)RSV_ETIMEOUT);
-        // let copies still in flight land before the CTA exits (bounded)
         if (lane == 0) {
+            atomicCAS(P.status, 0, (int)RSV_ETIMEOUT);
+            // let copies still in flight land before the CTA exits (bounded)
             const uint64_t limit = global_timer() + 1000000000ull;
             for (int q = 0; q < NS; ++q)
                 if (pending & (1u << q))
@@ -325,13 +379,14 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     }
 }
 
-// Pack the factor into warp-step chunks.  One thread per (tile, step, lane).
-// Block values come from `v` (FP64, or the FP32 copy for mixed precision);
-// D^{-1} from the FP64 factor; both are stored as T.
+// Factor rows in warp-step order.  One thread per (tile, step, lane).  Block
+// values come from `v` (FP64, or the FP32 copy for mixed precision); D^{-1}
+// from the FP64 factor; both are stored as T.
 template <typename T, typename Tv>
 __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__restrict__ order,
                            const int32_t *__restrict__ rp, const Tv *__restrict__ v,
                            const double *__restrict__ dinv, T *__restrict__ Ff, T *__restrict__ Fb) {
+    constexpr int NQP = Bits<T>::NQP;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)nT * S * 32;
     if (gid >= total) return;
@@ -344,12 +399,10 @@ __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__
     for (int dir = 0; dir < 2; ++dir) {
         const bool fwd = dir == 0;
         const int i = fwd ? (s - a - b) : (nx - 1 - (s - (TJ - 1 - a) - (TK - 1 - b)));
-        T *out = (fwd ? Ff : Fb) + ((size_t)t * S + s) * CHUNK + lane;
+        T *out = (fwd ? Ff : Fb) + (((size_t)t * S + s) * 32 + lane) * NQP;
         const bool valid = j < ny && k < nz && i >= 0 && i < nx;
-        if (!valid) {
-            for (int q = 0; q < NQ; ++q) out[q * 32] = T(0);
-            continue;
-        }
+        for (int q = 0; q < NQP; ++q) out[q] = T(0);
+        if (!valid) continue;
         const int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
         // slots of the row: -z, -y, -x, self, +x, +y, +z (absent faces skipped)
         int q = 0, mz = -1, my = -1, mx = -1, px = -1, py = -1, pz = -1;
@@ -362,55 +415,96 @@ __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__
         if (k < nz - 1) pz = q++;
         const int sl[3] = {fwd ? mz : px, fwd ? my : py, fwd ? mx : pz};
         for (int blk = 0; blk < 3; ++blk)
-            for (int e = 0; e < 9; ++e)
-                out[(blk * 9 + e) * 32] = sl[blk] >= 0 ? (T)v[9 * ((int64_t)rp[c] + sl[blk]) + e] : T(0);
-        for (int e = 0; e < 9; ++e) out[(27 + e) * 32] = (T)dinv[9 * c + e];
+            if (sl[blk] >= 0)
+                for (int e = 0; e < 9; ++e) out[blk * 9 + e] = (T)v[9 * ((int64_t)rp[c] + sl[blk]) + e];
+        for (int e = 0; e < 9; ++e) out[27 + e] = (T)dinv[9 * c + e];
     }
 }
 
+// Before a forward sweep: r into tile order, and the forward edge buffers to
+// the sentinel.  One thread per (tile, step, lane).
 template <typename T>
-__global__ void fill_sentinel(int64_t n, T *p) {
+__global__ void gather_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__restrict__ order,
+                             const T *__restrict__ r, T *__restrict__ Vt, T *__restrict__ EJ, T *__restrict__ EK) {
     using U = typename Bits<T>::U;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        reinterpret_cast<U *>(p)[i] = Bits<T>::SENT;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)nT * S * 32;
+    if (gid >= total) return;
+    const int lane = (int)(gid & 31);
+    const int s = (int)((gid >> 5) % S);
+    const int t = (int)((gid >> 5) / S);
+    const int a = lane & 7, b = lane >> 3;
+    const int2 JK = order[t];
+    const int j = JK.x * TJ + a, k = JK.y * TK + b, i = s - a - b;
+    T *o = Vt + (((size_t)t * S + s) * 32 + lane) * 4;
+    if (j < ny && k < nz && i >= 0 && i < nx) {
+        const int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
+        o[0] = r[3 * c];
+        o[1] = r[3 * c + 1];
+        o[2] = r[3 * c + 2];
+    } else {
+        o[0] = o[1] = o[2] = T(0);
+    }
+    o[3] = T(0);
+    // edge buffers [t][s][TK][4] and [t][s][TJ][4]: the 32 threads of a (t, s) row
+    // cover its 16 + 32 entries
+    const size_t row = (size_t)t * S + s;
+    if (lane < TK * 4) reinterpret_cast<U *>(EJ)[row * TK * 4 + lane] = Bits<T>::SENT;
+    reinterpret_cast<U *>(EK)[row * TJ * 4 + lane] = Bits<T>::SENT;
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_) {
-    IluTiles *Tl = T_;
+cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
+    using St = Stage<T>;
     const int nx = A->nx, ny = A->ny, nz = A->nz;
     const int nTJ = (ny + TJ - 1) / TJ, nTK = (nz + TK - 1) / TK;
     const int nT = nTJ * nTK;
     const int S = nx + TJ + TK - 2;
-    const size_t chunk_bytes = CHUNK * sizeof(T);
     cudaError_t e = cudaSuccess;
     if (!Tl->Ff || Tl->nT != nT || Tl->S != S || Tl->elem != (int)sizeof(T)) {
         free_tiles(Tl);
         std::vector<int2> order;
+        std::vector<int> pos(nT);
         order.reserve(nT);
         for (int d = 0; d <= nTJ + nTK - 2; ++d)
             for (int J = 0; J < nTJ; ++J) {
                 const int K = d - J;
-                if (K >= 0 && K < nTK) order.push_back(make_int2(J, K));
+                if (K >= 0 && K < nTK) {
+                    pos[J * nTK + K] = (int)order.size();
+                    order.push_back(make_int2(J, K));
+                }
             }
         Tl->nT = nT;
         Tl->S = S;
+        Tl->nTK = nTK;
         Tl->elem = (int)sizeof(T);
-        const size_t fbytes = (size_t)nT * S * chunk_bytes;
-        if ((e = cudaMalloc(&Tl->Ff, fbytes)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&Tl->Fb, fbytes)) != cudaSuccess) return e;
-        if ((e = cudaMalloc((void **)&Tl->order, sizeof(int2) * nT)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&Tl->scratch, sizeof(T) * 3 * std::max<int64_t>(A->nb, 1))) != cudaSuccess) return e;
+        const size_t rows = (size_t)nT * S;
+        auto alloc = [&](void **p, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        };
+        alloc(&Tl->Ff, rows * St::FB);
+        alloc(&Tl->Fb, rows * St::FB);
+        alloc(&Tl->Vf, rows * St::VB);
+        alloc(&Tl->Vb, rows * St::VB);
+        alloc(&Tl->EJf, rows * St::EJB);
+        alloc(&Tl->EKf, rows * St::EKB);
+        alloc(&Tl->EJb, rows * St::EJB);
+        alloc(&Tl->EKb, rows * St::EKB);
+        alloc((void **)&Tl->order, sizeof(int2) * nT);
+        alloc((void **)&Tl->pos_of, sizeof(int) * nT);
+        if (e != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(Tl->order, order.data(), sizeof(int2) * nT, cudaMemcpyHostToDevice, A->stream)) !=
-            cudaSuccess)
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(Tl->pos_of, pos.data(), sizeof(int) * nT, cudaMemcpyHostToDevice, A->stream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(A->stream)) != cudaSuccess)
             return e;
-        if ((e = cudaStreamSynchronize(A->stream)) != cudaSuccess) return e;
         int dev = 0, sms = 0, per_f = 0, per_b = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = NS * chunk_bytes + NS * sizeof(uint64_t);
+        const size_t smem = NS * St::SIZE * sizeof(T) + NS * sizeof(uint64_t);
         if ((e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
@@ -433,41 +527,35 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_) {
     else
         pack_tiles<T, float><<<g, 256, 0, A->stream>>>(nx, ny, nz, nT, S, Tl->order, A->d_rp, A->d_v32, dinv,
                                                        (T *)Tl->Ff, (T *)Tl->Fb);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return reset_tiles_scratch(A, Tl);
-}
-
-cudaError_t reset_tiles_scratch(const rsv_mat *A, IluTiles *Tl) {
-    const int64_t n = 3 * A->nb;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
-    rsv::count_launches(1);
-    if (Tl->elem == 8)
-        fill_sentinel<double><<<g, 256, 0, A->stream>>>(n, (double *)Tl->scratch);
-    else
-        fill_sentinel<float><<<g, 256, 0, A->stream>>>(n, (float *)Tl->scratch);
     return cudaGetLastError();
 }
 
 void free_tiles(IluTiles *Tl) {
-    if (Tl->Ff) cudaFree(Tl->Ff);
-    if (Tl->Fb) cudaFree(Tl->Fb);
-    if (Tl->order) cudaFree(Tl->order);
-    if (Tl->scratch) cudaFree(Tl->scratch);
+    for (void *p : {Tl->Ff, Tl->Fb, Tl->Vf, Tl->Vb, Tl->EJf, Tl->EKf, Tl->EJb, Tl->EKb, (void *)Tl->order,
+                    (void *)Tl->pos_of})
+        if (p) cudaFree(p);
     *Tl = IluTiles();
 }
 
 template <typename T>
 cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &Tl, const T *r, T *z, const int *done,
                                    int *status, unsigned long long timeout_ns) {
-    SweepArgs<T> f{A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, (const T *)Tl.Ff, r, (T *)Tl.scratch, z,
+    const int64_t total = (int64_t)Tl.nT * Tl.S * 32;
+    rsv::count_launches(3);
+    gather_tiles<T><<<(unsigned)((total + 255) / 256), 256, 0, A->stream>>>(
+        A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, r, (T *)Tl.Vf, (T *)Tl.EJf, (T *)Tl.EKf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    SweepArgs<T> f{A->nx, A->ny, A->nz, Tl.nT, Tl.nTK, Tl.S, Tl.order, Tl.pos_of, (const T *)Tl.Ff,
+                   (const T *)Tl.Vf, (T *)Tl.Vb, nullptr, (T *)Tl.EJf, (T *)Tl.EKf, (T *)Tl.EJb, (T *)Tl.EKb,
                    done, status, timeout_ns};
-    SweepArgs<T> bw{A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, (const T *)Tl.Fb, (const T *)Tl.scratch, z,
-                    (T *)Tl.scratch, done, status, timeout_ns};
+    SweepArgs<T> bw{A->nx, A->ny, A->nz, Tl.nT, Tl.nTK, Tl.S, Tl.order, Tl.pos_of, (const T *)Tl.Fb,
+                    (const T *)Tl.Vb, nullptr, z, (T *)Tl.EJb, (T *)Tl.EKb, nullptr, nullptr,
+                    done, status, timeout_ns};
     void *fa[] = {&f};
     void *ba[] = {&bw};
-    rsv::count_launches(2);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<T, true>, dim3(Tl.grid), dim3(32), fa,
-                                                Tl.smem, A->stream);
+    e = cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<T, true>, dim3(Tl.grid), dim3(32), fa, Tl.smem,
+                                    A->stream);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)ilu_sweep_tiles<T, false>, dim3(Tl.grid), dim3(32), ba, Tl.smem,
                                        A->stream);

@@ -213,7 +213,6 @@ struct rsv_solver {
     float *dinv32 = nullptr;     // FP32 copy for mixed block Jacobi
     Schedule sch;
     IluTiles tiles;
-    bool scratch_dirty = false;  // a sweep timed out: its sentinel scratch must be refilled
     double ms_setup = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -550,7 +549,6 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
             RSV_CUDA_TRY(tiles_setup<float>(A, s->dinv, &s->tiles));
         else
             RSV_CUDA_TRY(tiles_setup<double>(A, s->dinv, &s->tiles));
-        s->scratch_dirty = false;
     }
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
@@ -607,10 +605,6 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
         dx = s->d_x;
     }
     RSV_CUDA_TRY(cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
-    if (s->scratch_dirty && s->tiles.scratch) {
-        RSV_CUDA_TRY(reset_tiles_scratch(s->A, &s->tiles));
-        s->scratch_dirty = false;
-    }
     double bnorm = 0.0;
     RSV_CUDA_TRY(launch_dot<double>(s->st, n, db, db, s->partial, &s->ds->bnorm, &s->ds->counter[0], 1, nullptr));
     RSV_CUDA_TRY(cudaMemcpyAsync(&bnorm, &s->ds->bnorm, sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -622,7 +616,6 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
     rsv_solve_info local{};
     rsv_status st = s->mixed ? solve_mixed(s, db, dx, tol, &local) : solve_fp64(s, db, dx, tol, &local);
     if (st == RSV_ECUDA || st == RSV_ENOMEM) return st;
-    if (st == RSV_ETIMEOUT) s->scratch_dirty = true;
     // FP64 true residual, recomputed; the iteration count from the device
     double rn = 0.0;
     int iters = 0;
