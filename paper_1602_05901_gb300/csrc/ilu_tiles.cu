@@ -10,8 +10,9 @@
 // step earlier and arrive by warp shuffle; the -x neighbour is the lane's own
 // previous result.
 //
-// Everything else a step needs arrives through one shared-memory ring filled
-// by TMA bulk copies (cp.async.bulk + mbarrier) NS - 1 steps ahead:
+// Everything else a step needs arrives through shared-memory rings filled by
+// TMA bulk copies (cp.async.bulk + mbarrier): a deep data ring (NSD - 1 steps
+// ahead, hiding HBM latency) and a shallow edge ring (NSE - 1 steps ahead):
 //   * the factor row of each lane (three off-diagonal blocks and D^{-1}, 36
 //     values, packed at setup in exactly the order the warp reads them);
 //   * the input vector, gathered into the same tile order before the sweep;
@@ -41,27 +42,32 @@ namespace rsv {
 namespace {
 
 constexpr int TJ = 8, TK = 4;
-constexpr int NS = 4;  // ring stages; copies run NS - 1 steps ahead
+constexpr int NSE = 3;  // edge ring stages: neighbour values are copied NSE - 1 steps ahead
 
 template <typename T> struct Bits;
 template <> struct Bits<double> {
     using U = unsigned long long;
     static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;  // signalling NaN
     static constexpr int NQP = 38;                    // padded factor row: conflict-free 16-byte reads
+    static constexpr int NSD = 6;                     // data ring stages (copies NSD - 1 steps ahead)
 };
 template <> struct Bits<float> {
     using U = unsigned int;
     static constexpr U SENT = 0x7FA5C0DEu;
     static constexpr int NQP = 36;
+    static constexpr int NSD = 10;
 };
 
-// Stage layout (in elements of T): factor [32][NQP] | vector [32][4] | edge j [4][4] | edge k [8][4]
+// Data ring stage: factor [32][NQP] | vector [32][4].  Edge ring stage: edge j [4][4] | edge k [8][4].
+// The data ring runs deep (hides HBM latency); the edge ring runs shallow, so that
+// neighbour values are copied as late as possible and are mostly already published.
 template <typename T> struct Stage {
     static constexpr int F = 32 * Bits<T>::NQP;
     static constexpr int V = 32 * 4;
     static constexpr int EJ = TK * 4;
     static constexpr int EK = TJ * 4;
-    static constexpr int SIZE = F + V + EJ + EK;
+    static constexpr int SIZE = F + V;
+    static constexpr int ESIZE = EJ + EK;
     static constexpr unsigned FB = F * sizeof(T), VB = V * sizeof(T), EJB = EJ * sizeof(T), EKB = EK * sizeof(T);
 };
 
@@ -155,19 +161,22 @@ template <typename T, bool FWD>
 __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     using St = Stage<T>;
     constexpr int NQP = Bits<T>::NQP;
+    constexpr int NSD = Bits<T>::NSD;
     if (P.done && *(volatile const int *)P.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    T *ring = reinterpret_cast<T *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * St::SIZE * sizeof(T));
+    T *ring = reinterpret_cast<T *>(smem);                       // NSD data stages
+    T *ering = ring + NSD * St::SIZE;                            // NSE edge stages
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ering + NSE * St::ESIZE);  // NSD data + NSE edge barriers
+    uint64_t *ebars = bars + NSD;
     const int lane = threadIdx.x;
     const int a = lane & 7, b = lane >> 3;
     const int nx = P.nx, ny = P.ny, nz = P.nz, S = P.S;
     if (lane == 0) {
-        for (int q = 0; q < NS; ++q) mbar_init(&bars[q], 1);
+        for (int q = 0; q < NSD + NSE; ++q) mbar_init(&bars[q], 1);
         fence_barrier_init();
     }
     __syncwarp();
-    unsigned phase = 0, pending = 0;
+    unsigned phase = 0, pending = 0;  // bit q: data stage q; bit NSD + q: edge stage q
     const uint64_t deadline = global_timer() + P.timeout_ns;
     bool failed = false;
     const int nTJ = (ny + TJ - 1) / TJ;
@@ -205,30 +214,50 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
             for (int q = lane; q < S * St::EJ; q += 32) ej[q] = Bits<T>::SENT;
             for (int q = lane; q < S * St::EK; q += 32) ek[q] = Bits<T>::SENT;
         }
-        const unsigned stage_bytes = St::FB + St::VB + (pj >= 0 ? St::EJB : 0u) + (pk >= 0 ? St::EKB : 0u);
-        auto issue = [&](int s, int st) {
+        const bool edges = pj >= 0 || pk >= 0;
+        const unsigned edge_bytes = (pj >= 0 ? St::EJB : 0u) + (pk >= 0 ? St::EKB : 0u);
+        auto issue = [&](int s) {
+            const int st = s % NSD;
             T *dst = ring + st * St::SIZE;
-            mbar_expect(&bars[st], stage_bytes);
+            mbar_expect(&bars[st], St::FB + St::VB);
             tma_load_1d(dst, Ft + (size_t)s * St::F, St::FB, &bars[st]);
             tma_load_1d(dst + St::F, Vt + (size_t)s * St::V, St::VB, &bars[st]);
-            if (pj >= 0) tma_load_1d(dst + St::F + St::V, EJsrc + (size_t)s * St::EJ, St::EJB, &bars[st]);
-            if (pk >= 0) tma_load_1d(dst + St::F + St::V + St::EJ, EKsrc + (size_t)s * St::EK, St::EKB, &bars[st]);
             pending |= 1u << st;
+        };
+        auto issue_edges = [&](int s) {
+            if (!edges) return;
+            const int st = s % NSE;
+            T *dst = ering + st * St::ESIZE;
+            mbar_expect(&ebars[st], edge_bytes);
+            if (pj >= 0) tma_load_1d(dst, EJsrc + (size_t)s * St::EJ, St::EJB, &ebars[st]);
+            if (pk >= 0) tma_load_1d(dst + St::EJ, EKsrc + (size_t)s * St::EK, St::EKB, &ebars[st]);
+            pending |= 1u << (NSD + st);
+        };
+        auto wait_stage = [&](uint64_t *bar, int bit) {
+            unsigned spins = 0;
+            while (!mbar_try_wait(bar, (phase >> bit) & 1u)) {
+                if ((++spins & 1023u) == 0 && global_timer() > deadline) {
+                    failed = true;
+                    return;
+                }
+            }
+            phase ^= 1u << bit;
+            pending &= ~(1u << bit);
         };
         if (lane == 0) {
             fence_proxy_async();
-            for (int q = 0; q < NS - 1 && q < S; ++q) issue(q, q);
+            for (int q = 0; q < NSD - 1 && q < S; ++q) issue(q);
+            for (int q = 0; q < NSE - 1 && q < S; ++q) issue_edges(q);
         }
         T prev[3] = {T(0), T(0), T(0)};
 
-        for (int s0 = 0; s0 < S; s0 += NS) {
-#pragma unroll
-            for (int u = 0; u < NS; ++u) {
-                const int s = s0 + u;
-                if (s >= S) break;
-                if (lane == 0 && s + NS - 1 < S) {
+        for (int s0 = 0; s0 < S; s0 += 4) {
+#pragma unroll 1
+            for (int s = s0; s < s0 + 4 && s < S; ++s) {
+                if (lane == 0) {
                     fence_proxy_async();
-                    issue(s + NS - 1, (u + NS - 1) % NS);
+                    if (s + NSD - 1 < S) issue(s + NSD - 1);
+                    if (s + NSE - 1 < S) issue_edges(s + NSE - 1);
                 }
                 const int i = FWD ? (s - off) : (nx - 1 - (s - off));
                 const bool valid = jk_ok && i >= 0 && i < nx;
@@ -243,25 +272,13 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     nk[e] = has_k ? vk : T(0);
                     own[e] = has_i ? prev[e] : T(0);
                 }
-                // wait for this step's stage
-                {
-                    unsigned spins = 0;
-                    bool landed = true;
-                    while (!mbar_try_wait(&bars[u], (phase >> u) & 1u)) {
-                        if ((++spins & 1023u) == 0 && global_timer() > deadline) {
-                            failed = true;
-                            landed = false;
-                            break;
-                        }
-                    }
-                    if (landed) {
-                        phase ^= 1u << u;
-                        pending &= ~(1u << u);
-                    }
-                }
-                const T *stg = ring + u * St::SIZE;
+                // wait for this step's stages
+                wait_stage(&bars[s % NSD], s % NSD);
+                if (edges) wait_stage(&ebars[s % NSE], NSD + s % NSE);
+                const T *stg = ring + (s % NSD) * St::SIZE;
+                const T *estg = ering + (s % NSE) * St::ESIZE;
                 if (valid && edge_j && has_j) {
-                    const T *e4 = stg + St::F + St::V + b * 4;
+                    const T *e4 = estg + b * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
                     if (!poll3(P.EJ + ((size_t)pj * S + s) * St::EJ + b * 4, v3, deadline)) failed = true;
                     nj[0] = v3[0];
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     nj[2] = v3[2];
                 }
                 if (valid && edge_k && has_k) {
-                    const T *e4 = stg + St::F + St::V + St::EJ + a * 4;
+                    const T *e4 = estg + St::EJ + a * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
                     if (!poll3(P.EK + ((size_t)pk * S + s) * St::EK + a * 4, v3, deadline)) failed = true;
                     nk[0] = v3[0];
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
             atomicCAS(P.status, 0, (int)RSV_ETIMEOUT);
             // let copies still in flight land before the CTA exits (bounded)
             const uint64_t limit = global_timer() + 1000000000ull;
-            for (int q = 0; q < NS; ++q)
+            for (int q = 0; q < NSD + NSE; ++q)
                 if (pending & (1u << q))
                     while (!mbar_try_wait(&bars[q], (phase >> q) & 1u) && global_timer() < limit) {
                     }
@@ -504,7 +521,8 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
         int dev = 0, sms = 0, per_f = 0, per_b = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = NS * St::SIZE * sizeof(T) + NS * sizeof(uint64_t);
+        const size_t smem = (Bits<T>::NSD * St::SIZE + NSE * St::ESIZE) * sizeof(T) +
+                            (Bits<T>::NSD + NSE) * sizeof(uint64_t);
         if ((e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
