@@ -1,9 +1,19 @@
 // Vector algebra of the Krylov solvers (Section "Algebraic Operations":
 // y = a x + b y, <x,y>, ||x||), fused where a solver step allows it.
-// Vectors are FP64 or FP32 (the inner solves of mixed precision); every
-// reduction accumulates in FP64.  Reductions are deterministic: every CTA
-// writes one partial per output, and the last CTA to finish (ticket counter)
-// sums the partials in CTA order.
+//
+// Vectors are FP64, or FP32 in the inner solves of mixed precision.  Every
+// reduction is FP64-accurate: FP64 vectors accumulate with FP64 FMAs; FP32
+// vectors accumulate each thread's products in double-float form (an FP32
+// pair hi + lo updated with error-free transformations: the exact rounding
+// error of each product from an FMA, and of each addition from Knuth's
+// two-sum), which GB300 runs on its FP32 pipes instead of its much narrower
+// FP64 pipe.  Each thread's pair is then widened to FP64 for the block and
+// grid reductions.
+//
+// Reductions are deterministic: every CTA writes one partial per output, and
+// the last CTA to finish (ticket counter) sums the partials in CTA order.
+// Rows are processed as 16-byte vectors when every pointer and the basis
+// leading dimension allow it.
 #include "common.cuh"
 
 namespace rsv {
@@ -30,46 +40,102 @@ __device__ __forceinline__ bool last_cta(unsigned *counter) {
     return am_last;
 }
 
-// Product of two vector entries, exact in FP64 for FP32 inputs.
-template <typename T>
-__device__ __forceinline__ double prod(T a, T b) {
-    return (double)a * (double)b;
+// Sum of products, FP64-accurate.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);         // a*b = p + pe exactly
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));  // hi + p = s + err
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using V = float4;
+    static constexpr int N = 4;
+    __device__ __forceinline__ static float get(const float4 &v, int q) {
+        return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+    }
+    __device__ __forceinline__ static void set(float4 &v, int q, float x) {
+        if (q == 0) v.x = x; else if (q == 1) v.y = x; else if (q == 2) v.z = x; else v.w = x;
+    }
+};
+template <> struct Vec<double> {
+    using V = double2;
+    static constexpr int N = 2;
+    __device__ __forceinline__ static double get(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
+    __device__ __forceinline__ static void set(double2 &v, int q, double x) {
+        if (q == 0) v.x = x; else v.y = x;
+    }
+};
+
+// Block-reduce `v` (one value per thread per output slot) into partial[slot * grid + block].
+__device__ __forceinline__ void block_partial(double v, double *sm, double *partial, int slot) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kRedThreads / 32; ++q) s += sm[q];
+        partial[(int64_t)slot * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *__restrict__ w,
                                                            const T *__restrict__ V, int64_t ldv, int k,
                                                            double *partial, double *out, unsigned *counter,
                                                            const int *done) {
     if (is_done(done)) return;
-    __shared__ double sm[kGroup][kRedThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    using VT = Vec<T>;
+    __shared__ double sm[kRedThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int g0 = 0; g0 < k; g0 += kGroup) {
-        double acc[kGroup];
-#pragma unroll
-        for (int i = 0; i < kGroup; ++i) acc[i] = 0.0;
+        Acc<T> acc[kGroup];
         const int kg = min(kGroup, k - g0);
-        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
-            const T wr = w[r];
+        if (VEC) {
+            const int64_t nv = n / VT::N;
+            for (int64_t r = tid; r < nv; r += stride) {
+                const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
 #pragma unroll
-            for (int i = 0; i < kGroup; ++i)
-                if (i < kg) acc[i] += prod(wr, V[(int64_t)(g0 + i) * ldv + r]);
-        }
+                for (int i = 0; i < kGroup; ++i)
+                    if (i < kg) {
+                        const typename VT::V vr =
+                            reinterpret_cast<const typename VT::V *>(V + (int64_t)(g0 + i) * ldv)[r];
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i) {
-            if (i < kg) {
-                double s = warp_sum(acc[i]);
-                if (lane == 0) sm[i][warp] = s;
+                        for (int q = 0; q < VT::N; ++q) acc[i].add(VT::get(wr, q), VT::get(vr, q));
+                    }
+            }
+            for (int64_t r = nv * VT::N + tid; r < n; r += stride) {
+#pragma unroll
+                for (int i = 0; i < kGroup; ++i)
+                    if (i < kg) acc[i].add(w[r], V[(int64_t)(g0 + i) * ldv + r]);
+            }
+        } else {
+            for (int64_t r = tid; r < n; r += stride) {
+                const T wr = w[r];
+#pragma unroll
+                for (int i = 0; i < kGroup; ++i)
+                    if (i < kg) acc[i].add(wr, V[(int64_t)(g0 + i) * ldv + r]);
             }
         }
-        __syncthreads();
-        if (threadIdx.x < kg) {
-            double s = 0.0;
-            for (int q = 0; q < kRedThreads / 32; ++q) s += sm[threadIdx.x][q];
-            partial[(int64_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
-        }
-        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kGroup; ++i)
+            if (i < kg) block_partial(acc[i].value(), sm, partial, g0 + i);
     }
     if (last_cta(counter)) {
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -81,34 +147,49 @@ __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *_
     }
 }
 
-// out = base + sgn * sum_i c_i V_i, in the vector precision; ||out|| in FP64.
-template <typename T>
+// out = base + sgn * sum_i c_i V_i, in the vector precision; ||out|| FP64-accurate.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *base, const T *__restrict__ V,
                                                             int64_t ldv, int k, const double *c, double sgn, T *out,
                                                             double *partial, double *nrm, unsigned *counter,
                                                             const int *done) {
     if (is_done(done)) return;
+    using VT = Vec<T>;
     __shared__ T sc[kMaxRestart + 1];
     __shared__ double sm[kRedThreads / 32];
     for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = (T)(sgn * c[i]);
     __syncthreads();
-    double ss = 0.0;
+    Acc<T> ss;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tail = 0;
+    if (VEC) {
+        const int64_t nv = n / VT::N;
+        for (int64_t r = tid; r < nv; r += stride) {
+            typename VT::V acc;
+            if (base)
+                acc = reinterpret_cast<const typename VT::V *>(base)[r];
+            else
+                for (int q = 0; q < VT::N; ++q) VT::set(acc, q, T(0));
+            for (int i = 0; i < k; ++i) {
+                const typename VT::V vr = reinterpret_cast<const typename VT::V *>(V + (int64_t)i * ldv)[r];
+#pragma unroll
+                for (int q = 0; q < VT::N; ++q) VT::set(acc, q, fma(sc[i], VT::get(vr, q), VT::get(acc, q)));
+            }
+            reinterpret_cast<typename VT::V *>(out)[r] = acc;
+#pragma unroll
+            for (int q = 0; q < VT::N; ++q) ss.add(VT::get(acc, q), VT::get(acc, q));
+        }
+        tail = nv * VT::N;
+    }
+    for (int64_t r = tail + tid; r < n; r += stride) {
         T acc = base ? base[r] : T(0);
-        for (int i = 0; i < k; ++i) acc += sc[i] * V[(int64_t)i * ldv + r];
+        for (int i = 0; i < k; ++i) acc = fma(sc[i], V[(int64_t)i * ldv + r], acc);
         out[r] = acc;
-        ss += prod(acc, acc);
+        ss.add(acc, acc);
     }
     if (!nrm) return;
-    ss = warp_sum(ss);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = ss;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < kRedThreads / 32; ++q) s += sm[q];
-        partial[blockIdx.x] = s;
-    }
+    block_partial(ss.value(), sm, partial, 0);
     if (last_cta(counter)) {
         if (threadIdx.x == 0) {
             double s = 0.0;
@@ -119,23 +200,29 @@ __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *
     }
 }
 
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__restrict__ x,
                                                           const T *__restrict__ y, double *partial, double *out,
                                                           unsigned *counter, int sqrt_out, const int *done) {
     if (is_done(done)) return;
+    using VT = Vec<T>;
     __shared__ double sm[kRedThreads / 32];
-    double acc = 0.0;
+    Acc<T> acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) acc += prod(x[r], y[r]);
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < kRedThreads / 32; ++q) s += sm[q];
-        partial[blockIdx.x] = s;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tail = 0;
+    if (VEC) {
+        const int64_t nv = n / VT::N;
+        for (int64_t r = tid; r < nv; r += stride) {
+            const typename VT::V a = reinterpret_cast<const typename VT::V *>(x)[r];
+            const typename VT::V b = reinterpret_cast<const typename VT::V *>(y)[r];
+#pragma unroll
+            for (int q = 0; q < VT::N; ++q) acc.add(VT::get(a, q), VT::get(b, q));
+        }
+        tail = nv * VT::N;
     }
+    for (int64_t r = tail + tid; r < n; r += stride) acc.add(x[r], y[r]);
+    block_partial(acc.value(), sm, partial, 0);
     if (last_cta(counter)) {
         if (threadIdx.x == 0) {
             double s = 0.0;
@@ -176,13 +263,26 @@ __global__ void add_f32_scaled(int64_t n, const float *__restrict__ df, const do
 
 int elementwise_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8)); }
 
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+bool vec_ok(int64_t ldv, std::initializer_list<const void *> ptrs) {
+    if (ldv % Vec<T>::N != 0) return false;
+    for (const void *p : ptrs)
+        if (p && !aligned16(p)) return false;
+    return true;
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int64_t ldv, int k, double *partial,
                         double *out, unsigned *counter, const int *done) {
     rsv::count_launches(1);
-    mdot_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, counter, done);
+    if (vec_ok<T>(ldv, {w, V}))
+        mdot_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, counter, done);
+    else
+        mdot_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, counter, done);
     return cudaGetLastError();
 }
 
@@ -190,7 +290,12 @@ template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
                          double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done) {
     rsv::count_launches(1);
-    maxpy_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, base, V, ldv, k, c, sgn, out, partial, nrm, counter, done);
+    if (vec_ok<T>(ldv, {base, V, out}))
+        maxpy_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, base, V, ldv, k, c, sgn, out, partial, nrm,
+                                                                  counter, done);
+    else
+        maxpy_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, base, V, ldv, k, c, sgn, out, partial, nrm,
+                                                                   counter, done);
     return cudaGetLastError();
 }
 
@@ -198,7 +303,10 @@ template <typename T>
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,
                        unsigned *counter, int sqrt_out, const int *done) {
     rsv::count_launches(1);
-    dot_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(n, x, y, partial, out, counter, sqrt_out, done);
+    if (vec_ok<T>(Vec<T>::N, {x, y}))
+        dot_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, x, y, partial, out, counter, sqrt_out, done);
+    else
+        dot_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, x, y, partial, out, counter, sqrt_out, done);
     return cudaGetLastError();
 }
 

@@ -199,6 +199,7 @@ struct rsv_solver {
     rsv_solver_params p{};
     cudaStream_t st = nullptr;
     int64_t n = 0;
+    int64_t ldv = 0;             // leading dimension of the Krylov vectors (n rounded up to 4)
     int pc_type = -1;
     rsv_pc_params pcp{};
     uint64_t pc_version = ~0ull;
@@ -281,7 +282,7 @@ rsv_status set_tol(rsv_solver *s, double tol) {
 // the FP64 outer residual checks the correction anyway.  Counts cycles.
 template <typename T>
 rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, bool confirm) {
-    const int64_t n = s->n;
+    const int64_t n = s->n, ldv = s->ldv;
     const int m = s->p.restart;
     const bool flex = s->p.solver == RSV_FGMRES;
     DevState *ds = s->ds;
@@ -300,17 +301,17 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
         gmres_cycle_init<<<1, 1, 0, s->st>>>(ds);
         RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, V, &ds->beta, nullptr));
         for (int j = 0; j < m; ++j) {
-            T *vj = V + (size_t)j * n;
-            T *wj = V + (size_t)(j + 1) * n;
-            T *z = flex ? Z + (size_t)j * n : t;
+            T *vj = V + (size_t)j * ldv;
+            T *wj = V + (size_t)(j + 1) * ldv;
+            T *z = flex ? Z + (size_t)j * ldv : t;
             RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
             // classical Gram-Schmidt, two passes (re-orthogonalised)
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, n, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done));
-            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, n, j + 1, ds->h1, -1.0, wj, s->partial, nullptr,
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done));
+            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, nullptr,
                                          &ds->counter[1], &ds->done));
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, n, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done));
-            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, n, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done));
+            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
                                          &ds->counter[1], &ds->done));
             rsv::count_launches(1);
             gmres_givens<<<1, 1, 0, s->st>>>(ds, j, m);
@@ -322,10 +323,10 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
             rsv::count_launches(1);
             gmres_backsolve<<<1, 1, 0, s->st>>>(ds, m);
             if (flex) {
-                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, x, Z, n, h.jend, ds->y, 1.0, x, s->partial, nullptr,
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, x, Z, ldv, h.jend, ds->y, 1.0, x, s->partial, nullptr,
                                              &ds->counter[1], nullptr));
             } else {
-                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, (const T *)nullptr, V, n, h.jend, ds->y, 1.0, w, s->partial,
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, (const T *)nullptr, V, ldv, h.jend, ds->y, 1.0, w, s->partial,
                                              nullptr, &ds->counter[1], nullptr));
                 RSV_CUDA_TRY(pc_apply<T>(s, w, t, nullptr));
                 RSV_CUDA_TRY(launch_axpby<T>(s->st, n, T(1), t, T(1), x, x));
@@ -339,10 +340,10 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
 // Right-preconditioned BiCGSTAB in precision T from the x given.
 template <typename T>
 rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
-    const int64_t n = s->n;
+    const int64_t n = s->n, ldv = s->ldv;
     DevState *ds = s->ds;
-    T *r = (T *)s->kw.V, *rh = r + n, *p = r + 2 * n, *v = r + 3 * n, *ph = r + 4 * n, *sh = r + 5 * n,
-      *sv = r + 6 * n, *t = r + 7 * n;  // s (sv) and t adjacent: one two-column dot
+    T *r = (T *)s->kw.V, *rh = r + ldv, *p = r + 2 * ldv, *v = r + 3 * ldv, *ph = r + 4 * ldv, *sh = r + 5 * ldv,
+      *sv = r + 6 * ldv, *t = r + 7 * ldv;  // s (sv) and t adjacent: one two-column dot
     const double btol = s->p.btol;
     RSV_TRY(set_tol(s, tol));
     RSV_CUDA_TRY(residual<T>(s, b, x, r, &ds->red[9]));
@@ -380,7 +381,7 @@ rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
             bicg_consume_half<<<1, 1, 0, s->st>>>(ds);
             RSV_CUDA_TRY(pc_apply<T>(s, sv, sh, done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), sh, T(0), t, done));
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, t, sv, n, 2, s->partial, &ds->red[4], &ds->counter[0], done));
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, t, sv, ldv, 2, s->partial, &ds->red[4], &ds->counter[0], done));
             rsv::count_launches(2);
             bicg_omega<<<1, 1, 0, s->st>>>(ds, btol);
             bicg_update_xr<T><<<g, 256, 0, s->st>>>(n, ds, ph, sh, sv, t, x, r);
@@ -486,8 +487,9 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
     s->p = *p;
     s->st = A->stream;
     s->n = 3 * A->nb;
+    s->ldv = (s->n + 3) & ~int64_t(3);
     s->mixed = p->precision == RSV_PREC_MIXED;
-    const int64_t n = std::max<int64_t>(s->n, 1);
+    const int64_t n = std::max<int64_t>(s->ldv, 4);
     const int m = p->restart;
     const size_t es = s->mixed ? sizeof(float) : sizeof(double);
     cudaError_t e = cudaSuccess;
