@@ -129,14 +129,16 @@ rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
     cudaError_t e;
     const size_t vbytes = sizeof(double) * (9 * (size_t)A->nnzb + 16);
     if ((e = cudaMalloc((void **)&A->d_rp, sizeof(int32_t) * (A->nb + 1))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&A->d_ci, sizeof(int32_t) * A->nnzb)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&A->d_ci, sizeof(int32_t) * (A->nnzb + 16))) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_v, vbytes)) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_v32, vbytes / 2)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A->d_rp, A->h_rp.data(), sizeof(int32_t) * (A->nb + 1), cudaMemcpyHostToDevice,
                              A->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A->d_ci, A->h_ci.data(), sizeof(int32_t) * A->nnzb, cudaMemcpyHostToDevice,
                              A->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(A->d_ci + A->nnzb, 0, sizeof(int32_t) * 16, A->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(A->d_v, 0, vbytes, A->stream)) != cudaSuccess ||
+        (e = spmv_init()) != cudaSuccess ||
         (e = cudaMemsetAsync(A->d_v32, 0, vbytes / 2, A->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(A->stream)) != cudaSuccess) {
         mat_free(A);

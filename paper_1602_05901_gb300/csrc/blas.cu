@@ -94,16 +94,32 @@ __device__ __forceinline__ void block_partial(double v, double *sm, double *part
     __syncthreads();
 }
 
+// out[i] = <w, V_i> for i < k; if self_nrm, also out[k] = <w, w> and *self_nrm = ||w||.
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *__restrict__ w,
                                                            const T *__restrict__ V, int64_t ldv, int k,
-                                                           double *partial, double *out, unsigned *counter,
-                                                           const int *done) {
-    if (is_done(done)) return;
+                                                           double *partial, double *out, double *self_nrm,
+                                                           unsigned *counter, const int *done, const int *skip) {
+    if (is_done(done) || is_done(skip)) return;
     using VT = Vec<T>;
     __shared__ double sm[kRedThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (self_nrm) {
+        Acc<T> a;
+        if (VEC) {
+            const int64_t nv = n / VT::N;
+            for (int64_t r = tid; r < nv; r += stride) {
+                const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
+#pragma unroll
+                for (int q = 0; q < VT::N; ++q) a.add(VT::get(wr, q), VT::get(wr, q));
+            }
+            for (int64_t r = nv * VT::N + tid; r < n; r += stride) a.add(w[r], w[r]);
+        } else {
+            for (int64_t r = tid; r < n; r += stride) a.add(w[r], w[r]);
+        }
+        block_partial(a.value(), sm, partial, k);
+    }
     for (int g0 = 0; g0 < k; g0 += kGroup) {
         Acc<T> acc[kGroup];
         const int kg = min(kGroup, k - g0);
@@ -138,10 +154,12 @@ __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *_
             if (i < kg) block_partial(acc[i].value(), sm, partial, g0 + i);
     }
     if (last_cta(counter)) {
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int kk = self_nrm ? k + 1 : k;
+        for (int i = threadIdx.x; i < kk; i += blockDim.x) {
             double s = 0.0;
             for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[(int64_t)i * gridDim.x + b]);
             out[i] = s;
+            if (i == k) *self_nrm = sqrt(s);
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
@@ -152,8 +170,8 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *base, const T *__restrict__ V,
                                                             int64_t ldv, int k, const double *c, double sgn, T *out,
                                                             double *partial, double *nrm, unsigned *counter,
-                                                            const int *done) {
-    if (is_done(done)) return;
+                                                            const int *done, const int *skip) {
+    if (is_done(done) || is_done(skip)) return;
     using VT = Vec<T>;
     __shared__ T sc[kMaxRestart + 1];
     __shared__ double sm[kRedThreads / 32];
@@ -277,25 +295,28 @@ bool vec_ok(int64_t ldv, std::initializer_list<const void *> ptrs) {
 
 template <typename T>
 cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int64_t ldv, int k, double *partial,
-                        double *out, unsigned *counter, const int *done) {
+                        double *out, unsigned *counter, const int *done, double *self_nrm, const int *skip) {
     rsv::count_launches(1);
     if (vec_ok<T>(ldv, {w, V}))
-        mdot_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, counter, done);
+        mdot_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, self_nrm, counter,
+                                                                 done, skip);
     else
-        mdot_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, counter, done);
+        mdot_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, V, ldv, k, partial, out, self_nrm, counter,
+                                                                  done, skip);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
-                         double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done) {
+                         double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done,
+                         const int *skip) {
     rsv::count_launches(1);
     if (vec_ok<T>(ldv, {base, V, out}))
         maxpy_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, base, V, ldv, k, c, sgn, out, partial, nrm,
-                                                                  counter, done);
+                                                                  counter, done, skip);
     else
         maxpy_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, base, V, ldv, k, c, sgn, out, partial, nrm,
-                                                                   counter, done);
+                                                                   counter, done, skip);
     return cudaGetLastError();
 }
 
@@ -342,9 +363,9 @@ cudaError_t launch_add_f32_scaled(cudaStream_t st, int64_t n, const float *df, c
 
 #define RSV_BLAS_INST(T)                                                                                            \
     template cudaError_t launch_mdot<T>(cudaStream_t, int64_t, const T *, const T *, int64_t, int, double *,       \
-                                        double *, unsigned *, const int *);                                        \
+                                        double *, unsigned *, const int *, double *, const int *);                 \
     template cudaError_t launch_maxpy<T>(cudaStream_t, int64_t, const T *, const T *, int64_t, int, const double *, \
-                                         double, T *, double *, double *, unsigned *, const int *);                 \
+                                         double, T *, double *, double *, unsigned *, const int *, const int *);    \
     template cudaError_t launch_dot<T>(cudaStream_t, int64_t, const T *, const T *, double *, double *, unsigned *, \
                                        int, const int *);                                                           \
     template cudaError_t launch_axpby<T>(cudaStream_t, int64_t, T, const T *, T, const T *, T *);                  \

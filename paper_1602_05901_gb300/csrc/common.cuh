@@ -43,7 +43,7 @@ struct DevState {
     double y[kMaxRestart];
     double h1[kMaxRestart + 1], h2[kMaxRestart + 1];  // CGS2 projection coefficients
     double red[kMaxRestart + 1];                       // generic reduction outputs
-    double beta, hn, inv_hn, tol;
+    double beta, hn, wnorm, tol;
     double rho, rho1, alpha, omega;
     double bnorm;
     int done;       // 1: stop this cycle / iteration loop
@@ -51,6 +51,7 @@ struct DevState {
     int iters;      // Krylov iterations so far (device count)
     int jend;       // Arnoldi steps taken in the current cycle
     int conv;       // the current cycle met the tolerance on its residual estimate
+    int skip2;      // the first Gram-Schmidt pass kept enough of the norm: skip the second
     int maxit;
     unsigned counter[4];  // last-block tickets of the reduction kernels
 };
@@ -94,6 +95,8 @@ struct rsv_mat {
 namespace rsv {
 
 // ---- launchers implemented in spmv.cu
+// One-time kernel attributes (large dynamic shared memory); called at matrix creation.
+cudaError_t spmv_init();
 cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
                             const int *done);
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
@@ -102,13 +105,17 @@ cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, flo
 
 // ---- launchers implemented in blas.cu (T = double or float; reductions in FP64)
 // out[i] = <w, V_i> for i < k; V_i = V + i*ldv.  Deterministic two-level reduction.
+// self_nrm (optional): also out[k] = <w, w> and *self_nrm = ||w||.  skip (optional): a second
+// device flag that, like done, makes the kernel return at once.
 template <typename T>
 cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int64_t ldv, int k, double *partial,
-                        double *out, unsigned *counter, const int *done);
+                        double *out, unsigned *counter, const int *done, double *self_nrm = nullptr,
+                        const int *skip = nullptr);
 // out = base + sgn * sum_i c[i] V_i (base may be null); if nrm != nullptr, *nrm = ||out||_2.
 template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
-                         double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done);
+                         double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done,
+                         const int *skip = nullptr);
 // *out = ||x||_2 (sqrt_out=1) or <x,y>
 template <typename T>
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,

@@ -8,10 +8,11 @@
 // Kernels of a step that follows convergence see the device `done` flag and
 // return at once.
 //
-// Arnoldi orthogonalisation is classical Gram-Schmidt applied twice (two
-// passes of "all projections, then one multi-vector update"); the Hessenberg
-// columns, Givens rotations and the residual estimate are FP64 scalars kept
-// in device memory.
+// Arnoldi orthogonalisation is classical Gram-Schmidt ("all projections, then
+// one multi-vector update"), repeated once when the first pass cancelled more
+// than 1 - 1/sqrt(2) of the vector's norm (Kahan's "twice is enough" test);
+// the Hessenberg columns, Givens rotations and the residual estimate are FP64
+// scalars kept in device memory.
 //
 // Mixed precision (precision = RSV_PREC_MIXED): an FP64 iterative-refinement
 // loop r = b - A x (FP64 SpMV, FP64 norm), inner solve A d = r / ||r|| with
@@ -68,6 +69,16 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
     const bool met = fabs(ds->g[j + 1]) <= ds->tol;
     if (met || lucky) ds->conv = 1;
     if (met || ds->iters >= ds->maxit || lucky || j + 1 == m) ds->done = 1;
+}
+
+// After the first Gram-Schmidt pass: keep its result when ||w'|| >= ||w|| / sqrt(2),
+// otherwise run the second pass (its coefficients add to the first pass's).
+__global__ void gmres_reorth_check(DevState *ds, int k) {
+    if (ds->done) return;
+    const bool keep = ds->hn >= 0.70710678118654752 * ds->wnorm;
+    if (threadIdx.x == 0) ds->skip2 = keep ? 1 : 0;
+    if (keep)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) ds->h2[i] = 0.0;
 }
 
 __global__ void gmres_backsolve(DevState *ds, int m) {
@@ -306,13 +317,18 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
             T *z = flex ? Z + (size_t)j * ldv : t;
             RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
-            // classical Gram-Schmidt, two passes (re-orthogonalised)
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done));
-            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, nullptr,
+            // classical Gram-Schmidt; a second pass only when the first one cancelled
+            // more than 1 - 1/sqrt(2) of the norm ("twice is enough")
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done,
+                                        &ds->wnorm));
+            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, &ds->hn,
                                          &ds->counter[1], &ds->done));
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done));
+            rsv::count_launches(1);
+            gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done,
+                                        nullptr, &ds->skip2));
             RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
-                                         &ds->counter[1], &ds->done));
+                                         &ds->counter[1], &ds->done, &ds->skip2));
             rsv::count_launches(1);
             gmres_givens<<<1, 1, 0, s->st>>>(ds, j, m);
             RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, wj, &ds->hn, &ds->done));

@@ -1,43 +1,100 @@
 // BSR SpMV y = alpha A x + beta y for 3x3 blocks (Section "Algebraic
-// Operations", first equation).  One CTA owns R consecutive block rows: it
-// stages their contiguous run of block values and column indices in shared
-// memory with coalesced loads, then one thread per scalar row forms the
-// three-term products against x.
+// Operations", first equation).
 #include "common.cuh"
 
 namespace rsv {
 namespace {
 
-constexpr int kRows = 64;  // block rows per CTA (7 blocks max per row)
+constexpr int kRows = 128;  // block rows per CTA (at most 7 blocks per row)
 
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Shared-memory layout of one CTA: block values | column indices | row pointers | mbarrier.
+template <typename T, int R> struct SpmvSmem {
+    static constexpr int VALS = R * 7 * 9 + 32 / sizeof(T);  // + room for aligning both ends to 16 bytes
+    static constexpr int CI = R * 7 + 8;
+    static constexpr size_t BYTES = (size_t)VALS * sizeof(T) + CI * 4 + (R + 4) * 4 + 16;
+};
+
+// One CTA owns R consecutive block rows.  Their blocks and column indices are
+// contiguous in the BSR arrays, so one thread stages both ranges with two TMA
+// bulk copies (aligned down/up to 16 bytes; the arrays carry tail padding)
+// while the others load the row pointers; then thread (row, e) forms
+// sum_p A_p[e][:] . x[3 col_p : 3 col_p + 3].
 template <typename T, int R>
-__global__ void __launch_bounds__(3 * R) spmv_bsr3_staged(int nb, const int32_t *__restrict__ rp,
-                                                          const int32_t *__restrict__ ci,
-                                                          const T *__restrict__ v, T alpha,
-                                                          const T *__restrict__ x, T beta,
-                                                          T *__restrict__ y, const int *done) {
+__global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci, const T *__restrict__ v,
+                                                       T alpha, const T *__restrict__ x, T beta, T *__restrict__ y,
+                                                       const int *done) {
     if (done && *(volatile const int *)done) return;
-    __shared__ T sv[R * 7 * 9];
-    __shared__ int32_t sci[R * 7];
-    __shared__ int32_t srp[R + 1];
+    using L = SpmvSmem<T, R>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    T *sv = reinterpret_cast<T *>(smem);
+    int32_t *sci = reinterpret_cast<int32_t *>(smem + (size_t)L::VALS * sizeof(T));
+    int32_t *srp = sci + L::CI;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(srp + R + 4);
     const int r0 = blockIdx.x * R;
     const int nr = min(R, nb - r0);
-    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t];
+    const int p0 = rp[r0], p1 = rp[r0 + nr];
+    const uintptr_t vb0 = (uintptr_t)(v + (int64_t)p0 * 9), vb1 = (uintptr_t)(v + (int64_t)p1 * 9);
+    const uintptr_t va0 = vb0 & ~(uintptr_t)15, va1 = (vb1 + 15) & ~(uintptr_t)15;
+    const uintptr_t cb0 = (uintptr_t)(ci + p0), cb1 = (uintptr_t)(ci + p1);
+    const uintptr_t ca0 = cb0 & ~(uintptr_t)15, ca1 = (cb1 + 15) & ~(uintptr_t)15;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned bytes = (unsigned)((va1 - va0) + (ca1 - ca0));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sv)),
+            "l"(va0), "r"((unsigned)(va1 - va0)), "r"(smem_u32(bar))
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sci)),
+            "l"(ca0), "r"((unsigned)(ca1 - ca0)), "r"(smem_u32(bar))
+            : "memory");
+    }
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t] - p0;
     __syncthreads();
-    const int p0 = srp[0];
-    const int np = srp[nr] - p0;
-    const T *vsrc = v + (int64_t)p0 * 9;
-    for (int q = threadIdx.x; q < np * 9; q += blockDim.x) sv[q] = vsrc[q];
-    for (int q = threadIdx.x; q < np; q += blockDim.x) sci[q] = ci[p0 + q];
-    __syncthreads();
+    {
+        unsigned ok = 0, spins = 0;
+        uint64_t deadline = 0;
+        for (;;) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(smem_u32(bar))
+                : "memory");
+            if (ok) break;
+            // the copy is plain memory traffic; the limit only guards against a stuck wait
+            if ((++spins & 1023u) == 0) {
+                const uint64_t now = global_timer();
+                if (deadline == 0) deadline = now + 2000000000ull;
+                else if (now > deadline) return;
+            }
+        }
+    }
+    const int voff = (int)((vb0 - va0) / sizeof(T));
+    const int coff = (int)((cb0 - ca0) / 4);
     const int t = threadIdx.x;
     if (t >= nr * 3) return;
     const int rl = t / 3, e = t - 3 * (t / 3);
     T acc = T(0);
-    for (int p = srp[rl] - p0; p < srp[rl + 1] - p0; ++p) {
-        const T *a = sv + p * 9 + 3 * e;
-        const T *xc = x + 3 * (int64_t)sci[p];
-        acc += a[0] * xc[0] + a[1] * xc[1] + a[2] * xc[2];
+    for (int p = srp[rl]; p < srp[rl + 1]; ++p) {
+        const T *a = sv + voff + p * 9 + 3 * e;
+        const T *xc = x + 3 * (int64_t)sci[coff + p];
+        acc = fma(a[0], xc[0], acc);
+        acc = fma(a[1], xc[1], acc);
+        acc = fma(a[2], xc[2], acc);
     }
     const int64_t row = 3 * (int64_t)(r0 + rl) + e;
     y[row] = (beta == T(0)) ? alpha * acc : alpha * acc + beta * y[row];
@@ -50,13 +107,22 @@ __global__ void cast_f64_f32(int64_t n, const double *__restrict__ a, float *__r
 
 }  // namespace
 
+cudaError_t spmv_init() {
+    cudaError_t e = cudaFuncSetAttribute((const void *)spmv_bsr3_tma<double, kRows>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SpmvSmem<double, kRows>::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)spmv_bsr3_tma<float, kRows>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SpmvSmem<float, kRows>::BYTES);
+}
+
 cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
                             const int *done) {
     if (A->nb == 0) return cudaSuccess;
     int grid = (int)((A->nb + kRows - 1) / kRows);
     rsv::count_launches(1);
-    spmv_bsr3_staged<double, kRows><<<grid, 3 * kRows, 0, A->stream>>>((int)A->nb, A->d_rp, A->d_ci, A->d_v,
-                                                                        alpha, x, beta, y, done);
+    spmv_bsr3_tma<double, kRows><<<grid, 3 * kRows, SpmvSmem<double, kRows>::BYTES, A->stream>>>(
+        (int)A->nb, A->d_rp, A->d_ci, A->d_v, alpha, x, beta, y, done);
     return cudaGetLastError();
 }
 
@@ -65,8 +131,8 @@ cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float
     if (A->nb == 0) return cudaSuccess;
     int grid = (int)((A->nb + kRows - 1) / kRows);
     rsv::count_launches(1);
-    spmv_bsr3_staged<float, kRows><<<grid, 3 * kRows, 0, A->stream>>>((int)A->nb, A->d_rp, A->d_ci, A->d_v32,
-                                                                       alpha, x, beta, y, done);
+    spmv_bsr3_tma<float, kRows><<<grid, 3 * kRows, SpmvSmem<float, kRows>::BYTES, A->stream>>>(
+        (int)A->nb, A->d_rp, A->d_ci, A->d_v32, alpha, x, beta, y, done);
     return cudaGetLastError();
 }
 
