@@ -95,6 +95,15 @@ __device__ __forceinline__ void block_partial(double v, double *sm, double *part
 }
 
 // out[i] = <w, V_i> for i < k; if self_nrm, also out[k] = <w, w> and *self_nrm = ||w||.
+// Final reduction in the last CTA: warp w sums the gridDim.x partials of
+// outputs w, w + 8, ...; each lane adds a fixed strided subset, then a
+// shuffle tree combines the lanes (a fixed order: deterministic).
+__device__ __forceinline__ double final_sum(const double *partial, int slot) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x & 31; b < gridDim.x; b += 32) s += __ldcg(&partial[(int64_t)slot * gridDim.x + b]);
+    return warp_sum(s);
+}
+
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *__restrict__ w,
                                                            const T *__restrict__ V, int64_t ldv, int k,
@@ -155,11 +164,12 @@ __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *_
     }
     if (last_cta(counter)) {
         const int kk = self_nrm ? k + 1 : k;
-        for (int i = threadIdx.x; i < kk; i += blockDim.x) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[(int64_t)i * gridDim.x + b]);
-            out[i] = s;
-            if (i == k) *self_nrm = sqrt(s);
+        for (int i = threadIdx.x >> 5; i < kk; i += kRedThreads / 32) {
+            const double s = final_sum(partial, i);
+            if ((threadIdx.x & 31) == 0) {
+                out[i] = s;
+                if (i == k) *self_nrm = sqrt(s);
+            }
         }
         if (threadIdx.x == 0) *counter = 0u;
     }
@@ -209,11 +219,12 @@ __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *
     if (!nrm) return;
     block_partial(ss.value(), sm, partial, 0);
     if (last_cta(counter)) {
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[b]);
-            *nrm = sqrt(s);
-            *counter = 0u;
+        if (threadIdx.x < 32) {
+            const double s = final_sum(partial, 0);
+            if (threadIdx.x == 0) {
+                *nrm = sqrt(s);
+                *counter = 0u;
+            }
         }
     }
 }
@@ -242,11 +253,12 @@ __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__
     for (int64_t r = tail + tid; r < n; r += stride) acc.add(x[r], y[r]);
     block_partial(acc.value(), sm, partial, 0);
     if (last_cta(counter)) {
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[b]);
-            *out = sqrt_out ? sqrt(s) : s;
-            *counter = 0u;
+        if (threadIdx.x < 32) {
+            const double s = final_sum(partial, 0);
+            if (threadIdx.x == 0) {
+                *out = sqrt_out ? sqrt(s) : s;
+                *counter = 0u;
+            }
         }
     }
 }
