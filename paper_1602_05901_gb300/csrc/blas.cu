@@ -105,7 +105,7 @@ __device__ __forceinline__ double final_sum(const double *partial, int slot) {
 }
 
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *__restrict__ w,
+__global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T *__restrict__ w,
                                                            const T *__restrict__ V, int64_t ldv, int k,
                                                            double *partial, double *out, double *self_nrm,
                                                            unsigned *counter, const int *done, const int *skip) {
@@ -135,14 +135,17 @@ __global__ void __launch_bounds__(kRedThreads) mdot_kernel(int64_t n, const T *_
         if (VEC) {
             const int64_t nv = n / VT::N;
             for (int64_t r = tid; r < nv; r += stride) {
+                // issue every load of the group first, then accumulate (keeps kg loads in flight)
                 const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
+                typename VT::V vr[kGroup];
+#pragma unroll
+                for (int i = 0; i < kGroup; ++i)
+                    if (i < kg) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)(g0 + i) * ldv)[r];
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i)
                     if (i < kg) {
-                        const typename VT::V vr =
-                            reinterpret_cast<const typename VT::V *>(V + (int64_t)(g0 + i) * ldv)[r];
 #pragma unroll
-                        for (int q = 0; q < VT::N; ++q) acc[i].add(VT::get(wr, q), VT::get(vr, q));
+                        for (int q = 0; q < VT::N; ++q) acc[i].add(VT::get(wr, q), VT::get(vr[i], q));
                     }
             }
             for (int64_t r = nv * VT::N + tid; r < n; r += stride) {
@@ -199,10 +202,19 @@ __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *
                 acc = reinterpret_cast<const typename VT::V *>(base)[r];
             else
                 for (int q = 0; q < VT::N; ++q) VT::set(acc, q, T(0));
-            for (int i = 0; i < k; ++i) {
-                const typename VT::V vr = reinterpret_cast<const typename VT::V *>(V + (int64_t)i * ldv)[r];
+            constexpr int B = 8;  // loads issued together
+            for (int i0 = 0; i0 < k; i0 += B) {
+                typename VT::V vr[B];
 #pragma unroll
-                for (int q = 0; q < VT::N; ++q) VT::set(acc, q, fma(sc[i], VT::get(vr, q), VT::get(acc, q)));
+                for (int i = 0; i < B; ++i)
+                    if (i0 + i < k) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)(i0 + i) * ldv)[r];
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (i0 + i < k) {
+#pragma unroll
+                        for (int q = 0; q < VT::N; ++q)
+                            VT::set(acc, q, fma(sc[i0 + i], VT::get(vr[i], q), VT::get(acc, q)));
+                    }
             }
             reinterpret_cast<typename VT::V *>(out)[r] = acc;
 #pragma unroll
