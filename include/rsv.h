@@ -171,8 +171,20 @@ RSV_API rsv_status rsv_precond_apply(rsv_solver *s, const double *r, double *z);
 /* Same in FP32 for a mixed-precision solver (its preconditioner is built on
  * the FP32-rounded matrix and stores FP32 factors); device float32[3*nb]. */
 RSV_API rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z);
+/* Inspect a CPR preconditioner (Section "CPR-like Preconditioners"): the
+ * number of multigrid levels, their grid dimensions (int[3*nlev]: nx, ny, nz
+ * per level, finest first), the quasi-IMPES weights (host float64[nb][3]) and
+ * the seven-point pressure stencils of every level, finest first,
+ * concatenated (host float64[sum_l cells_l][7], slots -z, -y, -x, centre, +x,
+ * +y, +z).  Any output may be NULL.  Synchronises the stream. */
+RSV_API rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, double *a7_host);
+/* One multigrid V-cycle on the finest pressure system from a zero guess
+ * (Section "Algebraic Multigrid Methods", V-cycle algorithm): x = V(b);
+ * device float64[nb] (FP64 solver with a CPR preconditioner only). */
+RSV_API rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x);
 /* Copy the inverted diagonal blocks of the preconditioner (block Jacobi:
- * A_ii^{-1}; block ILU(0): U_ii^{-1}) to host float64[nb][3][3]. */
+ * A_ii^{-1}; block ILU(0) and CPR: the ILU factor's U_ii^{-1}) to host
+ * float64[nb][3][3]. */
 RSV_API rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host);
 /* Solve A x = b.  b, x: float64[3*nb], host (on_device = 0) or device
  * (on_device = 1); x holds the initial guess on entry and the solution on

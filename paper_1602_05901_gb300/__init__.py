@@ -80,6 +80,8 @@ _SIGS = {
     "rsv_precond_apply": (_I, [_P, _P, _P]),
     "rsv_precond_apply_f32": (_I, [_P, _P, _P]),
     "rsv_precond_get_dinv": (_I, [_P, _P]),
+    "rsv_cpr_info": (_I, [_P, ctypes.POINTER(_I), _P, _P, _P]),
+    "rsv_cpr_vcycle": (_I, [_P, _P, _P]),
     "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
 }
 EXPORTS = tuple(_SIGS)
@@ -219,6 +221,28 @@ class Solver:
         out = np.zeros((self.A.nb, 3, 3))
         check(_lib.rsv_precond_get_dinv(self.handle, _ptr(out)), "rsv_precond_get_dinv")
         return out
+
+    def cpr_info(self, with_arrays=True):
+        """(levels [(nx, ny, nz)...], QI weights [nb,3], [per-level stencil [n_l,7]])."""
+        nl = ctypes.c_int()
+        dims = (ctypes.c_int * 24)()
+        check(_lib.rsv_cpr_info(self.handle, ctypes.byref(nl), dims, None, None), "rsv_cpr_info")
+        levels = [(dims[3 * l], dims[3 * l + 1], dims[3 * l + 2]) for l in range(nl.value)]
+        if not with_arrays:
+            return levels, None, None
+        total = sum(a * b_ * c for a, b_, c in levels)
+        w = np.zeros((self.A.nb, 3))
+        a7 = np.zeros((total, 7))
+        check(_lib.rsv_cpr_info(self.handle, None, None, _ptr(w), _ptr(a7)), "rsv_cpr_info")
+        out, off = [], 0
+        for a, b_, c in levels:
+            out.append(a7[off:off + a * b_ * c])
+            off += a * b_ * c
+        return levels, w, out
+
+    def vcycle(self, b, x):
+        check(_lib.rsv_cpr_vcycle(self.handle, _ptr(b), _ptr(x)), "rsv_cpr_vcycle")
+        return x
 
     def solve(self, b, x, raise_on_error=False):
         """b, x: float64 [3*nb], both host numpy or both CUDA tensors. Returns (status, info dict)."""

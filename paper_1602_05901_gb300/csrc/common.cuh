@@ -69,6 +69,21 @@ struct IluTiles {  // packed factor and buffers of the persistent tile sweeps (i
     void *EJb = nullptr, *EKb = nullptr;  // backward edge hand-off buffers
 };
 
+constexpr int kMaxLevels = 8;
+struct Cpr {  // CPR pressure stage: quasi-IMPES weights and the GMG hierarchy (cpr.cu)
+    bool mixed = false;
+    int nlev = 0, sweeps = 2, ncoarse = 0;
+    int dims[kMaxLevels][3] = {};
+    double *a7[kMaxLevels] = {};  // FP64 seven-point stencils, slot-major [7][n]
+    void *a7f[kMaxLevels] = {};   // FP32 copies (mixed precision)
+    void *x[kMaxLevels] = {}, *b[kMaxLevels] = {};  // per-level solution and right-hand side (T)
+    double *w64 = nullptr;        // quasi-IMPES weights [nb][3], FP64
+    void *w = nullptr;            // weights in T
+    double *dense = nullptr, *minv = nullptr, *work = nullptr;  // coarsest LU / inverse / scratch
+    int *piv = nullptr;
+    void *r = nullptr, *z = nullptr, *xp = nullptr;  // full-stage residual and ILU correction (T)
+};
+
 struct Schedule {  // i+j+k wavefront hyperplanes
     std::vector<int> plane_ptr;  // host, nplanes+1
     int32_t *cells = nullptr;    // device, nb cell indices grouped by plane (ascending within)
@@ -137,6 +152,15 @@ cudaError_t launch_bj_setup(const rsv_mat *A, bool from_f32, double *dinv, float
 template <typename T>
 cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const T *dinv, const T *r, T *z, const int *done);
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status);
+
+// ---- implemented in cpr.cu
+cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, Cpr *P, int *status);
+void free_cpr(Cpr *P);
+template <typename T>
+cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
+                      int *status, unsigned long long timeout_ns);
+template <typename T>
+cudaError_t cpr_vcycle(const rsv_mat *A, const Cpr &P, const T *b, T *x);
 
 // ---- launchers implemented in ilu_tiles.cu
 template <typename T>

@@ -1,0 +1,486 @@
+// CPR two-stage preconditioner (Section "CPR-like Preconditioners").
+//
+// Pressure stage: quasi-IMPES decoupling (named in the numerical experiments;
+// diagonal reading: with D = A_cc, w_c = (1, -D01/D11, -D02/D22)), the
+// restriction Pi_r f = (w_c . f_c)_c, and the pressure matrix
+// (A_pp)_cn = sum_r w_c[r] A_cn[r][0] (the pressure column of the weighted
+// block row), a seven-point scalar stencil.  It is solved approximately by
+// one geometric-multigrid V-cycle standing in for the paper's AMG (Section
+// "Algebraic Multigrid Methods": R = P^T, A_{l+1} = R A_l P, pre-smoother,
+// residual, restriction, recursion, prolongation, post-smoother, exact
+// coarsest solve):
+//   * P is piecewise constant on 2x2x2 boxes (coarse dims ceil(d/2)), so the
+//     Galerkin operator stays seven-point: entry (I, J) sums the fine
+//     couplings from box I to box J, couplings inside a box add to I's centre;
+//   * smoothing is red-black Gauss-Seidel, colour (i+j+k) mod 2, red then
+//     black before the recursion and black then red after it;
+//   * the coarsest level (at most gmg_max_coarse cells) is solved with its
+//     explicit inverse, computed at setup from a partial-pivoting LU.
+// Full stage (CPR-PF, two-stage multiplicative): x = Pi_p p; r = f - A x;
+// x = x + ILU0^{-1} r, with Pi_p p = (p_c, 0, 0)_c.
+//
+// Stencil storage: a7[s][c] (slot-major, coalesced), slots -z, -y, -x,
+// centre, +x, +y, +z; absent faces hold 0.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rsv {
+namespace {
+
+__device__ __forceinline__ bool gated(const int *done) { return done && *(volatile const int *)done; }
+
+struct G3 {
+    int nx, ny, nz;
+    __host__ __device__ int64_t n() const { return (int64_t)nx * ny * nz; }
+};
+
+__device__ __forceinline__ void ijk(int64_t c, G3 g, int &i, int &j, int &k) {
+    i = (int)(c % g.nx);
+    j = (int)((c / g.nx) % g.ny);
+    k = (int)(c / ((int64_t)g.nx * g.ny));
+}
+
+__constant__ int kDI[7] = {0, 0, -1, 0, 1, 0, 0};
+__constant__ int kDJ[7] = {0, -1, 0, 0, 0, 1, 0};
+__constant__ int kDK[7] = {-1, 0, 0, 0, 0, 0, 1};
+
+__device__ __forceinline__ int slot_of(int di, int dj, int dk) {
+    return dk < 0 ? 0 : dj < 0 ? 1 : di < 0 ? 2 : di > 0 ? 4 : dj > 0 ? 5 : dk > 0 ? 6 : 3;
+}
+
+// Quasi-IMPES weights and the pressure stencil of the block row of cell c.
+template <typename Tv>
+__global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *__restrict__ v,
+                                double *__restrict__ w, double *__restrict__ a7, int *status) {
+    const int64_t n = g.n();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int i, j, k;
+    ijk(c, g, i, j, k);
+    const bool has[7] = {k > 0, j > 0, i > 0, true, i < g.nx - 1, j < g.ny - 1, k < g.nz - 1};
+    int slot_pos[7], q = 0;
+    for (int s = 0; s < 7; ++s) slot_pos[s] = has[s] ? q++ : -1;
+    const Tv *d = v + 9 * ((int64_t)rp[c] + slot_pos[3]);
+    const double d11 = (double)d[4], d22 = (double)d[8];
+    if (!(fabs(d11) > 1e-300) || !(fabs(d22) > 1e-300)) {
+        atomicCAS(status, 0, (int)RSV_ESINGULAR);
+        return;
+    }
+    const double w0 = 1.0, w1 = -(double)d[1] / d11, w2 = -(double)d[2] / d22;
+    w[3 * c] = w0;
+    w[3 * c + 1] = w1;
+    w[3 * c + 2] = w2;
+    for (int s = 0; s < 7; ++s) {
+        double val = 0.0;
+        if (has[s]) {
+            const Tv *blk = v + 9 * ((int64_t)rp[c] + slot_pos[s]);
+            val = w0 * (double)blk[0] + w1 * (double)blk[3] + w2 * (double)blk[6];
+        }
+        a7[(int64_t)s * n + c] = val;
+    }
+}
+
+// Galerkin coarse operator P^T A P for piecewise-constant P: one thread per
+// coarse cell sums the couplings of its children (children and slots in a
+// fixed order, so the result is deterministic).
+__global__ void gmg_coarsen_kernel(G3 f, const double *__restrict__ af, G3 cg, double *__restrict__ ac) {
+    const int64_t nc = cg.n(), nf = f.n();
+    const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (C >= nc) return;
+    int I, J, K;
+    ijk(C, cg, I, J, K);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
+                const int64_t c = (int64_t)k * f.nx * f.ny + (int64_t)j * f.nx + i;
+                for (int s = 0; s < 7; ++s) {
+                    const int ii = i + kDI[s], jj = j + kDJ[s], kk = k + kDK[s];
+                    if (ii < 0 || jj < 0 || kk < 0 || ii >= f.nx || jj >= f.ny || kk >= f.nz) continue;
+                    acc[slot_of(ii / 2 - I, jj / 2 - J, kk / 2 - K)] += af[(int64_t)s * nf + c];
+                }
+            }
+    for (int s = 0; s < 7; ++s) ac[(int64_t)s * nc + C] = acc[s];
+}
+
+__global__ void cast_stencil(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// Dense matrix of the coarsest stencil, row-major n x n.
+__global__ void coarse_dense_kernel(G3 g, const double *__restrict__ a7, double *__restrict__ M) {
+    const int64_t n = g.n();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int64_t q = 0; q < n; ++q) M[c * n + q] = 0.0;
+    int i, j, k;
+    ijk(c, g, i, j, k);
+    for (int s = 0; s < 7; ++s) {
+        const int ii = i + kDI[s], jj = j + kDJ[s], kk = k + kDK[s];
+        if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nx || jj >= g.ny || kk >= g.nz) continue;
+        M[c * n + (int64_t)kk * g.nx * g.ny + (int64_t)jj * g.nx + ii] += a7[(int64_t)s * n + c];
+    }
+}
+
+// In-place LU with partial pivoting of the n x n matrix M (one CTA), then its
+// inverse into Minv by solving for the unit vectors.  |pivot| <= 1e-300
+// reports RSV_ESINGULAR.
+__global__ void __launch_bounds__(1024) coarse_lu_kernel(int n, double *M, int *piv, int *status) {
+    __shared__ double sval[32];
+    __shared__ int sidx[32];
+    __shared__ int spiv;
+    for (int k = 0; k < n; ++k) {
+        // pivot search in column k (max |M[i][k]|, smallest i on ties)
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double a = fabs(M[(int64_t)i * n + k]);
+            if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { sval[threadIdx.x >> 5] = best; sidx[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -1.0;
+            int p = k;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                if (sval[q] > b || (sval[q] == b && sidx[q] < p)) { b = sval[q]; p = sidx[q]; }
+            spiv = p;
+            piv[k] = p;
+            if (!(b > 1e-300)) atomicCAS(status, 0, (int)RSV_ESINGULAR);
+        }
+        __syncthreads();
+        const int p = spiv;
+        if (p != k)
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                const double t = M[(int64_t)k * n + q];
+                M[(int64_t)k * n + q] = M[(int64_t)p * n + q];
+                M[(int64_t)p * n + q] = t;
+            }
+        __syncthreads();
+        const double pk = M[(int64_t)k * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) M[(int64_t)i * n + k] /= pk;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+            const int i = k + 1 + (int)(t / m), q = k + 1 + (int)(t % m);
+            M[(int64_t)i * n + q] -= M[(int64_t)i * n + k] * M[(int64_t)k * n + q];
+        }
+        __syncthreads();
+    }
+}
+
+// Column j of the inverse: solve (LU) x = P e_j.  One CTA per column.
+__global__ void coarse_inverse_kernel(int n, const double *__restrict__ LU, const int *__restrict__ piv,
+                                      double *__restrict__ Minv, double *__restrict__ work) {
+    const int j = blockIdx.x;
+    double *x = work + (int64_t)j * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < n; ++k)
+            if (piv[k] != k) {
+                const double t = x[k];
+                x[k] = x[piv[k]];
+                x[piv[k]] = t;
+            }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {  // unit lower triangle
+        const double xk = x[k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) x[i] -= LU[(int64_t)i * n + k] * xk;
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {  // upper triangle
+        if (threadIdx.x == 0) x[k] /= LU[(int64_t)k * n + k];
+        __syncthreads();
+        const double xk = x[k];
+        for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] -= LU[(int64_t)i * n + k] * xk;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Minv[(int64_t)i * n + j] = x[i];
+}
+
+// x = Minv b (one warp per row), b and x in T, arithmetic in FP64.
+template <typename T>
+__global__ void coarse_apply_kernel(int n, const double *__restrict__ Minv, const T *__restrict__ b, T *__restrict__ x,
+                                    const int *done) {
+    if (gated(done)) return;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int q = lane; q < n; q += 32) s += Minv[(int64_t)row * n + q] * (double)b[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = (T)s;
+}
+
+// One red-black Gauss-Seidel half sweep: cells of colour (i+j+k) mod 2.
+template <typename T>
+__global__ void rbgs_kernel(G3 g, const T *__restrict__ a7, const T *__restrict__ b, T *__restrict__ x, int colour,
+                            const int *done) {
+    if (gated(done)) return;
+    const int64_t n = g.n();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int i, j, k;
+    ijk(c, g, i, j, k);
+    if (((i + j + k) & 1) != colour) return;
+    const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+    T s = b[c];
+    if (k > 0) s -= a7[0 * n + c] * x[c - sz];
+    if (j > 0) s -= a7[1 * n + c] * x[c - sy];
+    if (i > 0) s -= a7[2 * n + c] * x[c - 1];
+    if (i < g.nx - 1) s -= a7[4 * n + c] * x[c + 1];
+    if (j < g.ny - 1) s -= a7[5 * n + c] * x[c + sy];
+    if (k < g.nz - 1) s -= a7[6 * n + c] * x[c + sz];
+    x[c] = s / a7[3 * n + c];
+}
+
+// b_coarse[C] = sum over the children f of C of (b_f - (A x)_f): residual and
+// restriction R = P^T fused.
+template <typename T>
+__global__ void residual_restrict_kernel(G3 f, const T *__restrict__ a7, const T *__restrict__ b,
+                                         const T *__restrict__ x, G3 cg, T *__restrict__ bc, const int *done) {
+    if (gated(done)) return;
+    const int64_t nc = cg.n(), n = f.n();
+    const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (C >= nc) return;
+    int I, J, K;
+    ijk(C, cg, I, J, K);
+    const int64_t sy = f.nx, sz = (int64_t)f.nx * f.ny;
+    T acc = T(0);
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+                if (i >= f.nx || j >= f.ny || k >= f.nz) continue;
+                const int64_t c = (int64_t)k * sz + (int64_t)j * sy + i;
+                T r = b[c] - a7[3 * n + c] * x[c];
+                if (k > 0) r -= a7[0 * n + c] * x[c - sz];
+                if (j > 0) r -= a7[1 * n + c] * x[c - sy];
+                if (i > 0) r -= a7[2 * n + c] * x[c - 1];
+                if (i < f.nx - 1) r -= a7[4 * n + c] * x[c + 1];
+                if (j < f.ny - 1) r -= a7[5 * n + c] * x[c + sy];
+                if (k < f.nz - 1) r -= a7[6 * n + c] * x[c + sz];
+                acc += r;
+            }
+    bc[C] = acc;
+}
+
+// x_fine += P x_coarse (injection of the box value).
+template <typename T>
+__global__ void prolong_add_kernel(G3 f, const T *__restrict__ xc, G3 cg, T *__restrict__ x, const int *done) {
+    if (gated(done)) return;
+    const int64_t n = f.n();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    int i, j, k;
+    ijk(c, f, i, j, k);
+    x[c] += xc[(int64_t)(k / 2) * cg.nx * cg.ny + (int64_t)(j / 2) * cg.nx + i / 2];
+}
+
+template <typename T>
+__global__ void zero_kernel(int64_t n, T *x, const int *done) {
+    if (gated(done)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = T(0);
+}
+
+// p_c = w_c . f_c
+template <typename T>
+__global__ void restrict_pressure_kernel(int64_t nb, const T *__restrict__ w, const T *__restrict__ f,
+                                         T *__restrict__ p, const int *done) {
+    if (gated(done)) return;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    p[c] = w[3 * c] * f[3 * c] + w[3 * c + 1] * f[3 * c + 1] + w[3 * c + 2] * f[3 * c + 2];
+}
+
+// x_c = (p_c, 0, 0) and r = f (the copy the stage-two residual starts from)
+template <typename T>
+__global__ void prolong_pressure_kernel(int64_t nb, const T *__restrict__ p, const T *__restrict__ f,
+                                        T *__restrict__ x, T *__restrict__ r, const int *done) {
+    if (gated(done)) return;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    x[3 * c] = p[c];
+    x[3 * c + 1] = T(0);
+    x[3 * c + 2] = T(0);
+    r[3 * c] = f[3 * c];
+    r[3 * c + 1] = f[3 * c + 1];
+    r[3 * c + 2] = f[3 * c + 2];
+}
+
+template <typename T>
+__global__ void add_kernel(int64_t n, const T *__restrict__ z, T *__restrict__ x, const int *done) {
+    if (gated(done)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += z[i];
+}
+
+unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+void free_cpr(Cpr *P) {
+    for (int l = 0; l < kMaxLevels; ++l)
+        for (void *p : {(void *)P->a7[l], P->a7f[l], P->x[l], P->b[l]})
+            if (p) cudaFree(p);
+    for (void *p : {(void *)P->w64, P->w, (void *)P->minv, (void *)P->dense, (void *)P->piv, (void *)P->work,
+                    P->r, P->z, P->xp})
+        if (p) cudaFree(p);
+    *P = Cpr();
+}
+
+cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, Cpr *P,
+                      int *status) {
+    free_cpr(P);
+    cudaStream_t st = A->stream;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    P->mixed = mixed;
+    P->sweeps = sweeps;
+    // level sizes: halve (ceil) each dimension while the level has more than max_coarse cells
+    G3 g{A->nx, A->ny, A->nz};
+    int nl = 0;
+    P->dims[nl][0] = g.nx, P->dims[nl][1] = g.ny, P->dims[nl][2] = g.nz;
+    ++nl;
+    max_levels = std::min(std::max(max_levels, 1), kMaxLevels);
+    while (nl < max_levels && g.n() > max_coarse) {
+        g = G3{(g.nx + 1) / 2, (g.ny + 1) / 2, (g.nz + 1) / 2};
+        P->dims[nl][0] = g.nx, P->dims[nl][1] = g.ny, P->dims[nl][2] = g.nz;
+        ++nl;
+    }
+    P->nlev = nl;
+    const int64_t nb = A->nb;
+    const int nc = (int)g.n();
+    P->ncoarse = nc;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    };
+    alloc((void **)&P->w64, sizeof(double) * 3 * nb);
+    alloc(&P->w, es * 3 * nb);
+    for (int l = 0; l < nl; ++l) {
+        const int64_t n = (int64_t)P->dims[l][0] * P->dims[l][1] * P->dims[l][2];
+        alloc((void **)&P->a7[l], sizeof(double) * 7 * n);
+        if (mixed) alloc(&P->a7f[l], sizeof(float) * 7 * n);
+        alloc(&P->x[l], es * n);
+        alloc(&P->b[l], es * n);
+    }
+    alloc((void **)&P->dense, sizeof(double) * nc * nc);
+    alloc((void **)&P->minv, sizeof(double) * nc * nc);
+    alloc((void **)&P->work, sizeof(double) * nc * nc);
+    alloc((void **)&P->piv, sizeof(int) * nc);
+    alloc(&P->r, es * 3 * nb);
+    alloc(&P->z, es * 3 * nb);
+    alloc(&P->xp, es * 3 * nb);
+    if (e != cudaSuccess) return e;
+    G3 g0{A->nx, A->ny, A->nz};
+    count_launches(1);
+    if (mixed)
+        qi_setup_kernel<float><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v32, P->w64, P->a7[0], status);
+    else
+        qi_setup_kernel<double><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v, P->w64, P->a7[0], status);
+    for (int l = 0; l + 1 < nl; ++l) {
+        G3 f{P->dims[l][0], P->dims[l][1], P->dims[l][2]}, c{P->dims[l + 1][0], P->dims[l + 1][1], P->dims[l + 1][2]};
+        count_launches(1);
+        gmg_coarsen_kernel<<<blocks(c.n()), 256, 0, st>>>(f, P->a7[l], c, P->a7[l + 1]);
+    }
+    G3 gc{P->dims[nl - 1][0], P->dims[nl - 1][1], P->dims[nl - 1][2]};
+    count_launches(3);
+    coarse_dense_kernel<<<blocks(nc), 256, 0, st>>>(gc, P->a7[nl - 1], P->dense);
+    coarse_lu_kernel<<<1, 1024, 0, st>>>(nc, P->dense, P->piv, status);
+    coarse_inverse_kernel<<<nc, 128, 0, st>>>(nc, P->dense, P->piv, P->minv, P->work);
+    if (mixed) {
+        count_launches(1 + nl);
+        cast_stencil<<<blocks(3 * nb), 256, 0, st>>>(3 * nb, P->w64, (float *)P->w);
+        for (int l = 0; l < nl; ++l) {
+            const int64_t n = (int64_t)P->dims[l][0] * P->dims[l][1] * P->dims[l][2];
+            cast_stencil<<<blocks(7 * n), 256, 0, st>>>(7 * n, P->a7[l], (float *)P->a7f[l]);
+        }
+    } else {
+        e = cudaMemcpyAsync(P->w, P->w64, sizeof(double) * 3 * nb, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
+// One V-cycle on level l from a zero initial guess: x[l] = V(b[l]).
+template <typename T>
+static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done) {
+    const T *a7 = P.mixed ? (const T *)P.a7f[l] : (const T *)P.a7[l];
+    T *x = (T *)P.x[l], *b = (T *)P.b[l];
+    G3 g{P.dims[l][0], P.dims[l][1], P.dims[l][2]};
+    const int64_t n = g.n();
+    if (l == P.nlev - 1) {
+        count_launches(1);
+        coarse_apply_kernel<T><<<blocks(n * 32), 256, 0, st>>>((int)n, P.minv, b, x, done);
+        return cudaGetLastError();
+    }
+    count_launches(1 + 2 * P.sweeps);
+    zero_kernel<T><<<blocks(n), 256, 0, st>>>(n, x, done);
+    for (int s = 0; s < P.sweeps; ++s) {
+        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 0, done);
+        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 1, done);
+    }
+    G3 c{P.dims[l + 1][0], P.dims[l + 1][1], P.dims[l + 1][2]};
+    count_launches(1);
+    residual_restrict_kernel<T><<<blocks(c.n()), 256, 0, st>>>(g, a7, b, x, c, (T *)P.b[l + 1], done);
+    cudaError_t e = vcycle<T>(P, l + 1, st, done);
+    if (e != cudaSuccess) return e;
+    count_launches(1 + 2 * P.sweeps);
+    prolong_add_kernel<T><<<blocks(n), 256, 0, st>>>(g, (const T *)P.x[l + 1], c, x, done);
+    for (int s = 0; s < P.sweeps; ++s) {
+        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 1, done);
+        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 0, done);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
+                      int *status, unsigned long long timeout_ns) {
+    cudaStream_t st = A->stream;
+    const int64_t nb = A->nb;
+    T *r = (T *)P.r, *z = (T *)P.z;
+    count_launches(1);
+    restrict_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.w, f, (T *)P.b[0], done);
+    cudaError_t e = vcycle<T>(P, 0, st, done);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    prolong_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.x[0], f, x, r, done);
+    e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
+                         : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
+    if (e != cudaSuccess) return e;
+    e = launch_ilu_apply_tiles<T>(A, tiles, r, z, done, status, timeout_ns);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    add_kernel<T><<<blocks(3 * nb), 256, 0, st>>>(3 * nb, z, x, done);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cpr_vcycle(const rsv_mat *A, const Cpr &P, const T *b, T *x) {
+    const int64_t n = A->nb;
+    cudaError_t e = cudaMemcpyAsync(P.b[0], b, sizeof(T) * n, cudaMemcpyDeviceToDevice, A->stream);
+    if (e == cudaSuccess) e = vcycle<T>(P, 0, A->stream, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, P.x[0], sizeof(T) * n, cudaMemcpyDeviceToDevice, A->stream);
+    return e;
+}
+
+template cudaError_t cpr_apply<double>(const rsv_mat *, const Cpr &, const IluTiles &, const double *, double *,
+                                       const int *, int *, unsigned long long);
+template cudaError_t cpr_apply<float>(const rsv_mat *, const Cpr &, const IluTiles &, const float *, float *,
+                                      const int *, int *, unsigned long long);
+template cudaError_t cpr_vcycle<double>(const rsv_mat *, const Cpr &, const double *, double *);
+template cudaError_t cpr_vcycle<float>(const rsv_mat *, const Cpr &, const float *, float *);
+
+}  // namespace rsv

@@ -20,6 +20,7 @@
 // (dot products still accumulate in FP64), then x += ||r|| d.
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -225,6 +226,7 @@ struct rsv_solver {
     float *dinv32 = nullptr;     // FP32 copy for mixed block Jacobi
     Schedule sch;
     IluTiles tiles;
+    Cpr cpr;
     double ms_setup = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -253,6 +255,9 @@ cudaError_t pc_apply(rsv_solver *s, const T *r, T *z, const int *done) {
     case RSV_PC_BILU0:
         return launch_ilu_apply_tiles<T>(s->A, s->tiles, r, z, done, &s->ds->status,
                                          (unsigned long long)s->p.watchdog * 1000ull);
+    case RSV_PC_CPR:
+        return cpr_apply<T>(s->A, s->cpr, s->tiles, r, z, done, &s->ds->status,
+                            (unsigned long long)s->p.watchdog * 1000ull);
     }
     return cudaErrorInvalidValue;
 }
@@ -473,6 +478,7 @@ void solver_free(rsv_solver *s) {
         if (p) cudaFree(p);
     free_schedule(&s->sch);
     free_tiles(&s->tiles);
+    free_cpr(&s->cpr);
     if (s->e0) cudaEventDestroy(s->e0);
     if (s->e1) cudaEventDestroy(s->e1);
     delete s;
@@ -548,19 +554,21 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     rsv_pc_params pcp;
     rsv_pc_params_default(&pcp);
     if (params) pcp = *params;
-    if (pc_type == RSV_PC_CPR) return RSV_ENOTSUP;
+    if (pcp.gmg_max_levels < 1 || pcp.gmg_max_levels > kMaxLevels || pcp.gmg_max_coarse < 1 ||
+        pcp.gmg_max_coarse > 1024 || pcp.gmg_sweeps < 0 || pcp.gmg_sweeps > 16)
+        return RSV_EINVAL;
     rsv_mat *A = s->A;
     s->pc_type = -1;
     RSV_CUDA_TRY(cudaEventRecord(s->e0, s->st));
     RSV_CUDA_TRY(cudaMemsetAsync(&s->ds->status, 0, sizeof(int), s->st));
-    if ((pc_type == RSV_PC_BJACOBI || pc_type == RSV_PC_BILU0) && !s->dinv)
+    if (pc_type != RSV_PC_NONE && !s->dinv)
         RSV_CUDA_TRY(cudaMalloc((void **)&s->dinv, sizeof(double) * 9 * std::max<int64_t>(A->nb, 1)));
     if (pc_type == RSV_PC_BJACOBI) {
         if (s->mixed && !s->dinv32)
             RSV_CUDA_TRY(cudaMalloc((void **)&s->dinv32, sizeof(float) * 9 * std::max<int64_t>(A->nb, 1)));
         RSV_CUDA_TRY(launch_bj_setup(A, s->mixed, s->dinv, s->mixed ? s->dinv32 : nullptr, &s->ds->status));
     }
-    if (pc_type == RSV_PC_BILU0) {
+    if (pc_type == RSV_PC_BILU0 || pc_type == RSV_PC_CPR) {
         if (!s->sch.cells) RSV_CUDA_TRY(build_schedule(A, &s->sch));
         RSV_CUDA_TRY(launch_ilu_setup(A, s->sch, s->mixed, s->dinv, &s->ds->status));
         if (s->mixed)
@@ -568,6 +576,9 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
         else
             RSV_CUDA_TRY(tiles_setup<double>(A, s->dinv, &s->tiles));
     }
+    if (pc_type == RSV_PC_CPR)
+        RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, &s->cpr,
+                               &s->ds->status));
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
     RSV_TRY(read_status(s, &status));
@@ -601,9 +612,41 @@ rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z) {
     return RSV_OK;
 }
 
+rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, double *a7_host) {
+    if (!s || s->pc_type != RSV_PC_CPR) return RSV_EINVAL;
+    const Cpr &P = s->cpr;
+    if (nlev) *nlev = P.nlev;
+    if (dims)
+        for (int l = 0; l < P.nlev; ++l)
+            for (int d = 0; d < 3; ++d) dims[3 * l + d] = P.dims[l][d];
+    const int64_t nb = s->A->nb;
+    if (w_host) RSV_CUDA_TRY(cudaMemcpyAsync(w_host, P.w64, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, s->st));
+    if (a7_host) {
+        // level stencils, concatenated, each converted from slot-major [7][n] to [n][7]
+        std::vector<double> buf;
+        int64_t off = 0;
+        for (int l = 0; l < P.nlev; ++l) {
+            const int64_t n = (int64_t)P.dims[l][0] * P.dims[l][1] * P.dims[l][2];
+            buf.resize(7 * n);
+            RSV_CUDA_TRY(cudaMemcpyAsync(buf.data(), P.a7[l], sizeof(double) * 7 * n, cudaMemcpyDeviceToHost, s->st));
+            RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+            for (int64_t c = 0; c < n; ++c)
+                for (int q = 0; q < 7; ++q) a7_host[off + 7 * c + q] = buf[(size_t)q * n + c];
+            off += 7 * n;
+        }
+    }
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    return RSV_OK;
+}
+
+rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x) {
+    if (!s || !b || !x || b == x || s->pc_type != RSV_PC_CPR || s->mixed) return RSV_EINVAL;
+    RSV_CUDA_TRY(cpr_vcycle<double>(s->A, s->cpr, b, x));
+    return RSV_OK;
+}
+
 rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host) {
-    if (!s || !dinv_host || !s->dinv || (s->pc_type != RSV_PC_BJACOBI && s->pc_type != RSV_PC_BILU0))
-        return RSV_EINVAL;
+    if (!s || !dinv_host || !s->dinv || s->pc_type == RSV_PC_NONE || s->pc_type < 0) return RSV_EINVAL;
     RSV_CUDA_TRY(cudaMemcpyAsync(dinv_host, s->dinv, sizeof(double) * 9 * s->A->nb, cudaMemcpyDeviceToHost, s->st));
     RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
     return RSV_OK;

@@ -1,0 +1,144 @@
+"""CPR preconditioner on the GPU (quasi-IMPES, GMG V-cycle, two-stage apply) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DIMS = [(20, 20, 10), (13, 7, 5), (33, 17, 9), (1, 1, 1), (40, 24, 16)]
+
+
+@pytest.fixture(scope="module")
+def rsv():
+    from tests.helpers import build_library
+    build_library()
+    import paper_1602_05901_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def _setup(rsv, p, precision="fp64", **pcp):
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, precision=precision)
+    s.setup("cpr", **pcp)
+    return A, s
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_hierarchy_matches_oracle(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=51)
+    A, s = _setup(rsv, p)
+    levels, w, a7s = s.cpr_info()
+    o = oracle.System.from_problem(p, pc="cpr")
+    assert o.setup_status == 0
+    _, w_or, a7_or = o.factors()
+    assert len(levels) == o.gmg_levels()
+    assert levels[0] == dims
+    assert np.allclose(w, w_or, rtol=1e-13, atol=1e-15)
+    scale = np.abs(a7_or).max(axis=1, keepdims=True)
+    assert np.all(np.abs(a7s[0] - a7_or) <= 1e-12 * scale)
+    cur, cdims = a7_or, dims
+    for lv in range(1, len(levels)):
+        cdims, cur = oracle.gmg_coarsen(*cdims, cur)
+        assert tuple(cdims) == levels[lv]
+        sc = np.abs(cur).max(axis=1, keepdims=True)
+        assert np.all(np.abs(a7s[lv] - cur) <= 1e-12 * sc), lv
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("sweeps,coarse", [(2, 512), (1, 8), (0, 64)])
+def test_vcycle_matches_oracle(rsv, torch, dims, sweeps, coarse):
+    p = synth.make_problem(*dims, seed=52)
+    A, s = _setup(rsv, p, gmg_sweeps=sweeps, gmg_max_coarse=coarse)
+    _, _, a7 = oracle.System.from_problem(p, pc="cpr").factors()
+    b = np.random.default_rng(53).standard_normal(p.nb)
+    st, e_or, nl = oracle.gmg_vcycle(*dims, a7, b, max_levels=6, max_coarse=coarse, sweeps=sweeps)
+    assert st == 0
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    s.vcycle(bd, xd)
+    torch.cuda.synchronize()
+    e = xd.cpu().numpy()
+    assert np.linalg.norm(e - e_or) <= 1e-10 * np.linalg.norm(e_or)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_cpr_apply_matches_oracle(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=54)
+    A, s = _setup(rsv, p)
+    o = oracle.System.from_problem(p, pc="cpr")
+    f = np.random.default_rng(55).standard_normal(p.n)
+    st, z_or = o.pc_apply(f)
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+
+
+@pytest.mark.parametrize("dims", [(20, 20, 10), (33, 17, 9)])
+def test_cpr_apply_fp32_matches_oracle(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=56)
+    A, s = _setup(rsv, p, precision="mixed")
+    of = oracle.System.from_problem(p, pc="cpr", float_round=True)
+    f = np.random.default_rng(57).standard_normal(p.n).astype(np.float32)
+    _, z_or = of.pc_apply(f.astype(np.float64))
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab", "fgmres"])
+def test_cpr_solve_tiny(rsv, torch, precision, solver):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, solver=solver, precision=precision, maxit=4000)
+    s.setup("cpr")
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_OK, (st, info)
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
+    if precision == "fp64":
+        its = []
+        for t in range(6):
+            bb = p.b if t == 0 else p.b * (1 + 1e-15 * np.random.default_rng(1000 + t).standard_normal(p.n))
+            o = oracle.System.from_problem(p, pc="cpr")
+            ost, _, oinfo = o.bicgstab(bb, maxit=4000) if solver == "bicgstab" else o.gmres(
+                bb, flexible=(solver == "fgmres"), maxit=4000)
+            assert ost == 0
+            its.append(oinfo["iters"])
+        assert 0.9 * min(its) - 2 <= info["iters"] <= 1.1 * max(its) + 2, (info, its)
+
+
+def test_cpr_mid_full_size(rsv, torch):
+    p = synth.workload("mid_100x100x50")
+    for precision in ("fp64", "mixed"):
+        A = rsv.Matrix(p.nx, p.ny, p.nz)
+        A.set_values(p.vals)
+        s = rsv.Solver(A, solver="gmres", precision=precision, maxit=4000)
+        s.setup("cpr")
+        levels, _, _ = s.cpr_info(with_arrays=False)
+        assert levels[0] == (100, 100, 50) and len(levels) == 5 and levels[-1] == (7, 7, 4)
+        b = torch.from_numpy(p.b).cuda()
+        x = torch.zeros_like(b)
+        st, info = s.solve(b, x)
+        assert st == 0, info
+        relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(
+            p.b)
+        assert relres <= 1e-8
