@@ -149,6 +149,22 @@ RSV_API rsv_status rsv_norm2(void *stream, int64_t n, const double *x, double *r
 RSV_API rsv_status rsv_axpby(void *stream, int64_t n, double alpha, const double *x, double beta,
                      const double *y, double *z);
 
+/* Multi-vector dot product that allocates nothing: result[i] = <w, V_i> for
+ * i < k, V_i = V + i*ldv (device float64 arrays; result on the host, the call
+ * synchronises the stream).  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory when they need a reduction
+ * (a device-memory budget already handed out, a callback that forbids
+ * allocation, a loop that must not risk an allocator synchronisation).
+ * Its reduction scratch is one fixed file-scope device array (about 160 KB,
+ * held by every GPU that loads the library until the process exits) instead
+ * of memory from the allocator; no call to it allocates or frees.
+ * Limits: 1 <= k <= 64 (RSV_EINVAL otherwise), ldv >= n.  The first call on
+ * a device resolves the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array, so calls whose GPU
+ * work overlaps (other streams, other host threads) race: serialise them. */
+RSV_API rsv_status rsv_mdot_noalloc(void *stream, int64_t n, const double *w, const double *V, int64_t ldv, int k,
+                                    double *result);
+
 /* ---- solver + preconditioner (Sections "Solvers", "Preconditioners") ----
  * The solver keeps a reference to A (A must outlive it) and allocates its
  * Krylov workspace on A's stream. */

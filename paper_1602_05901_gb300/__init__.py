@@ -74,6 +74,7 @@ _SIGS = {
     "rsv_dot": (_I, [_P, _I64, _P, _P, ctypes.POINTER(_D)]),
     "rsv_norm2": (_I, [_P, _I64, _P, ctypes.POINTER(_D)]),
     "rsv_axpby": (_I, [_P, _I64, _D, _P, _D, _P, _P]),
+    "rsv_mdot_noalloc": (_I, [_P, _I64, _P, _P, _I64, _I, _P]),
     "rsv_solver_create": (_I, [_P, ctypes.POINTER(rsv_solver_params), _PP]),
     "rsv_solver_destroy": (None, [_P]),
     "rsv_precond_setup": (_I, [_P, _I, ctypes.POINTER(rsv_pc_params)]),
