@@ -174,6 +174,42 @@ def run_reference(args, rank, ws):
     return 0
 
 
+def run_profile_mode(mode):
+    """Small, self-checking runs of the hot path for ncu (no timing is reported)."""
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+    p = synth.workload(WORKLOAD)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    if mode == "profile-solve":
+        s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=60, precision="mixed")
+        s.setup("bilu0")
+        b = torch.from_numpy(p.b).cuda()
+        x = torch.zeros_like(b)
+        st, info = s.solve(b, x)
+        torch.cuda.synchronize()
+        assert st in (rsv.RSV_OK, rsv.RSV_ENOCONV), st
+        print("profile-solve", info)
+        return 0
+    s32 = rsv.Solver(A, precision="mixed")
+    s32.setup("bilu0")
+    s64 = rsv.Solver(A, precision="fp64")
+    s64.setup("bilu0")
+    x = torch.randn(p.n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    x32, y32 = x.float(), torch.empty(p.n, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        A.spmv(x, y)
+        A.spmv(x32, y32)
+        s32.apply(x32, y32)
+        s64.apply(x, y)
+    torch.cuda.synchronize()
+    print("profile-kernels done")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,7 +220,14 @@ def main():
     ap.add_argument("--cpu-sample-iters", type=int, default=60)
     ap.add_argument("--ref-sample-iters", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile-solve", "profile-kernels"],
+                    help="profile-solve: one short mixed GMRES(30)+BILU0 solve (60 inner iterations) on the "
+                         "benchmark workload, for an ncu launch list; profile-kernels: set up the benchmark "
+                         "workload and run each hot kernel (FP64/FP32 SpMV, FP32/FP64 ILU(0) apply) three times, "
+                         "for ncu captures. Neither prints a benchmark line.")
     args = ap.parse_args()
+    if args.mode != "bench":
+        return run_profile_mode(args.mode)
     if args.warmup < 3 and args.impl == "rsv":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
