@@ -54,6 +54,15 @@ def spmv_bytes(nb, nnzb, val_bytes=8):
 
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA cores) from the pool's nominal table
 
+# DRAM bytes per launch (read + write) measured by one ncu capture of the current kernels on this
+# workload (profiles/ilu_apply_mid_100x100x50.md).  Set an entry to None whenever its kernel changes.
+NCU_TRAFFIC = {
+    "ilu_apply_f32": 208.8e6,   # gather_tiles + forward + backward sweep, FP32
+    "ilu_apply_f64": 464.1e6,
+    "spmv_f32": 148.2e6,
+    "spmv_f64": 284.4e6,
+}
+
 
 def ilu_apply_flops(nb, nnzb):
     """FP64/FP32 flops of one block ILU(0) apply: a 3x3 block-vector product (9 FMA) per
@@ -323,11 +332,12 @@ def main():
     # dominant kernel of the timed (mixed) path per inner iteration: FP32 ILU apply vs FP32 SpMV
     if ilu32_ms >= spmv32_ms:
         dom = {"kernel": "block ILU(0) apply, FP32 (forward+backward tile sweeps)", "ms": ilu32_ms, "bytes": ib32,
-               "gbs": ilu32_gbs}
+               "gbs": ilu32_gbs, "traffic": NCU_TRAFFIC["ilu_apply_f32"]}
     else:
-        dom = {"kernel": "BSR SpMV FP32", "ms": spmv32_ms, "bytes": sb32, "gbs": spmv32_gbs}
+        dom = {"kernel": "BSR SpMV FP32", "ms": spmv32_ms, "bytes": sb32, "gbs": spmv32_gbs,
+               "traffic": NCU_TRAFFIC["spmv_f32"]}
     roofline = {"bound": "hbm", "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(dom["gbs"] / peak, 4), "traffic": None, "kernel": dom["kernel"],
+                "frac": round(dom["gbs"] / peak, 4), "traffic": dom["traffic"], "kernel": dom["kernel"],
                 "algorithmic_bytes_per_launch": dom["bytes"], "avg_launch_ms": round(dom["ms"], 4),
                 "peak_source": peak_src}
 
