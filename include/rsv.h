@@ -126,6 +126,14 @@ RSV_API void rsv_grid_destroy(rsv_grid *g);
  * Values start at zero.  The grid may be destroyed afterwards. */
 RSV_API rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out);
 RSV_API void rsv_mat_destroy(rsv_mat *A);
+/* A batch of nsys independent grids (dims: int[nsys][3], nx ny nz each) as
+ * one block-diagonal matrix: grid s occupies cells [off_s, off_{s+1}) in
+ * bottom-up order, unknowns 3*cell + e; values are passed concatenated in
+ * the same order.  Solve it with rsv_solve_batched (independent systems) or
+ * rsv_solve (the block-diagonal system as a whole).  CPR needs a single grid. */
+RSV_API rsv_status rsv_mat_create_batch(int nsys, const int *dims, void *stream, rsv_mat **out);
+/* Number of grids and their cell offsets (int64[nsys+1]; either may be NULL). */
+RSV_API rsv_status rsv_mat_get_batch(const rsv_mat *A, int *nsys, int64_t *cell_offsets);
 /* Host views of the pattern, owned by the matrix (valid until destroy). */
 RSV_API rsv_status rsv_mat_get_pattern(const rsv_mat *A, const int32_t **row_ptr, const int32_t **col_idx,
                                int64_t *nb, int64_t *nnzb);
@@ -206,6 +214,18 @@ RSV_API rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host);
  * (on_device = 1); x holds the initial guess on entry and the solution on
  * return (also on ENOCONV).  info may be NULL. */
 RSV_API rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info);
+
+/* Batched solve (the batch extension of the paper's per-process solves; its
+ * systems are independent as the paper's subdomain systems are, Section
+ * "Grid", partition constraints): every grid of a batch matrix is solved on
+ * its own by right-preconditioned BiCGSTAB (solver type must be BICGSTAB,
+ * preconditioner NONE, BJACOBI or BILU0), with its own scalars, tolerance
+ * rtol * ||b_s||, iteration count and status; FP64 or FP32 inner solves
+ * under per-system FP64 refinement.  One pass over all systems is captured
+ * in a CUDA graph and replayed.  b, x: float64[3*nb] (host or device), x
+ * holds the initial guess; infos: rsv_solve_info[nsys] or NULL.  Returns the
+ * first non-OK per-system status, else RSV_OK. */
+RSV_API rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *infos);
 
 #ifdef __cplusplus
 }

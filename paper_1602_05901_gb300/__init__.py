@@ -67,6 +67,8 @@ _SIGS = {
     "rsv_grid_destroy": (None, [_P]),
     "rsv_mat_create": (_I, [_P, _P, _PP]),
     "rsv_mat_destroy": (None, [_P]),
+    "rsv_mat_create_batch": (_I, [_I, _P, _P, _PP]),
+    "rsv_mat_get_batch": (_I, [_P, ctypes.POINTER(_I), _P]),
     "rsv_mat_get_pattern": (_I, [_P, _PP, _PP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "rsv_mat_set_values": (_I, [_P, _P, _I]),
     "rsv_spmv": (_I, [_P, _D, _P, _D, _P]),
@@ -84,6 +86,7 @@ _SIGS = {
     "rsv_cpr_info": (_I, [_P, ctypes.POINTER(_I), _P, _P, _P]),
     "rsv_cpr_vcycle": (_I, [_P, _P, _P]),
     "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
+    "rsv_solve_batched": (_I, [_P, _P, _P, _I, _P]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -150,19 +153,32 @@ def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2):
 
 
 class Matrix:
-    """Seven-point 3x3-block BSR matrix of an nx*ny*nz grid, resident on the GPU."""
+    """Seven-point 3x3-block BSR matrix of an nx*ny*nz grid, resident on the GPU.
 
-    def __init__(self, nx, ny, nz, stream=None):
+    ``Matrix.batch([(nx, ny, nz), ...])`` builds the block-diagonal matrix of a
+    batch of independent grids (solve it with ``Solver.solve_batched``)."""
+
+    def __init__(self, nx, ny, nz, stream=None, _batch_dims=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.stream = _stream_ptr(stream)
-        g = ctypes.c_void_p()
-        check(_lib.rsv_grid_create(nx, ny, nz, ctypes.byref(g)), "rsv_grid_create")
         h = ctypes.c_void_p()
-        try:
-            check(_lib.rsv_mat_create(g, self.stream, ctypes.byref(h)), "rsv_mat_create")
-        finally:
-            _lib.rsv_grid_destroy(g)
+        if _batch_dims is None:
+            g = ctypes.c_void_p()
+            check(_lib.rsv_grid_create(nx, ny, nz, ctypes.byref(g)), "rsv_grid_create")
+            try:
+                check(_lib.rsv_mat_create(g, self.stream, ctypes.byref(h)), "rsv_mat_create")
+            finally:
+                _lib.rsv_grid_destroy(g)
+        else:
+            dims = np.ascontiguousarray(np.asarray(_batch_dims, dtype=np.int32).reshape(-1, 3))
+            check(_lib.rsv_mat_create_batch(len(dims), _ptr(dims), self.stream, ctypes.byref(h)),
+                  "rsv_mat_create_batch")
         self.handle = h
+        nsys = ctypes.c_int()
+        check(_lib.rsv_mat_get_batch(h, ctypes.byref(nsys), None))
+        self.nsys = nsys.value
+        self.cell_offsets = np.zeros(self.nsys + 1, dtype=np.int64)
+        check(_lib.rsv_mat_get_batch(h, None, _ptr(self.cell_offsets)))
         rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
         nb, nnzb = _I64(), _I64()
         check(_lib.rsv_mat_get_pattern(h, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(nb), ctypes.byref(nnzb)))
@@ -173,6 +189,11 @@ class Matrix:
     @property
     def n(self):
         return 3 * self.nb
+
+    @classmethod
+    def batch(cls, dims, stream=None):
+        d0 = dims[0]
+        return cls(d0[0], d0[1], d0[2], stream=stream, _batch_dims=dims)
 
     def set_values(self, vals):
         """vals: float64 [nnzb,3,3] as a numpy array (host) or CUDA torch tensor."""
@@ -253,6 +274,13 @@ class Solver:
         if raise_on_error:
             check(st, "rsv_solve")
         return st, info.as_dict()
+
+    def solve_batched(self, b, x):
+        """Independent per-grid solves of a batch matrix. Returns (status, [info dict per grid])."""
+        on_dev = int(hasattr(b, "is_cuda") and b.is_cuda)
+        infos = (rsv_solve_info * self.A.nsys)()
+        st = _lib.rsv_solve_batched(self.handle, _ptr(b), _ptr(x), on_dev, infos)
+        return st, [i.as_dict() for i in infos]
 
     def __del__(self):
         h = getattr(self, "handle", None)

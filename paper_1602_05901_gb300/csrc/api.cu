@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -92,6 +93,8 @@ void rsv_grid_destroy(rsv_grid *g) { delete g; }
 
 static void mat_free(rsv_mat *A) {
     if (!A) return;
+    if (A->d_sys) cudaFree(A->d_sys);
+    if (A->d_sys_of_cell) cudaFree(A->d_sys_of_cell);
     if (A->d_rp) cudaFree(A->d_rp);
     if (A->d_ci) cudaFree(A->d_ci);
     if (A->d_v) cudaFree(A->d_v);
@@ -99,32 +102,52 @@ static void mat_free(rsv_mat *A) {
     delete A;
 }
 
-rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
-    if (!g || !out) return RSV_EINVAL;
+}  // extern "C"
+
+namespace rsv {
+
+// Seven-point BSR pattern of one grid or of a block-diagonal batch of grids
+// (each grid's cells contiguous, bottom-up within the grid).
+rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, rsv_mat **out) {
+    const int nsys = (int)dims.size() / 3;
+    int64_t total = 0;
+    for (int s = 0; s < nsys; ++s) {
+        if (dims[3 * s] < 1 || dims[3 * s + 1] < 1 || dims[3 * s + 2] < 1) return RSV_EINVAL;
+        total += (int64_t)dims[3 * s] * dims[3 * s + 1] * dims[3 * s + 2];
+    }
+    if (nsys < 1 || 3 * total >= (1ll << 31) || 7 * total >= (1ll << 31)) return RSV_EINVAL;
     rsv_mat *A = new (std::nothrow) rsv_mat();
     if (!A) return RSV_ENOMEM;
-    A->nx = g->nx;
-    A->ny = g->ny;
-    A->nz = g->nz;
-    A->nb = (int64_t)g->nx * g->ny * g->nz;
-    A->stream = (cudaStream_t)stream;
-    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    A->nx = dims[0];
+    A->ny = dims[1];
+    A->nz = dims[2];
+    A->nsys = nsys;
+    A->nb = total;
+    A->stream = stream;
     A->h_rp.resize(A->nb + 1);
     A->h_ci.reserve(7 * A->nb);
     A->h_rp[0] = 0;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                const int32_t c = nx * ny * k + nx * j + i;
-                if (k > 0) A->h_ci.push_back(c - nx * ny);
-                if (j > 0) A->h_ci.push_back(c - nx);
-                if (i > 0) A->h_ci.push_back(c - 1);
-                A->h_ci.push_back(c);
-                if (i < nx - 1) A->h_ci.push_back(c + 1);
-                if (j < ny - 1) A->h_ci.push_back(c + nx);
-                if (k < nz - 1) A->h_ci.push_back(c + nx * ny);
-                A->h_rp[c + 1] = (int32_t)A->h_ci.size();
-            }
+    std::vector<int32_t> sys_of_cell(A->nb);
+    int64_t c0 = 0;
+    for (int s = 0; s < nsys; ++s) {
+        const int nx = dims[3 * s], ny = dims[3 * s + 1], nz = dims[3 * s + 2];
+        A->h_sys.push_back(SysGrid{nx, ny, nz, 0, c0});
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const int32_t c = (int32_t)(c0 + (int64_t)nx * ny * k + (int64_t)nx * j + i);
+                    if (k > 0) A->h_ci.push_back(c - nx * ny);
+                    if (j > 0) A->h_ci.push_back(c - nx);
+                    if (i > 0) A->h_ci.push_back(c - 1);
+                    A->h_ci.push_back(c);
+                    if (i < nx - 1) A->h_ci.push_back(c + 1);
+                    if (j < ny - 1) A->h_ci.push_back(c + nx);
+                    if (k < nz - 1) A->h_ci.push_back(c + nx * ny);
+                    A->h_rp[c + 1] = (int32_t)A->h_ci.size();
+                    sys_of_cell[c] = s;
+                }
+        c0 += (int64_t)nx * ny * nz;
+    }
     A->nnzb = (int64_t)A->h_ci.size();
     cudaError_t e;
     const size_t vbytes = sizeof(double) * (9 * (size_t)A->nnzb + 16);
@@ -132,9 +155,15 @@ rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
         (e = cudaMalloc((void **)&A->d_ci, sizeof(int32_t) * (A->nnzb + 16))) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_v, vbytes)) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_v32, vbytes / 2)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&A->d_sys, sizeof(SysGrid) * nsys)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&A->d_sys_of_cell, sizeof(int32_t) * A->nb)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A->d_rp, A->h_rp.data(), sizeof(int32_t) * (A->nb + 1), cudaMemcpyHostToDevice,
                              A->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A->d_ci, A->h_ci.data(), sizeof(int32_t) * A->nnzb, cudaMemcpyHostToDevice,
+                             A->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(A->d_sys, A->h_sys.data(), sizeof(SysGrid) * nsys, cudaMemcpyHostToDevice,
+                             A->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(A->d_sys_of_cell, sys_of_cell.data(), sizeof(int32_t) * A->nb, cudaMemcpyHostToDevice,
                              A->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(A->d_ci + A->nnzb, 0, sizeof(int32_t) * 16, A->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(A->d_v, 0, vbytes, A->stream)) != cudaSuccess ||
@@ -145,6 +174,30 @@ rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
         return cuda_status(e);
     }
     *out = A;
+    return RSV_OK;
+}
+
+}  // namespace rsv
+
+extern "C" {
+
+rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
+    if (!g || !out) return RSV_EINVAL;
+    return mat_create_grids({g->nx, g->ny, g->nz}, (cudaStream_t)stream, out);
+}
+
+rsv_status rsv_mat_create_batch(int nsys, const int *dims, void *stream, rsv_mat **out) {
+    if (nsys < 1 || nsys > (1 << 20) || !dims || !out) return RSV_EINVAL;
+    return mat_create_grids(std::vector<int>(dims, dims + 3 * (size_t)nsys), (cudaStream_t)stream, out);
+}
+
+rsv_status rsv_mat_get_batch(const rsv_mat *A, int *nsys, int64_t *cell_offsets) {
+    if (!A) return RSV_EINVAL;
+    if (nsys) *nsys = A->nsys;
+    if (cell_offsets) {
+        for (int s = 0; s < A->nsys; ++s) cell_offsets[s] = A->h_sys[s].cell0;
+        cell_offsets[A->nsys] = A->nb;
+    }
     return RSV_OK;
 }
 

@@ -56,11 +56,20 @@ struct DevState {
     unsigned counter[4];  // last-block tickets of the reduction kernels
 };
 
+struct TileSys {  // one grid of the tile sweeps
+    int nx, ny, nz, nTJ, nTK, S, poff, pad;  // S: steps per tile; poff: first position of the grid
+    int64_t cell0;
+};
+
 struct IluTiles {  // packed factor and buffers of the persistent tile sweeps (ilu_tiles.cu)
-    int nT = 0, nTK = 0, S = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
+    int nT = 0, maxS = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
+    int64_t rows = 0;         // step rows of all tiles
     size_t smem = 0;
+    TileSys *tsys = nullptr;  // per grid
+    int *tile_sys = nullptr;  // position -> grid
+    int64_t *tile_row0 = nullptr;  // position -> first step row
     int2 *order = nullptr;    // tile (J, K) per processing position
-    int *pos_of = nullptr;    // J * nTK + K -> position
+    int *pos_of = nullptr;    // grid poff + J * nTK + K -> position
     void *Ff = nullptr;       // forward factor rows  [nT][S][32][NQP]
     void *Fb = nullptr;       // backward factor rows [nT][S][32][NQP]
     void *Vf = nullptr;       // forward input in tile order [nT][S][32][4]
@@ -96,8 +105,21 @@ struct rsv_grid {
     int nx, ny, nz;
 };
 
+namespace rsv {
+// One structured grid of a (possibly batched) matrix: its dims and first cell.
+struct SysGrid {
+    int nx, ny, nz, pad;
+    int64_t cell0;
+};
+}  // namespace rsv
+
 struct rsv_mat {
-    int nx, ny, nz;
+    int nx, ny, nz;                 // dims of the first (for a single-grid matrix: the only) grid
+    int nsys = 1;                   // >1: block-diagonal batch of independent grids
+    std::vector<rsv::SysGrid> h_sys;
+    rsv::SysGrid *d_sys = nullptr;  // per grid
+    int32_t *d_sys_of_cell = nullptr;  // grid of each cell
+    int spmv_rows = 128;            // block rows per CTA of the SpMV (autotuned for batches)
     int64_t nb, nnzb;
     cudaStream_t stream;
     std::vector<int32_t> h_rp, h_ci;

@@ -125,9 +125,12 @@ __device__ __forceinline__ float value_of(unsigned v) { return __uint_as_float(v
 
 template <typename T>
 struct SweepArgs {
-    int nx, ny, nz, nT, nTK, S;
-    const int2 *order;   // position -> tile (J, K)
-    const int *pos_of;   // J * nTK + K -> position
+    int nT;                    // tiles of all grids
+    const TileSys *tsys;       // per grid
+    const int *tile_sys;       // position -> grid
+    const int64_t *tile_row0;  // position -> first step row of the tile in the packed arrays
+    const int2 *order;         // position -> tile (J, K) inside its grid
+    const int *pos_of;         // grid's poff + J * nTK + K -> position
     const T *F;          // factor rows [nT][S][32][NQP]
     const T *V;          // input vector in tile order [nT][S][32][4]
     T *Vnext;            // forward: y in backward tile order [nT][S][32][4]; backward: null
@@ -170,7 +173,6 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     uint64_t *ebars = bars + NSD;
     const int lane = threadIdx.x;
     const int a = lane & 7, b = lane >> 3;
-    const int nx = P.nx, ny = P.ny, nz = P.nz, S = P.S;
     if (lane == 0) {
         for (int q = 0; q < NSD + NSE; ++q) mbar_init(&bars[q], 1);
         fence_barrier_init();
@@ -179,16 +181,17 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     unsigned phase = 0, pending = 0;  // bit q: data stage q; bit NSD + q: edge stage q
     const uint64_t deadline = global_timer() + P.timeout_ns;
     bool failed = false;
-    const int nTJ = (ny + TJ - 1) / TJ;
 
     for (int t = blockIdx.x; t < P.nT && !failed; t += gridDim.x) {
         const int tt = FWD ? t : (P.nT - 1 - t);
+        const TileSys G = P.tsys[P.tile_sys[tt]];
+        const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S, nTJ = G.nTJ, nTK = G.nTK;
         const int2 JK = P.order[tt];
-        // producers of this tile's edge inputs
-        const int pj = FWD ? (JK.x > 0 ? P.pos_of[(JK.x - 1) * P.nTK + JK.y] : -1)
-                           : (JK.x + 1 < nTJ ? P.pos_of[(JK.x + 1) * P.nTK + JK.y] : -1);
-        const int pk = FWD ? (JK.y > 0 ? P.pos_of[JK.x * P.nTK + JK.y - 1] : -1)
-                           : (JK.y + 1 < P.nTK ? P.pos_of[JK.x * P.nTK + JK.y + 1] : -1);
+        // producers of this tile's edge inputs (same grid)
+        const int pj = FWD ? (JK.x > 0 ? P.pos_of[G.poff + (JK.x - 1) * nTK + JK.y] : -1)
+                           : (JK.x + 1 < nTJ ? P.pos_of[G.poff + (JK.x + 1) * nTK + JK.y] : -1);
+        const int pk = FWD ? (JK.y > 0 ? P.pos_of[G.poff + JK.x * nTK + JK.y - 1] : -1)
+                           : (JK.y + 1 < nTK ? P.pos_of[G.poff + JK.x * nTK + JK.y + 1] : -1);
         const int j = JK.x * TJ + a, k = JK.y * TK + b;
         const bool jk_ok = (j < ny) && (k < nz);
         const bool has_j = FWD ? (j > 0) : (j + 1 < ny);
@@ -200,12 +203,13 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         const int lane_j = (FWD ? lane - 1 : lane + 1) & 31;
         const int lane_k = (FWD ? lane - 8 : lane + 8) & 31;
         const int off = FWD ? (a + b) : ((TJ - 1 - a) + (TK - 1 - b));
-        const int64_t base = (int64_t)k * nx * ny + (int64_t)j * nx;
-        const size_t tile0 = (size_t)tt * S;
+        const int64_t base = G.cell0 + (int64_t)k * nx * ny + (int64_t)j * nx;
+        const size_t tile0 = (size_t)P.tile_row0[tt];
+        const size_t rowj = pj >= 0 ? (size_t)P.tile_row0[pj] : 0, rowk = pk >= 0 ? (size_t)P.tile_row0[pk] : 0;
         const T *Ft = P.F + tile0 * St::F;
         const T *Vt = P.V + tile0 * St::V;
-        const T *EJsrc = pj >= 0 ? P.EJ + (size_t)pj * S * St::EJ : nullptr;
-        const T *EKsrc = pk >= 0 ? P.EK + (size_t)pk * S * St::EK : nullptr;
+        const T *EJsrc = pj >= 0 ? P.EJ + rowj * St::EJ : nullptr;
+        const T *EKsrc = pk >= 0 ? P.EK + rowk * St::EK : nullptr;
         if (FWD) {
             // this tile's backward-sweep edge buffers start at the sentinel
             using U = typename Bits<T>::U;
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                 if (valid && edge_j && has_j) {
                     const T *e4 = estg + b * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(P.EJ + ((size_t)pj * S + s) * St::EJ + b * 4, v3, deadline)) failed = true;
+                    if (!poll3(P.EJ + (rowj + s) * St::EJ + b * 4, v3, deadline)) failed = true;
                     nj[0] = v3[0];
                     nj[1] = v3[1];
                     nj[2] = v3[2];
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                 if (valid && edge_k && has_k) {
                     const T *e4 = estg + St::EJ + a * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(P.EK + ((size_t)pk * S + s) * St::EK + a * 4, v3, deadline)) failed = true;
+                    if (!poll3(P.EK + (rowk + s) * St::EK + a * 4, v3, deadline)) failed = true;
                     nk[0] = v3[0];
                     nk[1] = v3[1];
                     nk[2] = v3[2];
@@ -400,27 +404,29 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
 // values come from `v` (FP64, or the FP32 copy for mixed precision); D^{-1}
 // from the FP64 factor; both are stored as T.
 template <typename T, typename Tv>
-__global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__restrict__ order,
+__global__ void pack_tiles(const TileSys *__restrict__ tsys, const int *__restrict__ tile_sys,
+                           const int64_t *__restrict__ tile_row0, const int2 *__restrict__ order,
                            const int32_t *__restrict__ rp, const Tv *__restrict__ v,
                            const double *__restrict__ dinv, T *__restrict__ Ff, T *__restrict__ Fb) {
     constexpr int NQP = Bits<T>::NQP;
+    const int t = blockIdx.y;
+    const TileSys G = tsys[tile_sys[t]];
+    const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)nT * S * 32;
-    if (gid >= total) return;
+    if (gid >= (int64_t)S * 32) return;
     const int lane = (int)(gid & 31);
-    const int s = (int)((gid >> 5) % S);
-    const int t = (int)((gid >> 5) / S);
+    const int s = (int)(gid >> 5);
     const int a = lane & 7, b = lane >> 3;
     const int2 JK = order[t];
     const int j = JK.x * TJ + a, k = JK.y * TK + b;
     for (int dir = 0; dir < 2; ++dir) {
         const bool fwd = dir == 0;
         const int i = fwd ? (s - a - b) : (nx - 1 - (s - (TJ - 1 - a) - (TK - 1 - b)));
-        T *out = (fwd ? Ff : Fb) + (((size_t)t * S + s) * 32 + lane) * NQP;
+        T *out = (fwd ? Ff : Fb) + (((size_t)tile_row0[t] + s) * 32 + lane) * NQP;
         const bool valid = j < ny && k < nz && i >= 0 && i < nx;
         for (int q = 0; q < NQP; ++q) out[q] = T(0);
         if (!valid) continue;
-        const int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
+        const int64_t c = G.cell0 + (int64_t)k * nx * ny + (int64_t)j * nx + i;
         // slots of the row: -z, -y, -x, self, +x, +y, +z (absent faces skipped)
         int q = 0, mz = -1, my = -1, mx = -1, px = -1, py = -1, pz = -1;
         if (k > 0) mz = q++;
@@ -441,21 +447,24 @@ __global__ void pack_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__
 // Before a forward sweep: r into tile order, and the forward edge buffers to
 // the sentinel.  One thread per (tile, step, lane).
 template <typename T>
-__global__ void gather_tiles(int nx, int ny, int nz, int nT, int S, const int2 *__restrict__ order,
+__global__ void gather_tiles(const TileSys *__restrict__ tsys, const int *__restrict__ tile_sys,
+                             const int64_t *__restrict__ tile_row0, const int2 *__restrict__ order,
                              const T *__restrict__ r, T *__restrict__ Vt, T *__restrict__ EJ, T *__restrict__ EK) {
     using U = typename Bits<T>::U;
+    const int t = blockIdx.y;
+    const TileSys G = tsys[tile_sys[t]];
+    const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)nT * S * 32;
-    if (gid >= total) return;
+    if (gid >= (int64_t)S * 32) return;
     const int lane = (int)(gid & 31);
-    const int s = (int)((gid >> 5) % S);
-    const int t = (int)((gid >> 5) / S);
+    const int s = (int)(gid >> 5);
     const int a = lane & 7, b = lane >> 3;
     const int2 JK = order[t];
     const int j = JK.x * TJ + a, k = JK.y * TK + b, i = s - a - b;
-    T *o = Vt + (((size_t)t * S + s) * 32 + lane) * 4;
+    const size_t row = (size_t)tile_row0[t] + s;
+    T *o = Vt + (row * 32 + lane) * 4;
     if (j < ny && k < nz && i >= 0 && i < nx) {
-        const int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
+        const int64_t c = G.cell0 + (int64_t)k * nx * ny + (int64_t)j * nx + i;
         o[0] = r[3 * c];
         o[1] = r[3 * c + 1];
         o[2] = r[3 * c + 2];
@@ -463,9 +472,8 @@ __global__ void gather_tiles(int nx, int ny, int nz, int nT, int S, const int2 *
         o[0] = o[1] = o[2] = T(0);
     }
     o[3] = T(0);
-    // edge buffers [t][s][TK][4] and [t][s][TJ][4]: the 32 threads of a (t, s) row
+    // edge buffers [row][TK][4] and [row][TJ][4]: the 32 threads of a (t, s) row
     // cover its 16 + 32 entries
-    const size_t row = (size_t)t * S + s;
     if (lane < TK * 4) reinterpret_cast<U *>(EJ)[row * TK * 4 + lane] = Bits<T>::SENT;
     reinterpret_cast<U *>(EK)[row * TJ * 4 + lane] = Bits<T>::SENT;
 }
@@ -475,29 +483,47 @@ __global__ void gather_tiles(int nx, int ny, int nz, int nT, int S, const int2 *
 template <typename T>
 cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
     using St = Stage<T>;
-    const int nx = A->nx, ny = A->ny, nz = A->nz;
-    const int nTJ = (ny + TJ - 1) / TJ, nTK = (nz + TK - 1) / TK;
-    const int nT = nTJ * nTK;
-    const int S = nx + TJ + TK - 2;
     cudaError_t e = cudaSuccess;
-    if (!Tl->Ff || Tl->nT != nT || Tl->S != S || Tl->elem != (int)sizeof(T)) {
+    if (!Tl->Ff || Tl->elem != (int)sizeof(T)) {
         free_tiles(Tl);
+        // tiles of every grid, each grid's tiles in order of J+K, grids one after another
+        std::vector<TileSys> sys;
         std::vector<int2> order;
-        std::vector<int> pos(nT);
-        order.reserve(nT);
-        for (int d = 0; d <= nTJ + nTK - 2; ++d)
-            for (int J = 0; J < nTJ; ++J) {
-                const int K = d - J;
-                if (K >= 0 && K < nTK) {
-                    pos[J * nTK + K] = (int)order.size();
+        std::vector<int> tile_sys, pos;
+        std::vector<int64_t> row0;
+        int64_t rows = 0;
+        int maxS = 0;
+        for (int g = 0; g < A->nsys; ++g) {
+            const SysGrid &sg = A->h_sys[g];
+            TileSys ts;
+            ts.nx = sg.nx;
+            ts.ny = sg.ny;
+            ts.nz = sg.nz;
+            ts.nTJ = (sg.ny + TJ - 1) / TJ;
+            ts.nTK = (sg.nz + TK - 1) / TK;
+            ts.S = sg.nx + TJ + TK - 2;
+            ts.cell0 = sg.cell0;
+            ts.poff = (int)order.size();
+            maxS = std::max(maxS, ts.S);
+            pos.resize(order.size() + (size_t)ts.nTJ * ts.nTK);
+            for (int d = 0; d <= ts.nTJ + ts.nTK - 2; ++d)
+                for (int J = 0; J < ts.nTJ; ++J) {
+                    const int K = d - J;
+                    if (K < 0 || K >= ts.nTK) continue;
+                    pos[ts.poff + J * ts.nTK + K] = (int)order.size();
                     order.push_back(make_int2(J, K));
+                    tile_sys.push_back(g);
+                    row0.push_back(rows);
+                    rows += ts.S;
                 }
-            }
+            sys.push_back(ts);
+        }
+        const int nT = (int)order.size();
+        if (nT > 65535) return cudaErrorInvalidConfiguration;  // tiles index blockIdx.y of the pack/gather grids
         Tl->nT = nT;
-        Tl->S = S;
-        Tl->nTK = nTK;
+        Tl->maxS = maxS;
+        Tl->rows = rows;
         Tl->elem = (int)sizeof(T);
-        const size_t rows = (size_t)nT * S;
         auto alloc = [&](void **p, size_t bytes) {
             if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
         };
@@ -511,11 +537,20 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
         alloc(&Tl->EKb, rows * St::EKB);
         alloc((void **)&Tl->order, sizeof(int2) * nT);
         alloc((void **)&Tl->pos_of, sizeof(int) * nT);
+        alloc((void **)&Tl->tile_sys, sizeof(int) * nT);
+        alloc((void **)&Tl->tile_row0, sizeof(int64_t) * nT);
+        alloc((void **)&Tl->tsys, sizeof(TileSys) * sys.size());
         if (e != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(Tl->order, order.data(), sizeof(int2) * nT, cudaMemcpyHostToDevice, A->stream)) !=
                 cudaSuccess ||
             (e = cudaMemcpyAsync(Tl->pos_of, pos.data(), sizeof(int) * nT, cudaMemcpyHostToDevice, A->stream)) !=
                 cudaSuccess ||
+            (e = cudaMemcpyAsync(Tl->tile_sys, tile_sys.data(), sizeof(int) * nT, cudaMemcpyHostToDevice,
+                                 A->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(Tl->tile_row0, row0.data(), sizeof(int64_t) * nT, cudaMemcpyHostToDevice,
+                                 A->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(Tl->tsys, sys.data(), sizeof(TileSys) * sys.size(), cudaMemcpyHostToDevice,
+                                 A->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(A->stream)) != cudaSuccess)
             return e;
         int dev = 0, sms = 0, per_f = 0, per_b = 0;
@@ -536,21 +571,20 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
         Tl->grid = std::max(1, std::min(nT, sms * std::min(per_f, per_b)));
         Tl->smem = smem;
     }
-    const int64_t total = (int64_t)nT * S * 32;
-    const unsigned g = (unsigned)((total + 255) / 256);
+    const dim3 g((unsigned)((Tl->maxS * 32 + 255) / 256), (unsigned)Tl->nT);
     rsv::count_launches(1);
     if (sizeof(T) == 8)
-        pack_tiles<T, double><<<g, 256, 0, A->stream>>>(nx, ny, nz, nT, S, Tl->order, A->d_rp, A->d_v, dinv,
-                                                        (T *)Tl->Ff, (T *)Tl->Fb);
+        pack_tiles<T, double><<<g, 256, 0, A->stream>>>(Tl->tsys, Tl->tile_sys, Tl->tile_row0, Tl->order, A->d_rp,
+                                                        A->d_v, dinv, (T *)Tl->Ff, (T *)Tl->Fb);
     else
-        pack_tiles<T, float><<<g, 256, 0, A->stream>>>(nx, ny, nz, nT, S, Tl->order, A->d_rp, A->d_v32, dinv,
-                                                       (T *)Tl->Ff, (T *)Tl->Fb);
+        pack_tiles<T, float><<<g, 256, 0, A->stream>>>(Tl->tsys, Tl->tile_sys, Tl->tile_row0, Tl->order, A->d_rp,
+                                                       A->d_v32, dinv, (T *)Tl->Ff, (T *)Tl->Fb);
     return cudaGetLastError();
 }
 
 void free_tiles(IluTiles *Tl) {
     for (void *p : {Tl->Ff, Tl->Fb, Tl->Vf, Tl->Vb, Tl->EJf, Tl->EKf, Tl->EJb, Tl->EKb, (void *)Tl->order,
-                    (void *)Tl->pos_of})
+                    (void *)Tl->pos_of, (void *)Tl->tile_sys, (void *)Tl->tile_row0, (void *)Tl->tsys})
         if (p) cudaFree(p);
     *Tl = IluTiles();
 }
@@ -558,16 +592,16 @@ void free_tiles(IluTiles *Tl) {
 template <typename T>
 cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &Tl, const T *r, T *z, const int *done,
                                    int *status, unsigned long long timeout_ns) {
-    const int64_t total = (int64_t)Tl.nT * Tl.S * 32;
     rsv::count_launches(3);
-    gather_tiles<T><<<(unsigned)((total + 255) / 256), 256, 0, A->stream>>>(
-        A->nx, A->ny, A->nz, Tl.nT, Tl.S, Tl.order, r, (T *)Tl.Vf, (T *)Tl.EJf, (T *)Tl.EKf);
+    const dim3 g((unsigned)((Tl.maxS * 32 + 255) / 256), (unsigned)Tl.nT);
+    gather_tiles<T><<<g, 256, 0, A->stream>>>(Tl.tsys, Tl.tile_sys, Tl.tile_row0, Tl.order, r, (T *)Tl.Vf,
+                                              (T *)Tl.EJf, (T *)Tl.EKf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    SweepArgs<T> f{A->nx, A->ny, A->nz, Tl.nT, Tl.nTK, Tl.S, Tl.order, Tl.pos_of, (const T *)Tl.Ff,
+    SweepArgs<T> f{Tl.nT, Tl.tsys, Tl.tile_sys, Tl.tile_row0, Tl.order, Tl.pos_of, (const T *)Tl.Ff,
                    (const T *)Tl.Vf, (T *)Tl.Vb, nullptr, (T *)Tl.EJf, (T *)Tl.EKf, (T *)Tl.EJb, (T *)Tl.EKb,
                    done, status, timeout_ns};
-    SweepArgs<T> bw{A->nx, A->ny, A->nz, Tl.nT, Tl.nTK, Tl.S, Tl.order, Tl.pos_of, (const T *)Tl.Fb,
+    SweepArgs<T> bw{Tl.nT, Tl.tsys, Tl.tile_sys, Tl.tile_row0, Tl.order, Tl.pos_of, (const T *)Tl.Fb,
                     (const T *)Tl.Vb, nullptr, z, (T *)Tl.EJb, (T *)Tl.EKb, nullptr, nullptr,
                     done, status, timeout_ns};
     void *fa[] = {&f};

@@ -78,12 +78,22 @@ __device__ __forceinline__ void load9(const Tv *p, double *o) {
 
 // dinv_c = A_cc^{-1} in FP64 from the FP64 values or their FP32 copy; dinv32
 // (optional) receives the FP32 rounding used by mixed-precision applies.
+// Grid of global cell c and c's index inside it.
+__device__ __forceinline__ Dims grid_of(int64_t c, const SysGrid *sys, const int32_t *sys_of_cell, int &local) {
+    const SysGrid g = sys[sys_of_cell[c]];
+    local = (int)(c - g.cell0);
+    return Dims{g.nx, g.ny, g.nz};
+}
+
 template <typename Tv>
-__global__ void bj_setup_kernel(int64_t nb, Dims g, const int32_t *__restrict__ rp, const Tv *__restrict__ v,
+__global__ void bj_setup_kernel(int64_t nb, const SysGrid *__restrict__ sys, const int32_t *__restrict__ sys_of_cell,
+                                const int32_t *__restrict__ rp, const Tv *__restrict__ v,
                                 double *__restrict__ dinv, float *__restrict__ dinv32, int *status) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= nb) return;
-    const RowSlots s = row_slots((int)c, g);
+    int local;
+    const Dims g = grid_of(c, sys, sys_of_cell, local);
+    const RowSlots s = row_slots(local, g);
     double a[9];
     load9(v + 9 * (int64_t)(rp[c] + s.d), a);
     if (!inv3(a, dinv + 9 * c)) atomicCAS(status, 0, (int)RSV_ESINGULAR);
@@ -109,12 +119,15 @@ __global__ void bj_apply_kernel(int64_t nb, const T *__restrict__ dinv, const T 
 // D_c = A_cc - sum_{l lower} (A_cl D_l^{-1}) A_lc, lower neighbours in
 // ascending column order (-z, -y, -x).
 template <typename Tv>
-__global__ void ilu_factor_plane(Dims g, const int32_t *__restrict__ rp, const Tv *__restrict__ v,
+__global__ void ilu_factor_plane(const SysGrid *__restrict__ sys, const int32_t *__restrict__ sys_of_cell,
+                                 const int32_t *__restrict__ rp, const Tv *__restrict__ v,
                                  const int32_t *__restrict__ cells, int p0, int p1, double *dinv, int *status) {
     const int t = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p1) return;
     const int c = cells[t];
-    const RowSlots s = row_slots(c, g);
+    int local;
+    const Dims g = grid_of(c, sys, sys_of_cell, local);
+    const RowSlots s = row_slots(local, g);
     const int64_t base = rp[c];
     double D[9];
     load9(v + 9 * (base + s.d), D);
@@ -123,7 +136,7 @@ __global__ void ilu_factor_plane(Dims g, const int32_t *__restrict__ rp, const T
     for (int q = 0; q < 3; ++q) {
         if (lower[q] < 0) continue;
         const int l = c - loff[q];
-        const RowSlots sl = row_slots(l, g);
+        const RowSlots sl = row_slots(local - loff[q], g);
         const int up = (q == 0) ? sl.pz : (q == 1) ? sl.py : sl.px;  // block of row l in column c
         double Acl[9], Dl[9], Alc[9], T[9], U[9];
         load9(v + 9 * (base + lower[q]), Acl);
@@ -142,19 +155,22 @@ constexpr int kPlaneThreads = 128;
 }  // namespace
 
 cudaError_t build_schedule(const rsv_mat *A, Schedule *sch) {
-    const int nx = A->nx, ny = A->ny, nz = A->nz;
-    const int nplanes = nx + ny + nz - 2;
+    // hyperplane h = i+j+k inside each grid; plane h of every grid of a batch shares one launch
+    int nplanes = 0;
+    for (const SysGrid &g : A->h_sys) nplanes = std::max(nplanes, g.nx + g.ny + g.nz - 2);
     std::vector<int> count(nplanes + 1, 0);
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) count[i + j + k + 1]++;
+    for (const SysGrid &g : A->h_sys)
+        for (int k = 0; k < g.nz; ++k)
+            for (int j = 0; j < g.ny; ++j)
+                for (int i = 0; i < g.nx; ++i) count[i + j + k + 1]++;
     for (int h = 0; h < nplanes; ++h) count[h + 1] += count[h];
     std::vector<int32_t> cells(A->nb);
     std::vector<int> fill(count.begin(), count.end() - 1);
-    for (int64_t c = 0; c < A->nb; ++c) {
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
-        cells[fill[i + j + k]++] = (int32_t)c;
-    }
+    for (const SysGrid &g : A->h_sys)
+        for (int64_t l = 0; l < (int64_t)g.nx * g.ny * g.nz; ++l) {
+            const int i = (int)(l % g.nx), j = (int)((l / g.nx) % g.ny), k = (int)(l / ((int64_t)g.nx * g.ny));
+            cells[fill[i + j + k]++] = (int32_t)(g.cell0 + l);
+        }
     sch->plane_ptr = count;
     sch->nplanes = nplanes;
     cudaError_t e = cudaMallocAsync((void **)&sch->cells, sizeof(int32_t) * std::max<int64_t>(A->nb, 1), A->stream);
@@ -170,13 +186,14 @@ void free_schedule(Schedule *sch) {
 }
 
 cudaError_t launch_bj_setup(const rsv_mat *A, bool from_f32, double *dinv, float *dinv32, int *status) {
-    Dims g{A->nx, A->ny, A->nz};
     int grid = (int)((A->nb + 127) / 128);
     rsv::count_launches(1);
     if (from_f32)
-        bj_setup_kernel<float><<<grid, 128, 0, A->stream>>>(A->nb, g, A->d_rp, A->d_v32, dinv, dinv32, status);
+        bj_setup_kernel<float><<<grid, 128, 0, A->stream>>>(A->nb, A->d_sys, A->d_sys_of_cell, A->d_rp, A->d_v32,
+                                                            dinv, dinv32, status);
     else
-        bj_setup_kernel<double><<<grid, 128, 0, A->stream>>>(A->nb, g, A->d_rp, A->d_v, dinv, dinv32, status);
+        bj_setup_kernel<double><<<grid, 128, 0, A->stream>>>(A->nb, A->d_sys, A->d_sys_of_cell, A->d_rp, A->d_v,
+                                                             dinv, dinv32, status);
     return cudaGetLastError();
 }
 
@@ -193,17 +210,16 @@ template cudaError_t launch_bj_apply<float>(cudaStream_t, int64_t, const float *
                                             const int *);
 
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status) {
-    Dims g{A->nx, A->ny, A->nz};
     for (int h = 0; h < sch.nplanes; ++h) {
         const int p0 = sch.plane_ptr[h], p1 = sch.plane_ptr[h + 1];
         const int grid = (p1 - p0 + kPlaneThreads - 1) / kPlaneThreads;
         rsv::count_launches(1);
         if (from_f32)
-            ilu_factor_plane<float><<<grid, kPlaneThreads, 0, A->stream>>>(g, A->d_rp, A->d_v32, sch.cells, p0, p1,
-                                                                           dinv, status);
+            ilu_factor_plane<float><<<grid, kPlaneThreads, 0, A->stream>>>(A->d_sys, A->d_sys_of_cell, A->d_rp,
+                                                                           A->d_v32, sch.cells, p0, p1, dinv, status);
         else
-            ilu_factor_plane<double><<<grid, kPlaneThreads, 0, A->stream>>>(g, A->d_rp, A->d_v, sch.cells, p0, p1,
-                                                                            dinv, status);
+            ilu_factor_plane<double><<<grid, kPlaneThreads, 0, A->stream>>>(A->d_sys, A->d_sys_of_cell, A->d_rp,
+                                                                            A->d_v, sch.cells, p0, p1, dinv, status);
     }
     return cudaGetLastError();
 }

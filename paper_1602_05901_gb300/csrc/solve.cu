@@ -22,7 +22,7 @@
 #include <new>
 #include <vector>
 
-#include "common.cuh"
+#include "solver.cuh"
 
 namespace rsv {
 namespace {
@@ -198,78 +198,7 @@ int egrid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 2
 
 using namespace rsv;
 
-// Krylov workspace of one vector precision.
-struct KrylovWork {
-    void *V = nullptr;   // (m+1) basis vectors (GMRES) or 8 vectors (BiCGSTAB)
-    void *Z = nullptr;   // m preconditioned vectors (FGMRES)
-    void *w = nullptr;   // scratch
-    void *t = nullptr;   // scratch
-};
-
-struct rsv_solver {
-    rsv_mat *A = nullptr;
-    rsv_solver_params p{};
-    cudaStream_t st = nullptr;
-    int64_t n = 0;
-    int64_t ldv = 0;             // leading dimension of the Krylov vectors (n rounded up to 4)
-    int pc_type = -1;
-    rsv_pc_params pcp{};
-    uint64_t pc_version = ~0ull;
-    bool mixed = false;
-    DevState *ds = nullptr;
-    double *partial = nullptr;
-    KrylovWork kw;               // FP64 work (FP64 solves) or FP32 work (mixed inner solves)
-    double *r64 = nullptr;       // FP64 residual (true residual / refinement)
-    double *d_b = nullptr, *d_x = nullptr;  // staging for host buffers
-    float *rf = nullptr, *df = nullptr;     // mixed: scaled inner right-hand side and correction
-    double *dinv = nullptr;      // FP64 inverted diagonal blocks (Jacobi: A_ii^-1, ILU: D_i^-1)
-    float *dinv32 = nullptr;     // FP32 copy for mixed block Jacobi
-    Schedule sch;
-    IluTiles tiles;
-    Cpr cpr;
-    double ms_setup = 0.0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-};
-
 namespace {
-
-template <typename T>
-cudaError_t spmv(rsv_solver *s, T alpha, const T *x, T beta, T *y, const int *done);
-template <>
-cudaError_t spmv<double>(rsv_solver *s, double alpha, const double *x, double beta, double *y, const int *done) {
-    return launch_spmv_f64(s->A, alpha, x, beta, y, done);
-}
-template <>
-cudaError_t spmv<float>(rsv_solver *s, float alpha, const float *x, float beta, float *y, const int *done) {
-    return launch_spmv_f32(s->A, alpha, x, beta, y, done);
-}
-
-// z = M^{-1} r on the solver stream in precision T; `done` gates the kernels.
-template <typename T>
-cudaError_t pc_apply(rsv_solver *s, const T *r, T *z, const int *done) {
-    switch (s->pc_type) {
-    case RSV_PC_NONE: return cudaMemcpyAsync(z, r, sizeof(T) * s->n, cudaMemcpyDeviceToDevice, s->st);
-    case RSV_PC_BJACOBI:
-        if (sizeof(T) == 8) return launch_bj_apply<T>(s->st, s->A->nb, (const T *)s->dinv, r, z, done);
-        return launch_bj_apply<T>(s->st, s->A->nb, (const T *)s->dinv32, r, z, done);
-    case RSV_PC_BILU0:
-        return launch_ilu_apply_tiles<T>(s->A, s->tiles, r, z, done, &s->ds->status,
-                                         (unsigned long long)s->p.watchdog * 1000ull);
-    case RSV_PC_CPR:
-        return cpr_apply<T>(s->A, s->cpr, s->tiles, r, z, done, &s->ds->status,
-                            (unsigned long long)s->p.watchdog * 1000ull);
-    }
-    return cudaErrorInvalidValue;
-}
-
-// r = b - A x and ||r|| into *nrm (device)
-template <typename T>
-cudaError_t residual(rsv_solver *s, const T *b, const T *x, T *r, double *nrm) {
-    cudaError_t e = cudaMemcpyAsync(r, b, sizeof(T) * s->n, cudaMemcpyDeviceToDevice, s->st);
-    if (e == cudaSuccess) e = spmv<T>(s, T(-1), x, T(1), r, nullptr);
-    if (e == cudaSuccess) e = launch_dot<T>(s->st, s->n, r, r, s->partial, nrm, &s->ds->counter[0], 1, nullptr);
-    return e;
-}
 
 struct HostState {
     double beta;
@@ -479,6 +408,7 @@ void solver_free(rsv_solver *s) {
     free_schedule(&s->sch);
     free_tiles(&s->tiles);
     free_cpr(&s->cpr);
+    free_batch(s);
     if (s->e0) cudaEventDestroy(s->e0);
     if (s->e1) cudaEventDestroy(s->e1);
     delete s;
@@ -576,6 +506,7 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
         else
             RSV_CUDA_TRY(tiles_setup<double>(A, s->dinv, &s->tiles));
     }
+    if (pc_type == RSV_PC_CPR && A->nsys > 1) return RSV_ENOTSUP;
     if (pc_type == RSV_PC_CPR)
         RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, &s->cpr,
                                &s->ds->status));

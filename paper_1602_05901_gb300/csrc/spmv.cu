@@ -107,33 +107,49 @@ __global__ void cast_f64_f32(int64_t n, const double *__restrict__ a, float *__r
 
 }  // namespace
 
+template <typename T, int R>
+cudaError_t spmv_attr() {
+    return cudaFuncSetAttribute((const void *)spmv_bsr3_tma<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SpmvSmem<T, R>::BYTES);
+}
+
+template <typename T, int R>
+cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done) {
+    const int grid = (int)((A->nb + R - 1) / R);
+    rsv::count_launches(1);
+    spmv_bsr3_tma<T, R><<<grid, 3 * R, SpmvSmem<T, R>::BYTES, A->stream>>>((int)A->nb, A->d_rp, A->d_ci, v, alpha,
+                                                                           x, beta, y, done);
+    return cudaGetLastError();
+}
+
+// Block rows per CTA: 128 by default; batches pick 32, 64 or 128 by timing.
+template <typename T>
+cudaError_t spmv_dispatch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done) {
+    if (A->nb == 0) return cudaSuccess;
+    switch (A->spmv_rows) {
+    case 32: return spmv_launch<T, 32>(A, v, alpha, x, beta, y, done);
+    case 64: return spmv_launch<T, 64>(A, v, alpha, x, beta, y, done);
+    default: return spmv_launch<T, kRows>(A, v, alpha, x, beta, y, done);
+    }
+}
+
 cudaError_t spmv_init() {
-    cudaError_t e = cudaFuncSetAttribute((const void *)spmv_bsr3_tma<double, kRows>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SpmvSmem<double, kRows>::BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void *)spmv_bsr3_tma<float, kRows>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SpmvSmem<float, kRows>::BYTES);
+    cudaError_t e;
+    if ((e = spmv_attr<double, 32>()) != cudaSuccess || (e = spmv_attr<double, 64>()) != cudaSuccess ||
+        (e = spmv_attr<double, kRows>()) != cudaSuccess || (e = spmv_attr<float, 32>()) != cudaSuccess ||
+        (e = spmv_attr<float, 64>()) != cudaSuccess || (e = spmv_attr<float, kRows>()) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
                             const int *done) {
-    if (A->nb == 0) return cudaSuccess;
-    int grid = (int)((A->nb + kRows - 1) / kRows);
-    rsv::count_launches(1);
-    spmv_bsr3_tma<double, kRows><<<grid, 3 * kRows, SpmvSmem<double, kRows>::BYTES, A->stream>>>(
-        (int)A->nb, A->d_rp, A->d_ci, A->d_v, alpha, x, beta, y, done);
-    return cudaGetLastError();
+    return spmv_dispatch<double>(A, A->d_v, alpha, x, beta, y, done);
 }
 
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
                             const int *done) {
-    if (A->nb == 0) return cudaSuccess;
-    int grid = (int)((A->nb + kRows - 1) / kRows);
-    rsv::count_launches(1);
-    spmv_bsr3_tma<float, kRows><<<grid, 3 * kRows, SpmvSmem<float, kRows>::BYTES, A->stream>>>(
-        (int)A->nb, A->d_rp, A->d_ci, A->d_v32, alpha, x, beta, y, done);
-    return cudaGetLastError();
+    return spmv_dispatch<float>(A, A->d_v32, alpha, x, beta, y, done);
 }
 
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b) {
