@@ -33,6 +33,7 @@ namespace {
 constexpr int kChunk = 8192;      // elements per reduction work item
 constexpr int kGraphIters = 4;    // BiCGSTAB passes per graph replay
 constexpr int kSegThreads = 256;
+constexpr int kStallPasses = 30;  // FP32 inner solves: passes without progress before handing back
 
 struct SegItem {
     int sys;
@@ -42,9 +43,9 @@ struct SegItem {
 
 // Per-system state of the batched BiCGSTAB (arrays of nsys).
 struct BatchDev {
-    double *rho, *rho1, *alpha, *omega, *beta, *tol, *rhn, *scale, *bnorm;
+    double *rho, *rho1, *alpha, *omega, *beta, *tol, *rhn, *scale, *bnorm, *best;
     double *red;     // [8][nsys]: 0 <rh,r> 1 <rh,v> 2 ||v|| 3 ||s|| 4 <t,s> 5 <t,t> 6 ||r|| 7 spare
-    int *done, *status, *iters, *half, *outer;
+    int *done, *status, *iters, *half, *outer, *stall;
     int *ndone;      // systems done (single counter)
     unsigned *ticket;  // [4][nsys] reduction tickets
     double *partial;   // [2][nitems]
@@ -202,7 +203,11 @@ __global__ void b_omega(BatchDev d, int nsys, double btol) {
     d.omega[s] = om;
 }
 
-__global__ void b_finish(BatchDev d, int nsys, int maxit) {
+// stall_limit > 0 (FP32 inner solves of refinement): a system whose residual
+// has not dropped below 0.99 of its best for stall_limit passes ends its
+// inner solve; FP32 BiCGSTAB can stagnate above the inner tolerance on an
+// ill-conditioned system, and the FP64 outer step continues from there.
+__global__ void b_finish(BatchDev d, int nsys, int maxit, int stall_limit) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys || d.done[s]) return;
     d.rho[s] = d.rho1[s];
@@ -210,6 +215,14 @@ __global__ void b_finish(BatchDev d, int nsys, int maxit) {
     if (!isfinite(rn)) return finish_sys(d, s, RSV_ENAN);
     if (rn <= d.tol[s]) return finish_sys(d, s, 0);
     if (d.iters[s] >= maxit) return finish_sys(d, s, RSV_ENOCONV);
+    if (stall_limit > 0) {
+        if (rn < 0.99 * d.best[s]) {
+            d.best[s] = rn;
+            d.stall[s] = 0;
+        } else if (++d.stall[s] >= stall_limit) {
+            return finish_sys(d, s, 0);
+        }
+    }
 }
 
 template <typename T>
@@ -271,6 +284,8 @@ __global__ void b_init(BatchDev d, int nsys, double rtol_or_inner, int mixed) {
     // FP64 mode: tol = rtol ||b||; mixed: the inner right-hand side has unit norm
     d.tol[s] = mixed ? rtol_or_inner : rtol_or_inner * d.bnorm[s];
     d.done[s] = d.outer[s];
+    d.best[s] = d.red[6 * nsys + s];
+    d.stall[s] = 0;
 }
 
 __global__ void b_count_done(BatchDev d, int nsys) {
@@ -381,7 +396,7 @@ cudaError_t bicg_passes(rsv_solver *s, BatchState *B, T *x) {
         b_update_xr<T><<<g, 256, 0, s->st>>>(n, d, soc, ph, sh, sv, t, x, r);
         // ||r|| of the new residual and <rh, r> for the next pass, in one sweep
         if ((e = seg_dot<T>(s, B, r, r, rh, d.red + 6 * nsys, d.red + 0 * nsys, 1, 0, d.done)) != cudaSuccess) break;
-        b_finish<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, s->p.maxit);
+        b_finish<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, s->p.maxit, sizeof(T) == 4 ? kStallPasses : 0);
         b_count_done<<<1, 256, 0, s->st>>>(d, nsys);
         e = cudaGetLastError();
     }
@@ -466,8 +481,8 @@ rsv_status batch_init(rsv_solver *s, BatchState **out) {
     ibeg.push_back((int)items.size());
     B->nitems = (int)items.size();
     const int ns = A->nsys;
-    const size_t nd = 9 + 8;  // scalar double arrays + red[8]
-    const size_t bytes = sizeof(double) * (nd * ns + 2 * (size_t)B->nitems) + sizeof(int) * (5 * ns + 4) +
+    const size_t nd = 10 + 8;  // scalar double arrays + red[8]
+    const size_t bytes = sizeof(double) * (nd * ns + 2 * (size_t)B->nitems) + sizeof(int) * (6 * ns + 4) +
                          sizeof(unsigned) * 4 * ns + 256;
     const size_t es = s->mixed ? sizeof(float) : sizeof(double);
     cudaError_t e = cudaSuccess;
@@ -487,13 +502,14 @@ rsv_status batch_init(rsv_solver *s, BatchState **out) {
         auto take_d = [&](size_t cnt) { double *q = (double *)p; p += sizeof(double) * cnt; return q; };
         BatchDev &d = B->dv;
         d.rho = take_d(ns); d.rho1 = take_d(ns); d.alpha = take_d(ns); d.omega = take_d(ns); d.beta = take_d(ns);
-        d.tol = take_d(ns); d.rhn = take_d(ns); d.scale = take_d(ns); d.bnorm = take_d(ns);
+        d.tol = take_d(ns); d.rhn = take_d(ns); d.scale = take_d(ns); d.bnorm = take_d(ns); d.best = take_d(ns);
         d.red = take_d(8 * (size_t)ns);
         d.partial = take_d(2 * (size_t)B->nitems);
         int *ip = (int *)p;
         d.done = ip; d.status = ip + ns; d.iters = ip + 2 * ns; d.half = ip + 3 * ns; d.outer = ip + 4 * ns;
-        d.ndone = ip + 5 * ns;
-        d.ticket = (unsigned *)(ip + 5 * ns + 4);
+        d.stall = ip + 5 * ns;
+        d.ndone = ip + 6 * ns;
+        d.ticket = (unsigned *)(ip + 6 * ns + 4);
         e = cudaStreamSynchronize(s->st);
     }
     if (e != cudaSuccess) {
@@ -586,7 +602,7 @@ extern "C" rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *
         dx = s->d_x;
     }
     // per-system state from scratch; ||b|| per system
-    RSV_CUDA_TRY(cudaMemsetAsync(d.done, 0, sizeof(int) * (5 * nsys + 4), s->st));
+    RSV_CUDA_TRY(cudaMemsetAsync(d.done, 0, sizeof(int) * (6 * nsys + 4), s->st));
     RSV_CUDA_TRY(cudaMemsetAsync(d.scale, 0, sizeof(double) * nsys, s->st));
     RSV_CUDA_TRY(seg_dot<double>(s, B, db, db, (const double *)nullptr, d.bnorm, nullptr, 1, 0, nullptr));
     if (!s->mixed) {
@@ -606,10 +622,9 @@ extern "C" rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *
             b_outer_check<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, s->p.rtol, rn, s->p.max_outer, s->p.maxit);
             // all finished?
             count_launches(1);
-            b_count_done<<<1, 256, 0, s->st>>>(BatchDev{d.rho, d.rho1, d.alpha, d.omega, d.beta, d.tol, d.rhn,
-                                                        d.scale, d.bnorm, d.red, d.outer, d.status, d.iters, d.half,
-                                                        d.outer, d.ndone, d.ticket, d.partial},
-                                                nsys);
+            BatchDev od = d;
+            od.done = d.outer;  // count the systems the outer loop has finished
+            b_count_done<<<1, 256, 0, s->st>>>(od, nsys);
             RSV_CUDA_TRY(cudaMemcpyAsync(B->h_ndone, d.ndone, sizeof(int), cudaMemcpyDeviceToHost, s->st));
             RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
             if (*B->h_ndone >= nsys) break;

@@ -131,18 +131,36 @@ __global__ void bicg_omega(DevState *ds, double btol) {
     ds->omega = om;
 }
 
-__global__ void bicg_finish_iter(DevState *ds) {
+// stall_limit > 0 (FP32 inner solves of refinement): stop when the residual
+// has not dropped below 0.99 of its best for stall_limit passes (FP32
+// BiCGSTAB can stagnate above the inner tolerance; the FP64 outer step
+// continues from the iterate reached).  red[14] best residual, red[15] count.
+__global__ void bicg_finish_iter(DevState *ds, int stall_limit) {
     if (ds->done) return;
     ds->rho = ds->rho1;
     const double rn = ds->red[9];
     if (!isfinite(rn)) return raise_status(ds, RSV_ENAN);
-    if (rn <= ds->tol || ds->iters >= ds->maxit) ds->done = 1;
+    if (rn <= ds->tol || ds->iters >= ds->maxit) {
+        ds->done = 1;
+        return;
+    }
+    if (stall_limit > 0) {
+        if (rn < 0.99 * ds->red[14]) {
+            ds->red[14] = rn;
+            ds->red[15] = 0.0;
+        } else if ((ds->red[15] += 1.0) >= stall_limit) {
+            ds->red[11] = 3.0;  // stopped on stagnation
+            ds->done = 1;
+        }
+    }
 }
 
 __global__ void bicg_init(DevState *ds) {
     ds->rho = ds->alpha = ds->omega = 1.0;
     ds->red[8] = ds->red[9];
     ds->red[11] = 0.0;
+    ds->red[14] = ds->red[9];
+    ds->red[15] = 0.0;
     ds->done = 0;
 }
 
@@ -337,7 +355,7 @@ rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
             bicg_update_xr<T><<<g, 256, 0, s->st>>>(n, ds, ph, sh, sv, t, x, r);
             RSV_CUDA_TRY(launch_dot<T>(s->st, n, r, r, s->partial, &ds->red[9], &ds->counter[0], 1, done));
             rsv::count_launches(1);
-            bicg_finish_iter<<<1, 1, 0, s->st>>>(ds);
+            bicg_finish_iter<<<1, 1, 0, s->st>>>(ds, sizeof(T) == 4 ? 30 : 0);
         }
         RSV_CUDA_TRY(cudaGetLastError());
         RSV_TRY(fetch(s, &h));
@@ -348,7 +366,8 @@ rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
     RSV_CUDA_TRY(cudaMemcpyAsync(&rn, &ds->red[9], sizeof(double), cudaMemcpyDeviceToHost, s->st));
     RSV_CUDA_TRY(cudaMemcpyAsync(&half, &ds->red[11], sizeof(double), cudaMemcpyDeviceToHost, s->st));
     RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
-    if (half != 0.0 || rn <= tol) return RSV_OK;
+    if (half == 1.0 || half == 2.0 || rn <= tol) return RSV_OK;
+    if (half == 3.0) return RSV_ENOCONV;  // stagnated: the refinement loop carries on
     return RSV_ENOCONV;
 }
 
