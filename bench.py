@@ -57,10 +57,10 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA cores) from the pool's nominal table
 # DRAM bytes per launch (read + write) measured by one ncu capture of the current kernels on this
 # workload (profiles/ilu_apply_mid_100x100x50.md).  Set an entry to None whenever its kernel changes.
 NCU_TRAFFIC = {
-    "ilu_apply_f32": 208.8e6,   # gather_tiles + forward + backward sweep, FP32
-    "ilu_apply_f64": 464.1e6,
+    "ilu_apply_f32": 209.2e6,   # gather_tiles + forward + backward sweep, FP32
+    "ilu_apply_f64": 463.8e6,
     "spmv_f32": 148.2e6,
-    "spmv_f64": 284.4e6,
+    "spmv_f64": 284.0e6,
 }
 
 
@@ -183,6 +183,59 @@ def run_reference(args, rank, ws):
     return 0
 
 
+def run_batch(args):
+    """The batched-ensemble workload: 64 independent systems solved by one batched call."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+    dims = synth.batch_sizes()
+    t0 = time.perf_counter()
+    probs = [synth.make_problem(*d, seed=1000 + q) for q, d in enumerate(dims)]
+    vals = np.concatenate([p.vals for p in probs])
+    b = np.concatenate([p.b for p in probs])
+    gen_s = time.perf_counter() - t0
+    A = rsv.Matrix.batch(dims)
+    A.set_values(torch.from_numpy(vals).cuda())
+    s = rsv.Solver(A, solver="bicgstab", precision="mixed", rtol=1e-8, maxit=4000)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+
+    def step():
+        s.setup("bilu0")
+        x.zero_()
+        st, infos = s.solve_batched(bd, x)
+        if st != rsv.RSV_OK:
+            raise RuntimeError(f"batched solve: {rsv.status_string(st)}")
+        return infos
+
+    for _ in range(max(args.warmup, 1)):
+        infos = step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = rsv.rsv_kernel_launches()
+    e0.record()
+    for _ in range(args.steps):
+        infos = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    its = [i["iters"] for i in infos]
+    rel = [i["true_relres"] for i in infos]
+    line = {"workload": "batch64_uneven", "metric": "batched solve time to rtol 1e-8 (all 64 systems)",
+            "value": round(ms, 3), "unit": "ms", "higher_is_better": False, "steps": args.steps,
+            "systems": len(dims), "cells": int(A.nb), "unknowns": int(3 * A.nb),
+            "systems_per_s": round(len(dims) / (ms * 1e-3), 1),
+            "iters_min_median_max": [int(min(its)), int(np.median(its)), int(max(its))],
+            "max_true_relres": float(max(rel)), "gpu_launches_per_step": int((rsv.rsv_kernel_launches() - l0) / args.steps),
+            "generation_s": round(gen_s, 1),
+            "config": {"solver": "bicgstab", "pc": "bilu0 (batched tile sweeps)",
+                       "precision": "FP32 inner + FP64 refinement", "graph": "CUDA graph of 4 passes"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_mode(mode):
     """Small, self-checking runs of the hot path for ncu (no timing is reported)."""
     import torch
@@ -229,12 +282,16 @@ def main():
     ap.add_argument("--cpu-sample-iters", type=int, default=60)
     ap.add_argument("--ref-sample-iters", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile-solve", "profile-kernels"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "profile-solve", "profile-kernels", "batch"],
                     help="profile-solve: one short mixed GMRES(30)+BILU0 solve (60 inner iterations) on the "
                          "benchmark workload, for an ncu launch list; profile-kernels: set up the benchmark "
                          "workload and run each hot kernel (FP64/FP32 SpMV, FP32/FP64 ILU(0) apply) three times, "
-                         "for ncu captures. Neither prints a benchmark line.")
+                         "for ncu captures. Neither prints a benchmark line. batch: time the 64-system "
+                         "uneven ensemble (grids from 16^3 to 96x96x48, BiCGSTAB + block ILU(0), FP32 inner "
+                         "solves under FP64 refinement, rtol 1e-8 per system) and print its own JSON line.")
     args = ap.parse_args()
+    if args.mode == "batch":
+        return run_batch(args)
     if args.mode != "bench":
         return run_profile_mode(args.mode)
     if args.warmup < 3 and args.impl == "rsv":
