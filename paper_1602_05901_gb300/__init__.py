@@ -87,6 +87,9 @@ _SIGS = {
     "rsv_cpr_vcycle": (_I, [_P, _P, _P]),
     "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
     "rsv_solve_batched": (_I, [_P, _P, _P, _I, _P]),
+    "rsv_conv3d_fwd": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P, _I, _P]),
+    "rsv_conv3d_dgrad": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P]),
+    "rsv_conv3d_wgrad": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P]),
 }
 EXPORTS = tuple(_SIGS)
 

@@ -37,8 +37,8 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(os.path.dirname(HERE), "include", "rsv.h")]
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
+        glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     jobs = []

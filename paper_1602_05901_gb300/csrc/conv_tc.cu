@@ -1,0 +1,695 @@
+// 3x3x3 (and 1x1x1) convolutions of the learned pressure stage as implicit
+// GEMMs on the tcgen05 tensor cores: BF16 operands staged by TMA, FP32
+// accumulators in TMEM, fused epilogues.
+//
+// Volumes are channels-last BF16, [nz][ny][nx][ld] with the layer's channels
+// at the start of each voxel's row of ld values.  A 3x3x3 weight is
+// w[co][t][ci] with tap t = 9(dz+1) + 3(dy+1) + (dx+1); the layer computes
+// the cross-correlation y[v, co] = sum_t sum_ci w[co,t,ci] x[v + off_t, ci]
+// with zeros outside the grid.
+//
+// Forward (and the input gradient, which is the same correlation with the
+// taps mirrored and the channel roles swapped):
+//   M = 128 voxels of one tile (a box of bw x bh x bd voxels), N = output
+//   channels, K = taps x input channels.  Each K step is one tap and one
+//   block of BK channels: TMA copies the tap-shifted box of the input volume
+//   (zero fill outside the grid gives the padding exactly) and the matching
+//   weight slice; four (BK = 64) or two (BK = 32) MMAs of K = 16 consume it.
+// Weight gradient:
+//   gw[co][t][ci] = sum_v gy[v, co] x[v + off_t, ci] reduces over voxels, so
+//   K = voxels.  Both operands are first copied voxel-major (one row of
+//   voxels per channel) into a flat layout padded by one zero slice in z and
+//   one zero row in y on each side, so that the dz and dy shifts of a tap are
+//   plain offsets of the flat TMA coordinate (zeros arrive at the borders).
+//   The dx shift cannot be such an offset (the innermost TMA coordinate must
+//   stay 16-byte aligned), so the input is copied three times, pre-shifted by
+//   dx = -1, 0, +1.  M = 128 rows of (tap, ci) pairs, N = output channels, K
+//   steps of 64 voxels; CTAs split the voxels and write FP32 partial sums
+//   that a second kernel adds in a fixed order.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "conv.cuh"
+#include "tc.cuh"
+
+namespace rsv {
+
+using namespace tc;
+
+// ------------------------------------------------------------------ host: tensor maps
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// BF16 tensor map of rank r: dims/box innermost first, strides in bytes for dims 1..r-1.
+rsv_status make_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides,
+                    const uint32_t *box, int swz) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return RSV_ENOTSUP;
+    if (((uintptr_t)base) & 15) return RSV_EINVAL;
+    for (int i = 0; i < rank - 1; ++i)
+        if (strides[i] % 16) return RSV_EINVAL;
+    cuuint64_t d[5], s[4];
+    cuuint32_t b[5], e[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        e[i] = 1;
+        if (i < rank - 1) s[i] = strides[i];
+    }
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void *>(base), d, s, b, e,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? RSV_OK : RSV_EINVAL;
+}
+
+constexpr int kStages = 4;
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ void raise(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ------------------------------------------------------------------ forward / input-gradient kernel
+struct FwdArgs {
+    int nx, ny, nz;
+    int bw, bh, bd;       // voxel box of one M tile
+    int tx, ty;           // tiles along x and y
+    int taps, nkb, ci;    // taps (27 or 1), channel blocks per tap, input channels
+    int n_total;          // output channels
+    const float *bias;    // [n_total] or null
+    int relu;
+    const __nv_bfloat16 *mask;  // multiply by (mask > 0): [V][ldm] or null
+    int ldm;
+    __nv_bfloat16 *y;     // [V][ldy] or null
+    int ldy;
+    float *y32;           // [V][n_total] or null
+    int *err;
+    uint64_t timeout_ns;
+};
+
+template <int BK, int BN>
+struct FwdSmem {
+    static constexpr uint32_t A = 128 * BK * 2, B = BN * BK * 2, STAGE = A + B;
+    static constexpr uint32_t BARS = kStages * STAGE;
+    static constexpr uint32_t BYTES = BARS + 256 + 1024;  // + barriers/slots + alignment slack
+};
+
+template <int BK, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const FwdArgs a) {
+    using L = FwdSmem<BK, BN>;
+    constexpr int SWZ = BK * 2;  // 128 or 64
+    constexpr uint32_t TCOLS = tmem_cols_for(BN);
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t *full = (uint64_t *)(sm + L::BARS);
+    uint64_t *empty = full + kStages;
+    uint64_t *done = empty + kStages;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    int *flags = (int *)(tmem_slot + 1);  // [0] failed, [1] loads issued, [2] loads consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tx) * a.bw;
+    const int y0 = ((tile / a.tx) % a.ty) * a.bh;
+    const int z0 = (tile / (a.tx * a.ty)) * a.bd;
+    const int n0 = blockIdx.y * BN;
+    const int nk = a.taps * a.nkb;
+    const uint64_t deadline = now_ns() + a.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        flags[0] = flags[1] = flags[2] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, TCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        prefetch_map(&tmA);
+        prefetch_map(&tmB);
+        const uint32_t bytes = (uint32_t)(a.bw * a.bh * a.bd) * BK * 2 + (uint32_t)BN * BK * 2;
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (kk >= kStages && !mbar_wait(&empty[s], ((kk / kStages) + 1) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            const int tap = kk / a.nkb, cb = kk % a.nkb;
+            int dz = 0, dy = 0, dx = 0;
+            if (a.taps == 27) {
+                dz = tap / 9 - 1;
+                dy = (tap / 3) % 3 - 1;
+                dx = tap % 3 - 1;
+            }
+            uint8_t *st = sm + s * L::STAGE;
+            mbar_expect_tx(&full[s], bytes);
+            tma_load_4d(st, &tmA, cb * BK, x0 + dx, y0 + dy, z0 + dz, &full[s]);
+            tma_load_2d(st + L::A, &tmB, tap * a.ci + cb * BK, n0, &full[s]);
+        }
+        flags[1] = kk;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(128, BN);
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (!mbar_wait(&full[s], (kk / kStages) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t sa = smem_u32(sm + s * L::STAGE), sb = sa + L::A;
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)
+                mma_bf16(tmem, kmajor_desc(sa + j * 32, SWZ), kmajor_desc(sb + j * 32, SWZ), idesc,
+                         (kk > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        flags[2] = kk;
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // Epilogue: warp w owns TMEM lanes 32w..32w+31, i.e. tile rows (voxels) 32w + lane.
+    const bool ok = mbar_wait(done, 0, deadline + a.timeout_ns);
+    fence_after_sync();
+    const int row = warp * 32 + lane;
+    const int rx = row % a.bw, ry = (row / a.bw) % a.bh, rz = row / (a.bw * a.bh);
+    const int x = x0 + rx, y = y0 + ry, z = z0 + rz;
+    const bool valid = ok && rz < a.bd && x < a.nx && y < a.ny && z < a.nz && !flags[0];
+    const int64_t v = ((int64_t)z * a.ny + y) * a.nx + x;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, acc);
+        if (!valid) continue;
+        const int n = n0 + c0;
+        if (a.bias) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] += a.bias[n + i];
+        }
+        if (a.relu) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = fmaxf(acc[i], 0.0f);
+        }
+        if (a.mask) {
+            const uint4 *mp = (const uint4 *)(a.mask + v * a.ldm + n);
+            uint4 mv[2] = {mp[0], mp[1]};
+            const __nv_bfloat16 *mb = (const __nv_bfloat16 *)mv;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (!(__bfloat162float(mb[i]) > 0.0f)) acc[i] = 0.0f;
+        }
+        if (a.y32) {
+            float4 *o = (float4 *)(a.y32 + v * a.n_total + n);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+        }
+        if (a.y) {
+            uint4 ov[2];
+            __nv_bfloat162 *ob = (__nv_bfloat162 *)ov;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ob[i] = __floats2bfloat162_rn(acc[2 * i], acc[2 * i + 1]);
+            uint4 *o = (uint4 *)(a.y + v * a.ldy + n);
+            o[0] = ov[0];
+            o[1] = ov[1];
+        }
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0 && (flags[0] || !ok)) {
+        raise(a.err, RSV_ETIMEOUT);
+        // let copies still in flight land before the shared memory is released
+        for (int kk = flags[2]; kk < flags[1]; ++kk)
+            mbar_wait(&full[kk % kStages], (kk / kStages) & 1, now_ns() + a.timeout_ns);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(tmem, TCOLS);
+}
+
+// ------------------------------------------------------------------ weight-gradient kernel
+struct WgArgs {
+    int nchunks, cps;          // 64-voxel K chunks in the padded volume; chunks per split
+    int taps, ci, cblk, tpt, ncb;  // tap-group rows: tpt taps x cblk channels; ncb = ci / cblk
+    int plane, row;            // flat shift of dz and dy in the padded layout
+    int co;                    // output channels (N total)
+    float *partial;            // [splits][taps][ci][co]
+    int *err;
+    uint64_t timeout_ns;
+};
+
+template <int BN>
+struct WgSmem {
+    static constexpr uint32_t A = 128 * 128, B = BN * 128, STAGE = A + B;
+    static constexpr uint32_t BARS = kStages * STAGE;
+    static constexpr uint32_t BYTES = BARS + 256 + 1024;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const WgArgs a) {
+    using L = WgSmem<BN>;
+    constexpr uint32_t TCOLS = tmem_cols_for(BN);
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t *full = (uint64_t *)(sm + L::BARS);
+    uint64_t *empty = full + kStages;
+    uint64_t *done = empty + kStages;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    int *flags = (int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tg = blockIdx.x / a.ncb, cb = blockIdx.x % a.ncb;
+    const int n0 = blockIdx.y * BN;
+    const int q0 = blockIdx.z * a.cps;
+    const int q1 = min(a.nchunks, q0 + a.cps);
+    const int nk = max(0, q1 - q0);
+    const int ntap = min(a.tpt, a.taps - tg * a.tpt);
+    const uint64_t deadline = now_ns() + a.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        flags[0] = flags[1] = flags[2] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, TCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_map(&tmA);
+        prefetch_map(&tmB);
+        const uint32_t bytes = (uint32_t)ntap * a.cblk * 128 + (uint32_t)BN * 128;
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (kk >= kStages && !mbar_wait(&empty[s], ((kk / kStages) + 1) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            const int f0 = (q0 + kk) * 64;
+            uint8_t *st = sm + s * L::STAGE;
+            mbar_expect_tx(&full[s], bytes);
+            for (int g = 0; g < ntap; ++g) {
+                const int tap = tg * a.tpt + g;
+                int dz = 0, dy = 0, dxi = 0;
+                if (a.taps == 27) {
+                    dz = tap / 9 - 1;
+                    dy = (tap / 3) % 3 - 1;
+                    dxi = tap % 3;
+                }
+                tma_load_3d(st + g * a.cblk * 128, &tmA, f0 + dz * a.plane + dy * a.row, cb * a.cblk, dxi, &full[s]);
+            }
+            tma_load_2d(st + L::A, &tmB, f0, n0, &full[s]);
+        }
+        flags[1] = kk;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_bf16(128, BN);
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (!mbar_wait(&full[s], (kk / kStages) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t sa = smem_u32(sm + s * L::STAGE), sb = sa + L::A;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_bf16(tmem, kmajor_desc(sa + j * 32, 128), kmajor_desc(sb + j * 32, 128), idesc,
+                         (kk > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        flags[2] = kk;
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, deadline + a.timeout_ns);
+    fence_after_sync();
+    const int row = warp * 32 + lane;
+    const int g = row / a.cblk, c = row % a.cblk;
+    const int tap = tg * a.tpt + g;
+    const bool valid = ok && g < ntap && !flags[0];
+    float *out = a.partial + (((int64_t)blockIdx.z * a.taps + tap) * a.ci + cb * a.cblk + c) * a.co + n0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, acc);
+        if (!valid) continue;
+        if (nk == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
+        }
+        float4 *o = (float4 *)(out + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0 && (flags[0] || !ok)) {
+        raise(a.err, RSV_ETIMEOUT);
+        for (int kk = flags[2]; kk < flags[1]; ++kk)
+            mbar_wait(&full[kk % kStages], (kk / kStages) & 1, now_ns() + a.timeout_ns);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(tmem, TCOLS);
+}
+
+// ------------------------------------------------------------------ helper kernels
+// Voxel-major copy of a channels-last volume into the zero-padded flat layout
+// of the weight gradient: out[d][c][f], f = ((z+1)(ny+2) + (y+1)) nx + x over
+// z in [-1, nz], y in [-1, ny]; out[d][c][f] = x[z, y, x + d - 1, c] when
+// nshift = 3 (d = 0, 1, 2), x[z, y, x, c] when nshift = 1; zero outside the grid.
+__global__ void __launch_bounds__(256)
+    to_voxel_major(const __nv_bfloat16 *__restrict__ src, int ld, int nch, int nx, int ny, int nz, int nshift,
+                   int64_t vpad, __nv_bfloat16 *__restrict__ dst) {
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t f0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int d = blockIdx.z;
+    const int plane = (ny + 2) * nx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t f = f0 + ty + 8 * k;
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (f < vpad && c0 + tx < nch) {
+            const int zp = (int)(f / plane), rem = (int)(f % plane);
+            const int z = zp - 1, y = rem / nx - 1;
+            const int x = rem % nx + (nshift == 3 ? d - 1 : 0);
+            if (z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx)
+                v = src[(((int64_t)z * ny + y) * nx + x) * ld + c0 + tx];
+        }
+        tile[ty + 8 * k][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = c0 + ty + 8 * k;
+        const int64_t f = f0 + tx;
+        if (c < nch && f < vpad) dst[((int64_t)d * nch + c) * vpad + f] = tile[tx][ty + 8 * k];
+    }
+}
+
+// gw[co][t][ci] = sum over splits of partial[s][t][ci][co], in split order.
+__global__ void wgrad_reduce(const float *__restrict__ partial, int splits, int taps, int ci, int co,
+                             float *__restrict__ gw) {
+    const int64_t total = (int64_t)taps * ci * co;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(i / ((int64_t)taps * ci));
+        const int t = (int)((i / ci) % taps);
+        const int c = (int)(i % ci);
+        float s = 0.0f;
+        for (int q = 0; q < splits; ++q) s += partial[(((int64_t)q * taps + t) * ci + c) * co + o];
+        gw[i] = s;
+    }
+}
+
+// gb[c] = sum over the padded voxel-major row c (pads are zero); one block per channel, fixed tree order.
+__global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16 *__restrict__ gyt, int64_t vpad,
+                                                 float *__restrict__ gb) {
+    __shared__ float red[256];
+    const __nv_bfloat16 *r = gyt + (int64_t)blockIdx.x * vpad;
+    float s = 0.0f;
+    for (int64_t f = threadIdx.x; f < vpad; f += 256) s += __bfloat162float(r[f]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[blockIdx.x] = red[0];
+}
+
+// Weights of the input gradient: wt[ci][t][co] = w[co][26 - t][ci].
+__global__ void flip_weights(const __nv_bfloat16 *__restrict__ w, int ci, int co, __nv_bfloat16 *__restrict__ wt) {
+    const int64_t total = (int64_t)ci * 27 * co;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / (27 * co));
+        const int t = (int)((i / co) % 27);
+        const int o = (int)(i % co);
+        wt[i] = w[((int64_t)o * 27 + (26 - t)) * ci + c];
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host launchers
+namespace {
+
+int pick_bn(int n) {
+    for (int b : {256, 192, 128, 96, 64, 32})
+        if (n % b == 0) return b;
+    return 0;
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, uint32_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int BK, int BN>
+cudaError_t launch_fwd_t(cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb, const FwdArgs &a) {
+    using L = FwdSmem<BK, BN>;
+    static cudaError_t attr = set_smem(conv_fwd_tc<BK, BN>, L::BYTES);
+    if (attr != cudaSuccess) return attr;
+    conv_fwd_tc<BK, BN><<<grid, kThreads, L::BYTES, st>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t launch_fwd_bk(int bn, cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb,
+                          const FwdArgs &a) {
+    switch (bn) {
+        case 32: return launch_fwd_t<BK, 32>(st, grid, ma, mb, a);
+        case 64: return launch_fwd_t<BK, 64>(st, grid, ma, mb, a);
+        case 96: return launch_fwd_t<BK, 96>(st, grid, ma, mb, a);
+        case 128: return launch_fwd_t<BK, 128>(st, grid, ma, mb, a);
+        case 192: return launch_fwd_t<BK, 192>(st, grid, ma, mb, a);
+        default: return launch_fwd_t<BK, 256>(st, grid, ma, mb, a);
+    }
+}
+
+template <int BN>
+cudaError_t launch_wg_t(cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb, const WgArgs &a) {
+    using L = WgSmem<BN>;
+    static cudaError_t attr = set_smem(conv_wgrad_tc<BN>, L::BYTES);
+    if (attr != cudaSuccess) return attr;
+    conv_wgrad_tc<BN><<<grid, kThreads, L::BYTES, st>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wg(int bn, cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb,
+                      const WgArgs &a) {
+    switch (bn) {
+        case 32: return launch_wg_t<32>(st, grid, ma, mb, a);
+        case 64: return launch_wg_t<64>(st, grid, ma, mb, a);
+        case 96: return launch_wg_t<96>(st, grid, ma, mb, a);
+        case 128: return launch_wg_t<128>(st, grid, ma, mb, a);
+        case 192: return launch_wg_t<192>(st, grid, ma, mb, a);
+        default: return launch_wg_t<256>(st, grid, ma, mb, a);
+    }
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+struct WgPlan {
+    int64_t vpad;
+    int nchunks, cblk, tpt, ncb, mtiles, bn, ntiles, splits, cps, nshift;
+    size_t xt_bytes, gyt_bytes, part_bytes;
+};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+WgPlan wg_plan(ConvVol v, int taps, int ci, int co) {
+    WgPlan p{};
+    p.vpad = (int64_t)(v.nz + 2) * (v.ny + 2) * v.nx;
+    p.nchunks = (int)((p.vpad + 63) / 64);
+    p.cblk = ci % 128 == 0 ? 128 : ci % 64 == 0 ? 64 : 32;
+    p.tpt = 128 / p.cblk;
+    p.ncb = ci / p.cblk;
+    p.mtiles = ((taps + p.tpt - 1) / p.tpt) * p.ncb;
+    p.bn = pick_bn(co);
+    p.ntiles = p.bn ? co / p.bn : 0;
+    const int ctas = std::max(1, p.mtiles * p.ntiles);
+    int splits = std::max(1, std::min(p.nchunks, (2 * 152 + ctas - 1) / ctas));
+    p.cps = (p.nchunks + splits - 1) / splits;
+    p.splits = (p.nchunks + p.cps - 1) / p.cps;
+    p.nshift = taps == 27 ? 3 : 1;
+    p.xt_bytes = round256((size_t)p.nshift * ci * p.vpad * 2);
+    p.gyt_bytes = round256((size_t)co * p.vpad * 2);
+    p.part_bytes = round256((size_t)p.splits * taps * ci * co * 4);
+    return p;
+}
+
+}  // namespace
+
+rsv_status conv_fwd(cudaStream_t st, ConvVol v, int taps, int ci, int co, const __nv_bfloat16 *x, int ldx,
+                    const __nv_bfloat16 *w, const float *bias, int relu, const __nv_bfloat16 *mask, int ldm,
+                    __nv_bfloat16 *y, int ldy, float *y32, int *err, uint64_t timeout_ns) {
+    if (v.nx <= 0 || v.ny <= 0 || v.nz <= 0 || (taps != 1 && taps != 27) || ci <= 0 || ci % 32 || co <= 0 ||
+        co % 32 || !x || !w || (!y && !y32) || ldx < ci || ldx % 8 || (y && (ldy < co || ldy % 8)) ||
+        (mask && (ldm < co || ldm % 8)))
+        return RSV_EINVAL;
+    if (!aligned16(x) || !aligned16(w) || (y && !aligned16(y)) || (y32 && !aligned16(y32)) ||
+        (mask && !aligned16(mask)))
+        return RSV_EINVAL;
+    const int BK = ci % 64 == 0 ? 64 : 32;
+    const int BN = pick_bn(co);
+    FwdArgs a{};
+    a.nx = v.nx;
+    a.ny = v.ny;
+    a.nz = v.nz;
+    a.bw = std::min(v.nx, 128);
+    a.bh = std::min(v.ny, 128 / a.bw);
+    a.bd = std::min(v.nz, 128 / (a.bw * a.bh));
+    a.tx = (v.nx + a.bw - 1) / a.bw;
+    a.ty = (v.ny + a.bh - 1) / a.bh;
+    const int tz = (v.nz + a.bd - 1) / a.bd;
+    a.taps = taps;
+    a.nkb = ci / BK;
+    a.ci = ci;
+    a.n_total = co;
+    a.bias = bias;
+    a.relu = relu;
+    a.mask = mask;
+    a.ldm = ldm;
+    a.y = y;
+    a.ldy = ldy;
+    a.y32 = y32;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    CUtensorMap ma, mb;
+    {
+        const uint64_t dims[4] = {(uint64_t)ci, (uint64_t)v.nx, (uint64_t)v.ny, (uint64_t)v.nz};
+        const uint64_t strides[3] = {(uint64_t)ldx * 2, (uint64_t)v.nx * ldx * 2, (uint64_t)v.nx * v.ny * ldx * 2};
+        const uint32_t box[4] = {(uint32_t)BK, (uint32_t)a.bw, (uint32_t)a.bh, (uint32_t)a.bd};
+        RSV_TRY(make_map(&ma, x, 4, dims, strides, box, BK * 2));
+    }
+    {
+        const uint64_t dims[2] = {(uint64_t)taps * ci, (uint64_t)co};
+        const uint64_t strides[1] = {(uint64_t)taps * ci * 2};
+        const uint32_t box[2] = {(uint32_t)BK, (uint32_t)BN};
+        RSV_TRY(make_map(&mb, w, 2, dims, strides, box, BK * 2));
+    }
+    const dim3 grid(a.tx * a.ty * tz, co / BN);
+    RSV_CUDA_TRY(BK == 64 ? launch_fwd_bk<64>(BN, st, grid, ma, mb, a) : launch_fwd_bk<32>(BN, st, grid, ma, mb, a));
+    count_launches(1);
+    return RSV_OK;
+}
+
+rsv_status conv_flip(cudaStream_t st, int ci, int co, const __nv_bfloat16 *w, __nv_bfloat16 *wt) {
+    if (ci <= 0 || co <= 0 || !w || !wt) return RSV_EINVAL;
+    const int64_t total = (int64_t)ci * 27 * co;
+    flip_weights<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(w, ci, co, wt);
+    RSV_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return RSV_OK;
+}
+
+size_t conv_wgrad_scratch(ConvVol v, int taps, int ci, int co) {
+    const WgPlan p = wg_plan(v, taps, ci, co);
+    return p.xt_bytes + p.gyt_bytes + p.part_bytes;
+}
+
+rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, const __nv_bfloat16 *x, int ldx,
+                      const __nv_bfloat16 *gy, int ldgy, float *gw, float *gb, void *scratch, int *err,
+                      uint64_t timeout_ns) {
+    if (v.nx <= 0 || v.ny <= 0 || v.nz <= 0 || v.nx % 8 || (taps != 1 && taps != 27) || ci <= 0 || ci % 32 ||
+        co <= 0 || co % 32 || !x || !gy || !gw || !scratch || ldx < ci || ldgy < co)
+        return RSV_EINVAL;
+    const WgPlan p = wg_plan(v, taps, ci, co);
+    __nv_bfloat16 *xt = (__nv_bfloat16 *)scratch;
+    __nv_bfloat16 *gyt = (__nv_bfloat16 *)((char *)scratch + p.xt_bytes);
+    float *part = (float *)((char *)scratch + p.xt_bytes + p.gyt_bytes);
+    if (!aligned16(scratch)) return RSV_EINVAL;
+    const int fblocks = (int)((p.vpad + 31) / 32);
+    to_voxel_major<<<dim3(fblocks, ci / 32, p.nshift), 256, 0, st>>>(x, ldx, ci, v.nx, v.ny, v.nz, p.nshift, p.vpad,
+                                                                       xt);
+    RSV_CUDA_TRY(cudaGetLastError());
+    to_voxel_major<<<dim3(fblocks, co / 32, 1), 256, 0, st>>>(gy, ldgy, co, v.nx, v.ny, v.nz, 1, p.vpad, gyt);
+    RSV_CUDA_TRY(cudaGetLastError());
+    CUtensorMap ma, mb;
+    {
+        const uint64_t dims[3] = {(uint64_t)p.vpad, (uint64_t)ci, (uint64_t)p.nshift};
+        const uint64_t strides[2] = {(uint64_t)p.vpad * 2, (uint64_t)ci * p.vpad * 2};
+        const uint32_t box[3] = {64u, (uint32_t)p.cblk, 1u};
+        RSV_TRY(make_map(&ma, xt, 3, dims, strides, box, 128));
+    }
+    {
+        const uint64_t dims[2] = {(uint64_t)p.vpad, (uint64_t)co};
+        const uint64_t strides[1] = {(uint64_t)p.vpad * 2};
+        const uint32_t box[2] = {64u, (uint32_t)p.bn};
+        RSV_TRY(make_map(&mb, gyt, 2, dims, strides, box, 128));
+    }
+    WgArgs a{};
+    a.nchunks = p.nchunks;
+    a.cps = p.cps;
+    a.taps = taps;
+    a.ci = ci;
+    a.cblk = p.cblk;
+    a.tpt = p.tpt;
+    a.ncb = p.ncb;
+    a.plane = (v.ny + 2) * v.nx;
+    a.row = v.nx;
+    a.co = co;
+    a.partial = part;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    RSV_CUDA_TRY(launch_wg(p.bn, st, dim3(p.mtiles, p.ntiles, p.splits), ma, mb, a));
+    const int64_t total = (int64_t)taps * ci * co;
+    wgrad_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(part, p.splits, taps, ci, co, gw);
+    RSV_CUDA_TRY(cudaGetLastError());
+    int n = 4;
+    if (gb) {
+        bias_grad<<<co, 256, 0, st>>>(gyt, p.vpad, gb);
+        RSV_CUDA_TRY(cudaGetLastError());
+        n = 5;
+    }
+    count_launches(n);
+    return RSV_OK;
+}
+
+}  // namespace rsv

@@ -7,11 +7,11 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "rsv.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("rsv.h", "rsv_unet.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"RSV_API\s+[\w\s\*]*?\b(rsv_\w+)\s*\(", text)))
 
 
