@@ -59,6 +59,51 @@ RSV_API rsv_status rsv_conv3d_dgrad(void *stream, int nx, int ny, int nz, int ci
 RSV_API rsv_status rsv_conv3d_wgrad(void *stream, int nx, int ny, int nz, int taps, int ci, int co,
                                     const uint16_t *x, int ldx, const uint16_t *gy, int ldgy, float *gw, float *gb);
 
+/* ------------------------------------------------------------------ the network
+ * Architecture (levels L, channels ch[l] = base * 2^l, l = 0..L-1):
+ *   encoder level l: (l > 0: 2x2x2 average pooling of level l-1's output)
+ *                    -> 3x3x3 conv + bias + ReLU -> 3x3x3 conv + bias + ReLU
+ *   decoder level l < L-1: concatenate [nearest-upsampled output of level l+1,
+ *                    encoder output of level l] -> two (3x3x3 conv + bias + ReLU)
+ *   head: 1x1x1 conv to one channel plus bias, no activation.
+ * Input channels: r_p / s with s = sqrt(mean(r_p^2)), and (ln k - mean) / std
+ * over the grid (a channel whose scale is zero is fed as zeros).  The stage's
+ * output is s * head.  Activations and conv weights are BF16, sums FP32.
+ *
+ * Parameters are one FP32 array: per layer its weight ([co][27][ci], the
+ * head's [1][ch[0]]) then its bias [co], layers in the order enc1a, enc1b,
+ * enc2a, ..., encLb, dec(L-1)a, dec(L-1)b, ..., dec1a, dec1b, head (enc1a has
+ * ci = 2; dec(l)a has ci = ch[l] + ch[l-1] in 1-based level numbering).
+ *
+ * Training: rsv_unet_train_step runs the forward pass, the loss
+ * mean((head - target / s)^2) over the voxels, the backward pass and one
+ * Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr; lr <= 0
+ * computes the gradient only).  The target is the pressure correction the
+ * network should imitate (for example one multigrid V-cycle applied to r_p).
+ */
+typedef struct rsv_unet rsv_unet;
+
+/* Network for an nx*ny*nz grid.  Requirements (RSV_EINVAL otherwise): 1 <= levels
+ * <= 5; base in {32, 64, 96, 128} with base * 2^(levels-1) <= 512; nx, ny, nz
+ * divisible by 2^(levels-1) and nx / 2^(levels-1) a multiple of 8.  Parameters
+ * start at zero (set them with rsv_unet_set_params).  Device memory: about
+ * 2.2 KB per fine-grid voxel at base 32 (activations kept for training). */
+RSV_API rsv_status rsv_unet_create(void *stream, int nx, int ny, int nz, int base, int levels, rsv_unet **out);
+RSV_API void rsv_unet_destroy(rsv_unet *u);
+RSV_API rsv_status rsv_unet_num_params(const rsv_unet *u, int64_t *n);
+/* Copy the FP32 parameter array in (host or device); resets the Adam moments and step count. */
+RSV_API rsv_status rsv_unet_set_params(rsv_unet *u, const float *params, int on_device);
+RSV_API rsv_status rsv_unet_get_params(const rsv_unet *u, float *params, int on_device);
+/* Gradient of the loss of the last rsv_unet_train_step, same layout as the parameters. */
+RSV_API rsv_status rsv_unet_get_grads(const rsv_unet *u, float *grads, int on_device);
+/* corr = s * U(r_p / s, ln k): rp, lnk and corr are device float64 arrays of
+ * nx*ny*nz values in cell order.  Synchronises the stream. */
+RSV_API rsv_status rsv_unet_apply(rsv_unet *u, const double *rp, const double *lnk, double *corr);
+/* One training step on one sample (device float64 arrays of nx*ny*nz values);
+ * *loss (host, may be NULL) receives the loss before the update. */
+RSV_API rsv_status rsv_unet_train_step(rsv_unet *u, const double *rp, const double *lnk, const double *target,
+                                       float lr, double *loss);
+
 #ifdef __cplusplus
 }
 #endif

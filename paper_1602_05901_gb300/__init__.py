@@ -90,6 +90,14 @@ _SIGS = {
     "rsv_conv3d_fwd": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P, _I, _P]),
     "rsv_conv3d_dgrad": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P]),
     "rsv_conv3d_wgrad": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P]),
+    "rsv_unet_create": (_I, [_P, _I, _I, _I, _I, _I, _PP]),
+    "rsv_unet_destroy": (None, [_P]),
+    "rsv_unet_num_params": (_I, [_P, ctypes.POINTER(_I64)]),
+    "rsv_unet_set_params": (_I, [_P, _P, _I]),
+    "rsv_unet_get_params": (_I, [_P, _P, _I]),
+    "rsv_unet_get_grads": (_I, [_P, _P, _I]),
+    "rsv_unet_apply": (_I, [_P, _P, _P, _P]),
+    "rsv_unet_train_step": (_I, [_P, _P, _P, _P, _F, ctypes.POINTER(_D)]),
 }
 EXPORTS = tuple(_SIGS)
 

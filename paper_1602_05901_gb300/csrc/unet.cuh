@@ -1,0 +1,14 @@
+// Internal interface of the learned pressure stage (unet.cu) for the solver.
+#pragma once
+
+#include "../../include/rsv_unet.h"
+#include "common.cuh"
+
+namespace rsv {
+
+// corr = s * U(rp / s, standardised lnk) on the network's grid, launched on st (no synchronisation).
+rsv_status unet_apply_device(rsv_unet *u, cudaStream_t st, const double *rp, const double *lnk, double *corr);
+// The network's device error word (synchronises st); 0 when no bounded wait ran out.
+int unet_error(rsv_unet *u, cudaStream_t st);
+
+}  // namespace rsv

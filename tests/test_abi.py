@@ -58,3 +58,16 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert rsv.status_string(rsv.RSV_ENOCONV) == "not converged within maxit"
     p = rsv.solver_params()
     assert (p.restart, p.rtol, p.maxit, p.btol) == (30, 1e-8, 2000, 1e-30)
+
+
+def test_unet_and_conv_argument_checks_without_gpu(lib):
+    import paper_1602_05901_gb300 as rsv
+    h = ctypes.c_void_p()
+    # nx / 2^(levels-1) must be a multiple of 8; base a multiple of 32; 1 <= levels <= 5
+    assert rsv.rsv_unet_create(None, 60, 16, 8, 32, 3, ctypes.byref(h)) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_create(None, 64, 16, 8, 16, 3, ctypes.byref(h)) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_create(None, 64, 16, 8, 32, 6, ctypes.byref(h)) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_create(None, 64, 15, 8, 32, 3, ctypes.byref(h)) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_create(None, 64, 16, 8, 32, 3, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_apply(None, None, None, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_train_step(None, None, None, None, 1e-3, None) == rsv.RSV_EINVAL

@@ -1,0 +1,171 @@
+"""The U-Net of the learned pressure stage on the GPU against the oracle (forward, gradients, Adam, training)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsv():
+    import paper_1602_05901_gb300 as rsv
+    return rsv
+
+
+def _params(base, levels, seed):
+    """He-normal weights and small biases, rounded to FP32 (the GPU's master precision)."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, co, ci, taps in U.layer_shapes(base, levels):
+        fan = taps * ci
+        w = rng.standard_normal((co, taps, ci) if taps == 27 else (co, ci)) * np.sqrt(2.0 / fan)
+        b = rng.standard_normal(co) * 0.05
+        p[name] = (w.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64))
+    return p
+
+
+def _flat(p, base, levels):
+    return np.concatenate([np.concatenate([p[n][0].ravel(), p[n][1].ravel()])
+                           for n, *_ in U.layer_shapes(base, levels)]).astype(np.float32)
+
+
+def _unflat(v, base, levels):
+    out, off = {}, 0
+    for n, co, ci, taps in U.layer_shapes(base, levels):
+        nw = co * ci * (27 if taps == 27 else 1)
+        out[n] = (v[off:off + nw], v[off + nw:off + nw + co])
+        off += nw + co
+    assert off == v.size
+    return out
+
+
+def _net(rsv, nx, ny, nz, base, levels, params):
+    h = ctypes.c_void_p()
+    rsv.check(rsv.rsv_unet_create(None, nx, ny, nz, base, levels, ctypes.byref(h)), "rsv_unet_create")
+    n = ctypes.c_int64()
+    rsv.check(rsv.rsv_unet_num_params(h, ctypes.byref(n)))
+    flat = _flat(params, base, levels)
+    assert n.value == flat.size
+    rsv.check(rsv.rsv_unet_set_params(h, flat.ctypes.data_as(ctypes.c_void_p), 0))
+    return h
+
+
+def _inputs(nx, ny, nz, seed):
+    rng = np.random.default_rng(seed)
+    rp = rng.standard_normal((nz, ny, nx)) * 3.0
+    lnk = rng.standard_normal((nz, ny, nx)) * 1.5 + np.log(100.0)
+    tgt = rng.standard_normal((nz, ny, nx)) * 2.0
+    return rp, lnk, tgt
+
+
+def _dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+CASES = [(64, 16, 8, 32, 3), (64, 16, 16, 32, 4), (32, 8, 8, 32, 2)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}_L{c[4]}" for c in CASES])
+def test_unet_forward_matches_oracle(rsv, case):
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, base, levels = case
+    params = _params(base, levels, 1)
+    h = _net(rsv, nx, ny, nz, base, levels, params)
+    rp, lnk, _ = _inputs(nx, ny, nz, 2)
+    corr = torch.zeros(nx * ny * nz, dtype=torch.float64, device="cuda")
+    rpd, lnkd = _dev(torch, rp), _dev(torch, lnk)   # keep the tensors alive across the call
+    rsv.check(rsv.rsv_unet_apply(h, _p(rpd), _p(lnkd), _p(corr)), "rsv_unet_apply")
+    got = corr.cpu().numpy().reshape(nz, ny, nx)
+    ref = U.apply_stage(params, rp, lnk, base, levels, bf16=True)
+    ref64 = U.apply_stage(params, rp, lnk, base, levels, bf16=False)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    # Same BF16 rounding points on both sides; only FP32 summation order differs.
+    assert rel < 5e-3, rel
+    assert np.linalg.norm(ref - ref64) / np.linalg.norm(ref64) < 0.1
+    rsv.rsv_unet_destroy(h)
+
+
+def test_unet_gradients_match_oracle(rsv):
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, base, levels = 64, 16, 8, 32, 3
+    params = _params(base, levels, 3)
+    h = _net(rsv, nx, ny, nz, base, levels, params)
+    rp, lnk, tgt = _inputs(nx, ny, nz, 4)
+    loss = ctypes.c_double()
+    rpd, lnkd, tgtd = _dev(torch, rp), _dev(torch, lnk), _dev(torch, tgt)
+    rsv.check(rsv.rsv_unet_train_step(h, _p(rpd), _p(lnkd), _p(tgtd), 0.0, ctypes.byref(loss)), "train_step")
+    g = np.zeros(_flat(params, base, levels).size, dtype=np.float32)
+    rsv.check(rsv.rsv_unet_get_grads(h, g.ctypes.data_as(ctypes.c_void_p), 0))
+    x, s = U.standardise(rp, lnk)
+    x = x.astype(np.float32).astype(np.float64)
+
+    def oracle_grads(eps, seed):
+        # eps > 0: weights perturbed by a relative 1e-7, far below BF16 resolution
+        r = np.random.default_rng(seed)
+        pp = {k: (v[0] * (1 + eps * r.standard_normal(v[0].shape)), v[1]) for k, v in params.items()}
+        out, act = U.forward(pp, x, base, levels, bf16=True)
+        l, gout = U.mse_loss(out, tgt / s)
+        return l, U.backward(pp, act, gout, base, levels, bf16=True)
+
+    lref, gref = oracle_grads(0.0, 0)
+    assert abs(loss.value - lref) <= 1e-4 * lref
+    # BF16 rounding makes the backward pass chaotic at the percent level: a
+    # perturbation far below BF16 resolution (the GPU's different FP32
+    # summation order is one) flips roundings that cascade.  The GPU must stay
+    # within 3x the oracle's own spread under such perturbations.
+    spreads = [oracle_grads(1e-7, q)[1] for q in (1, 2)]
+    gg = _unflat(g.astype(np.float64), base, levels)
+    for name in gref:
+        for k in (0, 1):
+            b = gref[name][k].ravel()
+            nb = max(np.linalg.norm(b), 1e-30)
+            spread = max(np.linalg.norm(sp[name][k].ravel() - b) / nb for sp in spreads)
+            rel = np.linalg.norm(gg[name][k].ravel() - b) / nb
+            assert rel < 3 * spread + 2e-3, (name, k, rel, spread)
+    rsv.rsv_unet_destroy(h)
+
+
+def test_unet_adam_first_step_closed_form(rsv):
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, base, levels = 32, 8, 8, 32, 2
+    params = _params(base, levels, 5)
+    p0 = _flat(params, base, levels)
+    h = _net(rsv, nx, ny, nz, base, levels, params)
+    rp, lnk, tgt = _inputs(nx, ny, nz, 6)
+    lr = 1e-3
+    rpd, lnkd, tgtd = _dev(torch, rp), _dev(torch, lnk), _dev(torch, tgt)
+    rsv.check(rsv.rsv_unet_train_step(h, _p(rpd), _p(lnkd), _p(tgtd), lr, None))
+    g = np.zeros_like(p0)
+    p1 = np.zeros_like(p0)
+    rsv.check(rsv.rsv_unet_get_grads(h, g.ctypes.data_as(ctypes.c_void_p), 0))
+    rsv.check(rsv.rsv_unet_get_params(h, p1.ctypes.data_as(ctypes.c_void_p), 0))
+    g64 = g.astype(np.float64)
+    # at step 1 the bias-corrected moments are g and g^2: the step is lr * g / (|g| + eps)
+    expect = p0 - lr * g64 / (np.abs(g64) + 1e-8)
+    assert np.allclose(p1, expect, rtol=0, atol=1e-6 * lr + 1e-7 * np.abs(p0).max())
+    assert np.count_nonzero(g) > 0.9 * g.size
+    rsv.rsv_unet_destroy(h)
+
+
+def test_unet_training_reduces_loss(rsv):
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, base, levels = 32, 16, 8, 32, 3
+    params = _params(base, levels, 7)
+    h = _net(rsv, nx, ny, nz, base, levels, params)
+    rp, lnk, tgt = _inputs(nx, ny, nz, 8)
+    rpd, lnkd, tgtd = _dev(torch, rp), _dev(torch, lnk), _dev(torch, tgt)
+    losses = []
+    for _ in range(60):
+        loss = ctypes.c_double()
+        rsv.check(rsv.rsv_unet_train_step(h, _p(rpd), _p(lnkd), _p(tgtd), 2e-3, ctypes.byref(loss)))
+        losses.append(loss.value)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.5 * losses[0], losses[::10]
+    rsv.rsv_unet_destroy(h)
