@@ -57,7 +57,15 @@ typedef enum {
     RSV_ENAN = 9         /* NaN or Inf met in a norm */
 } rsv_status;
 
-typedef enum { RSV_PC_NONE = 0, RSV_PC_BJACOBI = 1, RSV_PC_BILU0 = 2, RSV_PC_CPR = 3 } rsv_pc_type;
+/* RSV_PC_CPR_LEARNED: CPR whose pressure stage is a trained network (rsv_unet.h)
+ * instead of the multigrid V-cycle; FP64 flexible GMRES only. */
+typedef enum {
+    RSV_PC_NONE = 0,
+    RSV_PC_BJACOBI = 1,
+    RSV_PC_BILU0 = 2,
+    RSV_PC_CPR = 3,
+    RSV_PC_CPR_LEARNED = 4
+} rsv_pc_type;
 typedef enum { RSV_GMRES = 0, RSV_BICGSTAB = 1, RSV_FGMRES = 2 } rsv_solver_type;
 typedef enum { RSV_PREC_FP64 = 0, RSV_PREC_MIXED = 1 } rsv_precision;
 
@@ -100,6 +108,9 @@ typedef struct {
     double true_relres;    /* ||b - A x|| / ||b|| recomputed in FP64 on the device */
     double ms_setup;       /* last rsv_precond_setup, CUDA-event time */
     double ms_solve;       /* this solve, CUDA-event time */
+    int fallback_iter;     /* RSV_PC_CPR_LEARNED: iteration at which the solve switched to
+                              the plain V-cycle; -1 if it never did (other preconditioners: -1) */
+    int pad_;
 } rsv_solve_info;
 
 /* Defaults: GMRES, m = 30, rtol 1e-8, atol 0, btol 1e-30, maxit 2000, FP64,

@@ -104,6 +104,38 @@ RSV_API rsv_status rsv_unet_apply(rsv_unet *u, const double *rp, const double *l
 RSV_API rsv_status rsv_unet_train_step(rsv_unet *u, const double *rp, const double *lnk, const double *target,
                                        float lr, double *loss);
 
+/* n training steps in a row, sample i = (rp[i], lnk[i], target[i]) (host arrays of
+ * device pointers to float64 [nx*ny*nz]), each followed by an Adam step with
+ * learning rate lr > 0; losses (host, may be NULL) receives the n losses.  The
+ * stream is synchronised once, at the end. */
+RSV_API rsv_status rsv_unet_train_batch(rsv_unet *u, int n, const double *const *rp, const double *const *lnk,
+                                        const double *const *target, float lr, double *losses);
+
+/* ------------------------------------------------------------------ use inside the solver
+ * rsv_solver_set_learned: the network u (on the solver matrix's grid, one
+ * system) becomes the pressure stage of RSV_PC_CPR_LEARNED; lnk is ln k of the
+ * grid's cells (host or device float64, copied).  The solver does not own u:
+ * keep it alive while the solver uses it.  With RSV_PC_CPR_LEARNED, every CPR
+ * application runs the network on the restricted residual instead of the
+ * V-cycle, until the solve falls back to the V-cycle for its remaining
+ * iterations: when the network's output holds a NaN or Inf, or when the
+ * implicit residual norm falls by less than 10% over 5 consecutive
+ * iterations.  Both decisions are taken on the device; rsv_solve_info
+ * .fallback_iter reports where.  Requirements: FP64 precision and the FGMRES
+ * solver (the network is a nonlinear preconditioner), else RSV_ENOTSUP at
+ * rsv_precond_setup. */
+RSV_API rsv_status rsv_solver_set_learned(rsv_solver *s, rsv_unet *u, const double *lnk, int on_device);
+
+/* rsv_solver_record_pressure: from now on, every FP64 CPR application
+ * (RSV_PC_CPR) copies its restricted right-hand side r_p = Pi_r f (nb values)
+ * into buf + k*nb for k = 0, 1, ... up to max_samples (device float64 array
+ * [max_samples][nb]).  These are the inputs of the pressure stage that the
+ * plain solver generates: the training samples of the network (their targets
+ * come from rsv_cpr_vcycle).  buf = NULL stops recording.  The count restarts
+ * at zero; rsv_solver_recorded returns it (synchronises). */
+RSV_API rsv_status rsv_solver_record_pressure(rsv_solver *s, double *buf, int max_samples);
+RSV_API rsv_status rsv_solver_recorded(rsv_solver *s, int *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -252,3 +252,22 @@ def apply_stage(params, rp, lnk, base=32, levels=4, bf16=False):
         x = x.astype(np.float32).astype(np.float64)
     out, _ = forward(params, x, base, levels, bf16)
     return s * out
+
+
+def learned_cpr_apply(nx, ny, nz, row_ptr, col_idx, vals, params, lnk, f, base=32, levels=4, bf16=True):
+    """CPR two-stage preconditioner (Section "CPR") with the network as the pressure solver.
+
+    Stage one: p = Pi_r f (quasi-IMPES weights), x = Pi_p (s U(p / s, ln k));
+    stage two: x += ILU0^{-1} (f - A x).  The restriction, prolongation,
+    SpMV and ILU(0) are the oracle's own routines (oracle.c).
+    """
+    import oracle as O
+    st, w, _ = O.qi_setup(nx, ny, nz, row_ptr, col_idx, vals)
+    assert st == 0
+    p = O.restrict_pressure(w, f)
+    xp = apply_stage(params, p.reshape(nz, ny, nx), np.asarray(lnk).reshape(nz, ny, nx), base, levels, bf16)
+    x = O.prolong_pressure(xp.ravel())
+    r = O.spmv(row_ptr, col_idx, vals, x, alpha=-1.0, beta=1.0, y=np.array(f, dtype=np.float64))
+    st, lu, udinv, _ = O.bilu0_setup(row_ptr, col_idx, vals)
+    assert st == 0
+    return x + O.bilu0_apply(row_ptr, col_idx, lu, udinv, r)

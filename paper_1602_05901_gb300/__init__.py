@@ -28,10 +28,11 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 RSV_OK, RSV_EINVAL, RSV_ENOMEM, RSV_ECUDA, RSV_ENOTSUP, RSV_ESINGULAR = 0, 1, 2, 3, 4, 5
 RSV_EBREAKDOWN, RSV_ENOCONV, RSV_ETIMEOUT, RSV_ENAN = 6, 7, 8, 9
-RSV_PC_NONE, RSV_PC_BJACOBI, RSV_PC_BILU0, RSV_PC_CPR = 0, 1, 2, 3
+RSV_PC_NONE, RSV_PC_BJACOBI, RSV_PC_BILU0, RSV_PC_CPR, RSV_PC_CPR_LEARNED = 0, 1, 2, 3, 4
 RSV_GMRES, RSV_BICGSTAB, RSV_FGMRES = 0, 1, 2
 RSV_PREC_FP64, RSV_PREC_MIXED = 0, 1
-PC_TYPES = {"none": RSV_PC_NONE, "bjacobi": RSV_PC_BJACOBI, "bilu0": RSV_PC_BILU0, "cpr": RSV_PC_CPR}
+PC_TYPES = {"none": RSV_PC_NONE, "bjacobi": RSV_PC_BJACOBI, "bilu0": RSV_PC_BILU0, "cpr": RSV_PC_CPR,
+            "cpr_learned": RSV_PC_CPR_LEARNED}
 SOLVERS = {"gmres": RSV_GMRES, "bicgstab": RSV_BICGSTAB, "fgmres": RSV_FGMRES}
 
 
@@ -49,10 +50,10 @@ class rsv_pc_params(ctypes.Structure):
 class rsv_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("status", ctypes.c_int), ("true_relres", ctypes.c_double), ("ms_setup", ctypes.c_double),
-                ("ms_solve", ctypes.c_double)]
+                ("ms_solve", ctypes.c_double), ("fallback_iter", ctypes.c_int), ("pad_", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 _P, _I, _D, _F, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.c_int64
@@ -98,6 +99,10 @@ _SIGS = {
     "rsv_unet_get_grads": (_I, [_P, _P, _I]),
     "rsv_unet_apply": (_I, [_P, _P, _P, _P]),
     "rsv_unet_train_step": (_I, [_P, _P, _P, _P, _F, ctypes.POINTER(_D)]),
+    "rsv_unet_train_batch": (_I, [_P, _I, _P, _P, _P, _F, _P]),
+    "rsv_solver_set_learned": (_I, [_P, _P, _P, _I]),
+    "rsv_solver_record_pressure": (_I, [_P, _P, _I]),
+    "rsv_solver_recorded": (_I, [_P, ctypes.POINTER(_I)]),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -286,6 +291,24 @@ class Solver:
             check(st, "rsv_solve")
         return st, info.as_dict()
 
+    def set_learned(self, unet, lnk):
+        """Make ``unet`` (a Unet on this matrix's grid) the pressure stage of "cpr_learned"; lnk: ln k per cell."""
+        on_dev = int(hasattr(lnk, "is_cuda") and lnk.is_cuda)
+        if not on_dev:
+            lnk = np.ascontiguousarray(lnk, dtype=np.float64)
+        self._unet = unet   # the solver does not own the network: keep it alive
+        check(_lib.rsv_solver_set_learned(self.handle, unet.handle, _ptr(lnk), on_dev), "rsv_solver_set_learned")
+
+    def record_pressure(self, buf, max_samples):
+        """Record the restricted right-hand sides of FP64 CPR applications into buf (device [max][nb]); None stops."""
+        check(_lib.rsv_solver_record_pressure(self.handle, _ptr(buf) if buf is not None else None,
+                                              int(max_samples)), "rsv_solver_record_pressure")
+
+    def recorded(self):
+        c = ctypes.c_int()
+        check(_lib.rsv_solver_recorded(self.handle, ctypes.byref(c)), "rsv_solver_recorded")
+        return c.value
+
     def solve_batched(self, b, x):
         """Independent per-grid solves of a batch matrix. Returns (status, [info dict per grid])."""
         on_dev = int(hasattr(b, "is_cuda") and b.is_cuda)
@@ -297,4 +320,61 @@ class Solver:
         h = getattr(self, "handle", None)
         if h:
             _lib.rsv_solver_destroy(h)
+            self.handle = None
+
+
+class Unet:
+    """The learned pressure stage's network (rsv_unet.h) on an nx*ny*nz grid."""
+
+    def __init__(self, nx, ny, nz, base=32, levels=4, stream=None):
+        self.dims = (nx, ny, nz)
+        self.base, self.levels = base, levels
+        h = ctypes.c_void_p()
+        check(_lib.rsv_unet_create(_stream_ptr(stream), nx, ny, nz, base, levels, ctypes.byref(h)), "rsv_unet_create")
+        self.handle = h
+        n = ctypes.c_int64()
+        check(_lib.rsv_unet_num_params(h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def set_params(self, p):
+        on_dev = int(hasattr(p, "is_cuda") and p.is_cuda)
+        if not on_dev:
+            p = np.ascontiguousarray(p, dtype=np.float32)
+        assert (p.numel() if on_dev else p.size) == self.nparam
+        check(_lib.rsv_unet_set_params(self.handle, _ptr(p), on_dev), "rsv_unet_set_params")
+
+    def params(self):
+        out = np.zeros(self.nparam, dtype=np.float32)
+        check(_lib.rsv_unet_get_params(self.handle, _ptr(out), 0), "rsv_unet_get_params")
+        return out
+
+    def grads(self):
+        out = np.zeros(self.nparam, dtype=np.float32)
+        check(_lib.rsv_unet_get_grads(self.handle, _ptr(out), 0), "rsv_unet_get_grads")
+        return out
+
+    def apply(self, rp, lnk, corr):
+        """corr = s * U(rp / s, lnk); CUDA float64 tensors of nx*ny*nz values."""
+        check(_lib.rsv_unet_apply(self.handle, _ptr(rp), _ptr(lnk), _ptr(corr)), "rsv_unet_apply")
+        return corr
+
+    def train_step(self, rp, lnk, target, lr):
+        loss = ctypes.c_double()
+        check(_lib.rsv_unet_train_step(self.handle, _ptr(rp), _ptr(lnk), _ptr(target), float(lr),
+                                       ctypes.byref(loss)), "rsv_unet_train_step")
+        return loss.value
+
+    def train_batch(self, rps, lnks, targets, lr):
+        """len(rps) training steps (CUDA float64 tensors), one synchronisation; returns the losses."""
+        n = len(rps)
+        arr = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        losses = np.zeros(n)
+        check(_lib.rsv_unet_train_batch(self.handle, n, arr(rps), arr(lnks), arr(targets), float(lr),
+                                        _ptr(losses)), "rsv_unet_train_batch")
+        return losses
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.rsv_unet_destroy(h)
             self.handle = None

@@ -668,6 +668,7 @@ extern "C" rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *
             infos[q].true_relres = rel;
             infos[q].ms_setup = s->ms_setup;
             infos[q].ms_solve = ms;
+            infos[q].fallback_iter = -1;
         }
         if (st != RSV_OK && worst == RSV_OK) worst = (rsv_status)st;
     }

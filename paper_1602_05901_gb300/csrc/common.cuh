@@ -182,6 +182,13 @@ template <typename T>
 cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
                       int *status, unsigned long long timeout_ns);
 template <typename T>
+cudaError_t cpr_restrict(const rsv_mat *A, const Cpr &P, const T *f, const int *done);
+template <typename T>
+cudaError_t cpr_pressure_vcycle(const rsv_mat *A, const Cpr &P, const int *gate);
+template <typename T>
+cudaError_t cpr_finish(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
+                       int *status, unsigned long long timeout_ns);
+template <typename T>
 cudaError_t cpr_vcycle(const rsv_mat *A, const Cpr &P, const T *b, T *x);
 
 // ---- launchers implemented in ilu_tiles.cu

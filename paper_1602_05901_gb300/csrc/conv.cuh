@@ -17,7 +17,8 @@ struct ConvVol {
 // stored as BF16 into y[v][ldy] and/or as FP32 into y32[v][co].
 rsv_status conv_fwd(cudaStream_t st, ConvVol vol, int taps, int ci, int co, const __nv_bfloat16 *x, int ldx,
                     const __nv_bfloat16 *w, const float *bias, int relu, const __nv_bfloat16 *mask, int ldm,
-                    __nv_bfloat16 *y, int ldy, float *y32, int *err, uint64_t timeout_ns);
+                    __nv_bfloat16 *y, int ldy, float *y32, int *err, uint64_t timeout_ns,
+                    const int *gate = nullptr);
 
 // Weights of the input gradient: wt[ci][t][co] = w[co][26 - t][ci].
 rsv_status conv_flip(cudaStream_t st, int ci, int co, const __nv_bfloat16 *w, __nv_bfloat16 *wt);

@@ -106,6 +106,7 @@ struct FwdArgs {
     float *y32;           // [V][n_total] or null
     int *err;
     uint64_t timeout_ns;
+    const int *gate;      // skip the launch when *gate != 0 (may be null)
 };
 
 template <int BK, int BN>
@@ -118,6 +119,7 @@ struct FwdSmem {
 template <int BK, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const FwdArgs a) {
+    if (a.gate && *a.gate) return;  // uniform across the CTA, before any barrier or allocation
     using L = FwdSmem<BK, BN>;
     constexpr int SWZ = BK * 2;  // 128 or 64
     constexpr uint32_t TCOLS = tmem_cols_for(BN);
@@ -568,7 +570,7 @@ WgPlan wg_plan(ConvVol v, int taps, int ci, int co) {
 
 rsv_status conv_fwd(cudaStream_t st, ConvVol v, int taps, int ci, int co, const __nv_bfloat16 *x, int ldx,
                     const __nv_bfloat16 *w, const float *bias, int relu, const __nv_bfloat16 *mask, int ldm,
-                    __nv_bfloat16 *y, int ldy, float *y32, int *err, uint64_t timeout_ns) {
+                    __nv_bfloat16 *y, int ldy, float *y32, int *err, uint64_t timeout_ns, const int *gate) {
     if (v.nx <= 0 || v.ny <= 0 || v.nz <= 0 || (taps != 1 && taps != 27) || ci <= 0 || ci % 32 || co <= 0 ||
         co % 32 || !x || !w || (!y && !y32) || ldx < ci || ldx % 8 || (y && (ldy < co || ldy % 8)) ||
         (mask && (ldm < co || ldm % 8)))
@@ -601,6 +603,7 @@ rsv_status conv_fwd(cudaStream_t st, ConvVol v, int taps, int ci, int co, const 
     a.y32 = y32;
     a.err = err;
     a.timeout_ns = timeout_ns;
+    a.gate = gate;
     CUtensorMap ma, mb;
     {
         const uint64_t dims[4] = {(uint64_t)ci, (uint64_t)v.nx, (uint64_t)v.ny, (uint64_t)v.nz};

@@ -445,26 +445,46 @@ static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done)
     return cudaGetLastError();
 }
 
+// Stage one, first half: the restricted right-hand side P.b[0] = Pi_r f.
 template <typename T>
-cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
-                      int *status, unsigned long long timeout_ns) {
+cudaError_t cpr_restrict(const rsv_mat *A, const Cpr &P, const T *f, const int *done) {
+    count_launches(1);
+    restrict_pressure_kernel<T><<<blocks(A->nb), 256, 0, A->stream>>>(A->nb, (const T *)P.w, f, (T *)P.b[0], done);
+    return cudaGetLastError();
+}
+
+// The pressure solve P.x[0] = V-cycle(P.b[0]); kernels skip when *gate != 0.
+template <typename T>
+cudaError_t cpr_pressure_vcycle(const rsv_mat *A, const Cpr &P, const int *gate) {
+    return vcycle<T>(P, 0, A->stream, gate);
+}
+
+// Stage one's prolongation x = Pi_p P.x[0], then stage two: x += ILU0^{-1}(f - A x).
+template <typename T>
+cudaError_t cpr_finish(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
+                       int *status, unsigned long long timeout_ns) {
     cudaStream_t st = A->stream;
     const int64_t nb = A->nb;
     T *r = (T *)P.r, *z = (T *)P.z;
     count_launches(1);
-    restrict_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.w, f, (T *)P.b[0], done);
-    cudaError_t e = vcycle<T>(P, 0, st, done);
-    if (e != cudaSuccess) return e;
-    count_launches(1);
     prolong_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.x[0], f, x, r, done);
-    e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
-                         : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
+    cudaError_t e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
+                                     : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
     if (e != cudaSuccess) return e;
     e = launch_ilu_apply_tiles<T>(A, tiles, r, z, done, status, timeout_ns);
     if (e != cudaSuccess) return e;
     count_launches(1);
     add_kernel<T><<<blocks(3 * nb), 256, 0, st>>>(3 * nb, z, x, done);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
+                      int *status, unsigned long long timeout_ns) {
+    cudaError_t e = cpr_restrict<T>(A, P, f, done);
+    if (e == cudaSuccess) e = vcycle<T>(P, 0, A->stream, done);
+    if (e == cudaSuccess) e = cpr_finish<T>(A, P, tiles, f, x, done, status, timeout_ns);
+    return e;
 }
 
 template <typename T>
@@ -481,6 +501,10 @@ template cudaError_t cpr_apply<double>(const rsv_mat *, const Cpr &, const IluTi
 template cudaError_t cpr_apply<float>(const rsv_mat *, const Cpr &, const IluTiles &, const float *, float *,
                                       const int *, int *, unsigned long long);
 template cudaError_t cpr_vcycle<double>(const rsv_mat *, const Cpr &, const double *, double *);
+template cudaError_t cpr_restrict<double>(const rsv_mat *, const Cpr &, const double *, const int *);
+template cudaError_t cpr_pressure_vcycle<double>(const rsv_mat *, const Cpr &, const int *);
+template cudaError_t cpr_finish<double>(const rsv_mat *, const Cpr &, const IluTiles &, const double *, double *,
+                                        const int *, int *, unsigned long long);
 template cudaError_t cpr_vcycle<float>(const rsv_mat *, const Cpr &, const float *, float *);
 
 }  // namespace rsv

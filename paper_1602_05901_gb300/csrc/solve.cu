@@ -283,6 +283,7 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
                                          &ds->counter[1], &ds->done, &ds->skip2));
             rsv::count_launches(1);
             gmres_givens<<<1, 1, 0, s->st>>>(ds, j, m);
+            if (s->pc_type == RSV_PC_CPR_LEARNED) RSV_CUDA_TRY(learned_watch(s, j));
             RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, wj, &ds->hn, &ds->done));
         }
         RSV_TRY(fetch(s, &h));
@@ -428,6 +429,7 @@ void solver_free(rsv_solver *s) {
     free_tiles(&s->tiles);
     free_cpr(&s->cpr);
     free_batch(s);
+    learned_free(s);
     if (s->e0) cudaEventDestroy(s->e0);
     if (s->e1) cudaEventDestroy(s->e1);
     delete s;
@@ -499,7 +501,10 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
 void rsv_solver_destroy(rsv_solver *s) { solver_free(s); }
 
 rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params) {
-    if (!s || pc_type < RSV_PC_NONE || pc_type > RSV_PC_CPR) return RSV_EINVAL;
+    if (!s || pc_type < RSV_PC_NONE || pc_type > RSV_PC_CPR_LEARNED) return RSV_EINVAL;
+    if (pc_type == RSV_PC_CPR_LEARNED && (s->mixed || s->p.solver != RSV_FGMRES)) return RSV_ENOTSUP;
+    if (pc_type == RSV_PC_CPR_LEARNED && !s->unet) return RSV_EINVAL;
+    const bool cpr = pc_type == RSV_PC_CPR || pc_type == RSV_PC_CPR_LEARNED;
     rsv_pc_params pcp;
     rsv_pc_params_default(&pcp);
     if (params) pcp = *params;
@@ -517,7 +522,7 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
             RSV_CUDA_TRY(cudaMalloc((void **)&s->dinv32, sizeof(float) * 9 * std::max<int64_t>(A->nb, 1)));
         RSV_CUDA_TRY(launch_bj_setup(A, s->mixed, s->dinv, s->mixed ? s->dinv32 : nullptr, &s->ds->status));
     }
-    if (pc_type == RSV_PC_BILU0 || pc_type == RSV_PC_CPR) {
+    if (pc_type == RSV_PC_BILU0 || cpr) {
         if (!s->sch.cells) RSV_CUDA_TRY(build_schedule(A, &s->sch));
         RSV_CUDA_TRY(launch_ilu_setup(A, s->sch, s->mixed, s->dinv, &s->ds->status));
         if (s->mixed)
@@ -525,8 +530,8 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
         else
             RSV_CUDA_TRY(tiles_setup<double>(A, s->dinv, &s->tiles));
     }
-    if (pc_type == RSV_PC_CPR && A->nsys > 1) return RSV_ENOTSUP;
-    if (pc_type == RSV_PC_CPR)
+    if (cpr && A->nsys > 1) return RSV_ENOTSUP;
+    if (cpr)
         RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, &s->cpr,
                                &s->ds->status));
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
@@ -563,7 +568,7 @@ rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z) {
 }
 
 rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, double *a7_host) {
-    if (!s || s->pc_type != RSV_PC_CPR) return RSV_EINVAL;
+    if (!s || (s->pc_type != RSV_PC_CPR && s->pc_type != RSV_PC_CPR_LEARNED)) return RSV_EINVAL;
     const Cpr &P = s->cpr;
     if (nlev) *nlev = P.nlev;
     if (dims)
@@ -590,7 +595,8 @@ rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, dou
 }
 
 rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x) {
-    if (!s || !b || !x || b == x || s->pc_type != RSV_PC_CPR || s->mixed) return RSV_EINVAL;
+    if (!s || !b || !x || b == x || (s->pc_type != RSV_PC_CPR && s->pc_type != RSV_PC_CPR_LEARNED) || s->mixed)
+        return RSV_EINVAL;
     RSV_CUDA_TRY(cpr_vcycle<double>(s->A, s->cpr, b, x));
     return RSV_OK;
 }
@@ -624,9 +630,16 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
     const double tol = std::max(s->p.rtol * bnorm, s->p.atol);
     const int maxit = s->p.maxit;
     RSV_CUDA_TRY(cudaMemcpyAsync(&s->ds->maxit, &maxit, sizeof(int), cudaMemcpyHostToDevice, s->st));
+    const bool learned = s->pc_type == RSV_PC_CPR_LEARNED;
+    if (learned) RSV_TRY(learned_reset(s));
     rsv_solve_info local{};
     rsv_status st = s->mixed ? solve_mixed(s, db, dx, tol, &local) : solve_fp64(s, db, dx, tol, &local);
     if (st == RSV_ECUDA || st == RSV_ENOMEM) return st;
+    int fallback_iter = -1;
+    if (learned) {
+        const rsv_status ls = learned_finish(s, &fallback_iter);
+        if (ls != RSV_OK) st = ls;
+    }
     // FP64 true residual, recomputed; the iteration count from the device
     double rn = 0.0;
     int iters = 0;
@@ -646,6 +659,7 @@ rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, r
         info->true_relres = bnorm > 0 ? rn / bnorm : rn;
         info->ms_setup = s->ms_setup;
         info->ms_solve = ms;
+        info->fallback_iter = fallback_iter;
     }
     return st;
 }

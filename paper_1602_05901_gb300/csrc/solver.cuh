@@ -2,6 +2,7 @@
 // drivers (solve.cu) and the batched driver (batch.cu).
 #pragma once
 
+#include "../../include/rsv_unet.h"
 #include "common.cuh"
 
 // Krylov workspace of one vector precision.
@@ -34,11 +35,28 @@ struct rsv_solver {
     rsv::IluTiles tiles;
     rsv::Cpr cpr;
     void *batch = nullptr;       // batched-solve state (batch.cu)
+    // learned pressure stage (RSV_PC_CPR_LEARNED, learned.cu)
+    rsv_unet *unet = nullptr;    // not owned
+    double *lnk = nullptr;       // ln k of the cells, device
+    int *lflags = nullptr;       // [0] fell back, [1] skip network, [2] skip V-cycle, [3] steps seen, [4] fallback iteration
+    double *lhist = nullptr;     // the last 8 implicit residual norms (ring)
+    // recorder of the pressure stage's right-hand sides (RSV_PC_CPR, FP64)
+    double *rec_buf = nullptr;
+    int rec_max = 0;
+    int *rec_count = nullptr;
     double ms_setup = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
 namespace rsv {
+
+// learned.cu: CPR with the network as pressure stage, CPR with recording, the stall watch.
+cudaError_t learned_cpr_apply(rsv_solver *s, const double *f, double *x, const int *done);
+cudaError_t cpr_apply_recording(rsv_solver *s, const double *f, double *x, const int *done);
+cudaError_t learned_watch(rsv_solver *s, int j);
+rsv_status learned_reset(rsv_solver *s);
+rsv_status learned_finish(rsv_solver *s, int *fallback_iter);
+void learned_free(rsv_solver *s);
 
 template <typename T>
 cudaError_t spmv(rsv_solver *s, T alpha, const T *x, T beta, T *y, const int *done);
@@ -63,8 +81,13 @@ inline cudaError_t pc_apply(rsv_solver *s, const T *r, T *z, const int *done) {
         return launch_ilu_apply_tiles<T>(s->A, s->tiles, r, z, done, &s->ds->status,
                                          (unsigned long long)s->p.watchdog * 1000ull);
     case RSV_PC_CPR:
+        if (sizeof(T) == 8 && s->rec_buf)
+            return cpr_apply_recording(s, (const double *)r, (double *)z, done);
         return cpr_apply<T>(s->A, s->cpr, s->tiles, r, z, done, &s->ds->status,
                             (unsigned long long)s->p.watchdog * 1000ull);
+    case RSV_PC_CPR_LEARNED:
+        if (sizeof(T) == 8) return learned_cpr_apply(s, (const double *)r, (double *)z, done);
+        return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }

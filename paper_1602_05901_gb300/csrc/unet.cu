@@ -46,7 +46,8 @@ __device__ __forceinline__ __nv_bfloat16 tobf(float f) { return __float2bfloat16
 // mode 0: sum rp^2 and sum lnk; mode 1: sum (lnk - mu)^2 with mu = stats[1] / V.
 __global__ void __launch_bounds__(256) stats_partial(const double *__restrict__ rp, const double *__restrict__ lnk,
                                                      int64_t n, int mode, const double *__restrict__ stats,
-                                                     double *__restrict__ part) {
+                                                     double *__restrict__ part, const int *gate) {
+    if (gate && *gate) return;
     __shared__ double r0[256], r1[256];
     double a = 0.0, b = 0.0;
     const double mu = mode ? stats[1] / (double)n : 0.0;
@@ -76,8 +77,9 @@ __global__ void __launch_bounds__(256) stats_partial(const double *__restrict__ 
 }
 
 // stats: [0] sum rp^2, [1] sum lnk, [2] sum (lnk-mu)^2, [3] s = rms(rp), [4] mu, [5] sd
-__global__ void stats_final(const double *__restrict__ part, int nblk, int64_t n, int mode, double *stats) {
-    if (threadIdx.x != 0) return;
+__global__ void stats_final(const double *__restrict__ part, int nblk, int64_t n, int mode, double *stats,
+                            const int *gate) {
+    if (threadIdx.x != 0 || (gate && *gate)) return;
     double a = 0.0, b = 0.0;
     for (int i = 0; i < nblk; ++i) {
         a += part[2 * i];
@@ -97,7 +99,8 @@ __global__ void stats_final(const double *__restrict__ part, int nblk, int64_t n
 // in[v][2t + c] = standardised channel c at voxel v + off_t (zero outside), t < 27; channels 54..63 zero.
 __global__ void __launch_bounds__(256) im2col_inputs(const double *__restrict__ rp, const double *__restrict__ lnk,
                                                      const double *__restrict__ stats, int nx, int ny, int nz,
-                                                     __nv_bfloat16 *__restrict__ in) {
+                                                     __nv_bfloat16 *__restrict__ in, const int *gate) {
+    if (gate && *gate) return;
     const int64_t V = (int64_t)nx * ny * nz;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= V * 32) return;
@@ -119,7 +122,9 @@ __global__ void __launch_bounds__(256) im2col_inputs(const double *__restrict__ 
 
 // out[v'][c] = bf16(mean of the 8 children of v'), child values src[v][off + c] (ld lds).
 __global__ void __launch_bounds__(256) avgpool_bf16(const __nv_bfloat16 *__restrict__ src, int lds, int C, int nx,
-                                                    int ny, int nz, __nv_bfloat16 *__restrict__ dst) {
+                                                    int ny, int nz, __nv_bfloat16 *__restrict__ dst,
+                                                    const int *gate) {
+    if (gate && *gate) return;
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
     const int64_t total = (int64_t)cx * cy * cz * C;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -138,7 +143,9 @@ __global__ void __launch_bounds__(256) avgpool_bf16(const __nv_bfloat16 *__restr
 
 // dst[v][c] = src[parent(v)][c] for c < C (fine volume nx*ny*nz, dst ld ldd), 8 channels per thread.
 __global__ void __launch_bounds__(256) upsample_bf16(const __nv_bfloat16 *__restrict__ src, int C, int nx, int ny,
-                                                     int nz, __nv_bfloat16 *__restrict__ dst, int ldd) {
+                                                     int nz, __nv_bfloat16 *__restrict__ dst, int ldd,
+                                                     const int *gate) {
+    if (gate && *gate) return;
     const int c8 = C / 8;
     const int64_t total = (int64_t)nx * ny * nz * c8;
     const int cx = nx / 2, cy = ny / 2;
@@ -191,7 +198,8 @@ __global__ void __launch_bounds__(256) combine_skip_pool(const __nv_bfloat16 *__
 // out[v] = sum_c top[v][c] wh[c] + bh (FP32); corr[v] = s * out[v] (optional).
 __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16 *__restrict__ top, int C, int64_t V,
                                                 const float *__restrict__ wh, const double *__restrict__ stats,
-                                                float *__restrict__ out, double *__restrict__ corr) {
+                                                float *__restrict__ out, double *__restrict__ corr, const int *gate) {
+    if (gate && *gate) return;
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= V) return;
     float acc = 0.0f;
@@ -316,6 +324,7 @@ struct rsv_unet {
     void *wscratch = nullptr;
     int *err = nullptr;
     int adam_t = 0;
+    const int *gate = nullptr;  // forward kernels skip when *gate != 0 (solver use)
     bool acts_valid = false;  // activations of the last forward pass are kept (train step needs them)
     std::vector<void *> allocs;
 
@@ -423,7 +432,7 @@ rsv_status unet_alloc(rsv_unet *u) {
 rsv_status conv(rsv_unet *u, int l, int layer, const __nv_bfloat16 *x, int ldx, __nv_bfloat16 *y, int ldy) {
     const Layer &ly = u->layers[layer];
     return conv_fwd(u->st, u->vol[l], 27, ly.ci, ly.co, x, ldx, u->W(layer), u->B(layer), 1, nullptr, 0, y, ldy,
-                    nullptr, u->err, kTimeoutNs);
+                    nullptr, u->err, kTimeoutNs, u->gate);
 }
 
 // Forward pass; keeps every activation for the backward pass.  corr (optional) = s * output.
@@ -431,21 +440,23 @@ rsv_status forward(rsv_unet *u, const double *rp, const double *lnk, double *cor
     cudaStream_t st = u->st;
     const int L = u->L;
     const int64_t V0 = u->V[0];
-    stats_partial<<<kRedBlk, 256, 0, st>>>(rp, lnk, V0, 0, u->stats, u->part);
-    stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 0, u->stats);
-    stats_partial<<<kRedBlk, 256, 0, st>>>(rp, lnk, V0, 1, u->stats, u->part);
-    stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 1, u->stats);
-    im2col_inputs<<<blocks_for(V0 * 32, 256, 1 << 30), 256, 0, st>>>(rp, lnk, u->stats, u->nx, u->ny, u->nz, u->in);
+    const int *gate = u->gate;
+    stats_partial<<<kRedBlk, 256, 0, st>>>(rp, lnk, V0, 0, u->stats, u->part, gate);
+    stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 0, u->stats, gate);
+    stats_partial<<<kRedBlk, 256, 0, st>>>(rp, lnk, V0, 1, u->stats, u->part, gate);
+    stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 1, u->stats, gate);
+    im2col_inputs<<<blocks_for(V0 * 32, 256, 1 << 30), 256, 0, st>>>(rp, lnk, u->stats, u->nx, u->ny, u->nz, u->in,
+                                                                     gate);
     RSV_CUDA_TRY(cudaGetLastError());
     count_launches(5);
     // first layer: 1x1x1 GEMM over the im2col channels
     RSV_TRY(conv_fwd(st, u->vol[0], 1, 64, u->ch[0], u->in, 64, u->w1c, u->B(0), 1, nullptr, 0, u->ea[0], u->ch[0],
-                     nullptr, u->err, kTimeoutNs));
+                     nullptr, u->err, kTimeoutNs, gate));
     for (int l = 0; l < L; ++l) {
         if (l > 0) {
             const ConvVol &f = u->vol[l - 1];
             avgpool_bf16<<<blocks_for(u->V[l] * u->ch[l - 1]), 256, 0, st>>>(u->eb(l - 1), u->ldeb(l - 1), u->ch[l - 1],
-                                                                              f.nx, f.ny, f.nz, u->pool[l]);
+                                                                              f.nx, f.ny, f.nz, u->pool[l], gate);
             RSV_CUDA_TRY(cudaGetLastError());
             count_launches(1);
             RSV_TRY(conv(u, l, u->enc_a(l), u->pool[l], u->ch[l - 1], u->ea[l], u->ch[l]));
@@ -456,14 +467,14 @@ rsv_status forward(rsv_unet *u, const double *rp, const double *lnk, double *cor
         const __nv_bfloat16 *src = l == L - 2 ? u->ebL : u->db[l + 1];
         const ConvVol &f = u->vol[l];
         upsample_bf16<<<blocks_for(u->V[l] * u->ch[l + 1] / 8), 256, 0, st>>>(src, u->ch[l + 1], f.nx, f.ny, f.nz,
-                                                                              u->cat[l], u->catC[l]);
+                                                                              u->cat[l], u->catC[l], gate);
         RSV_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         RSV_TRY(conv(u, l, u->dec_a(l), u->cat[l], u->catC[l], u->da[l], u->ch[l]));
         RSV_TRY(conv(u, l, u->dec_b(l), u->da[l], u->ch[l], u->db[l], u->ch[l]));
     }
     head_fwd<<<blocks_for(V0, 256, 1 << 30), 256, 0, st>>>(u->top(), u->ch[0], V0, u->p + u->layers[u->head()].woff,
-                                                           u->stats, u->out, corr);
+                                                           u->stats, u->out, corr, gate);
     RSV_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     u->acts_valid = true;
@@ -548,12 +559,21 @@ rsv_status check_err(rsv_unet *u) {
 
 }  // namespace
 
-rsv_status unet_apply_device(rsv_unet *u, cudaStream_t st, const double *rp, const double *lnk, double *corr) {
+rsv_status unet_apply_device(rsv_unet *u, cudaStream_t st, const double *rp, const double *lnk, double *corr,
+                             const int *gate) {
     cudaStream_t saved = u->st;
     u->st = st;
+    u->gate = gate;
     rsv_status s = forward(u, rp, lnk, corr);
     u->st = saved;
+    u->gate = nullptr;
     return s;
+}
+
+void unet_dims(const rsv_unet *u, int *nx, int *ny, int *nz) {
+    *nx = u->nx;
+    *ny = u->ny;
+    *nz = u->nz;
 }
 
 int unet_error(rsv_unet *u, cudaStream_t st) {
@@ -671,4 +691,37 @@ extern "C" rsv_status rsv_unet_train_step(rsv_unet *u, const double *rp, const d
     }
     if (loss) RSV_CUDA_TRY(cudaMemcpyAsync(loss, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->st));
     return check_err(u);
+}
+
+extern "C" rsv_status rsv_unet_train_batch(rsv_unet *u, int n, const double *const *rp, const double *const *lnk,
+                                           const double *const *target, float lr, double *losses) {
+    if (!u || n < 0 || (n > 0 && (!rp || !lnk || !target)) || !(lr > 0.0f)) return RSV_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!rp[i] || !lnk[i] || !target[i]) return RSV_EINVAL;
+    double *dloss = nullptr;
+    if (losses && n > 0) RSV_CUDA_TRY(cudaMallocAsync((void **)&dloss, sizeof(double) * n, u->st));
+    rsv_status st = RSV_OK;
+    for (int i = 0; i < n && st == RSV_OK; ++i) {
+        st = forward(u, rp[i], lnk[i], nullptr);
+        if (st == RSV_OK) st = backward(u, target[i]);
+        if (st != RSV_OK) break;
+        u->adam_t += 1;
+        const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, u->adam_t)));
+        const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, u->adam_t)));
+        adam_kernel<<<blocks_for(u->nparam, 256, 2048), 256, 0, u->st>>>(u->p, u->g, u->m, u->v, u->nparam, lr, 0.9f,
+                                                                         0.999f, 1e-8f, c1, c2, u->pw);
+        pack_first<<<(u->ch[0] * 64 + 255) / 256, 256, 0, u->st>>>(u->p + u->layers[0].woff, u->ch[0], u->w1c);
+        count_launches(2);
+        if (dloss && cudaMemcpyAsync(dloss + i, u->loss, sizeof(double), cudaMemcpyDeviceToDevice, u->st) != cudaSuccess)
+            st = RSV_ECUDA;
+        if (cudaGetLastError() != cudaSuccess) st = RSV_ECUDA;
+    }
+    if (dloss) {
+        if (st == RSV_OK &&
+            cudaMemcpyAsync(losses, dloss, sizeof(double) * n, cudaMemcpyDeviceToHost, u->st) != cudaSuccess)
+            st = RSV_ECUDA;
+        cudaFreeAsync(dloss, u->st);
+    }
+    const rsv_status e = check_err(u);
+    return st != RSV_OK ? st : e;
 }

@@ -282,3 +282,35 @@ def batch_sizes(count=64, seed=3):
     ny = 16 + (u[:, 1] * 81).astype(int)
     nz = 16 + (u[:, 2] * 33).astype(int)
     return [(int(a), int(b), int(c)) for a, b, c in zip(nx, ny, nz)]
+
+
+S_NET = 20  # stream of the network's initial weights
+
+
+def unet_init(base=32, levels=4, seed=0, cin=2):
+    """Initial parameters of the learned stage's U-Net as one float32 array.
+
+    He-normal weights (standard deviation sqrt(2 / fan_in)) and zero biases,
+    drawn from the counter-based generator, laid out per layer as weight then
+    bias in the order enc1a, enc1b, ..., encLb, dec(L-1)a, dec(L-1)b, ...,
+    dec1a, dec1b, head (3x3x3 weights [co][27][ci], head [1][base]).
+    """
+    ch = [base << l for l in range(levels)]
+    shapes = []
+    prev = cin
+    for l in range(levels):
+        shapes += [(ch[l], prev, 27), (ch[l], ch[l], 27)]
+        prev = ch[l]
+    for l in range(levels - 2, -1, -1):
+        shapes += [(ch[l], ch[l + 1] + ch[l], 27), (ch[l], ch[l], 27)]
+    shapes.append((1, ch[0], 1))
+    parts = []
+    off = 0
+    for co, ci, taps in shapes:
+        nw = co * ci * taps
+        w = std_normal(seed, S_NET, np.arange(off, off + nw)) * np.sqrt(2.0 / (taps * ci))
+        if taps == 1:
+            w = w * 0.1  # a small head: the untrained stage starts near zero
+        parts += [w, np.zeros(co)]
+        off += nw
+    return np.concatenate(parts).astype(np.float32)

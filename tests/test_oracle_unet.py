@@ -167,3 +167,16 @@ def test_standardise():
     assert np.isclose(np.mean(x[..., 0] ** 2), 1.0)
     assert np.isclose(x[..., 1].mean(), 0.0, atol=1e-14) and np.isclose(x[..., 1].std(), 1.0)
     assert np.all(U.apply_stage(_params(2, 1, 1), np.zeros((2, 4, 4)), lnk, 2, 1) == 0)
+
+
+def test_learned_cpr_with_zero_network_is_block_ilu0():
+    """A network whose output is zero leaves only CPR's second stage: block ILU(0) of f."""
+    import oracle as O
+    import synth
+    nx, ny, nz = 8, 4, 2
+    p = synth.make_problem(nx, ny, nz, seed=2)
+    params = {n: (np.zeros((co, 27, ci) if t == 27 else (co, ci)), np.zeros(co)) for n, co, ci, t in U.layer_shapes(2, 2)}
+    f = np.random.default_rng(3).standard_normal(3 * p.nb)
+    z = U.learned_cpr_apply(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, params, p.lnk, f, base=2, levels=2, bf16=False)
+    st, lu, udinv, _ = O.bilu0_setup(p.row_ptr, p.col_idx, p.vals)
+    assert np.array_equal(z, 0.0 + O.bilu0_apply(p.row_ptr, p.col_idx, lu, udinv, f))
