@@ -236,6 +236,170 @@ def run_batch(args):
     return 0
 
 
+def unet_flops(nx, ny, nz, base=32, levels=4):
+    """(forward flops, training-step flops) of the U-Net, counted from its layers.
+
+    A 3x3x3 layer costs 2*V*co*ci*27 per pass; the first layer's 27 taps x 2 input
+    channels count as K = 54 (its padding to 64 is not counted).  Training runs the
+    forward pass, the input gradient of every layer but the first, and every
+    weight gradient.
+    """
+    ch = [base << l for l in range(levels)]
+    V = [(nx >> l) * (ny >> l) * (nz >> l) for l in range(levels)]
+    layers = []  # (V, co, K)
+    prev = 2
+    for l in range(levels):
+        layers += [(V[l], ch[l], prev * 27), (V[l], ch[l], ch[l] * 27)]
+        prev = ch[l]
+    for l in range(levels - 2, -1, -1):
+        layers += [(V[l], ch[l], (ch[l + 1] + ch[l]) * 27), (V[l], ch[l], ch[l] * 27)]
+    fwd = sum(2.0 * v * co * k for v, co, k in layers) + 2.0 * V[0] * ch[0]
+    dgrad = sum(2.0 * v * co * k for v, co, k in layers[1:])
+    return fwd, fwd + dgrad + fwd
+
+
+def tc_peak():
+    """Dense BF16 tensor peak (TFLOP/s): MEASURED_PEAKS.json when present, else the recipe's fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_unet(args):
+    """Time the learned stage's network at 128x128x64: one application and one training step."""
+    import numpy as np
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+    nx, ny, nz = 128, 128, 64
+    net = rsv.Unet(nx, ny, nz, base=32, levels=4)
+    net.set_params(synth.unet_init(32, 4, seed=0))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    V = nx * ny * nz
+    rp = torch.randn(V, dtype=torch.float64, device="cuda", generator=g)
+    lnk = torch.randn(V, dtype=torch.float64, device="cuda", generator=g)
+    tgt = torch.randn(V, dtype=torch.float64, device="cuda", generator=g) * 0.05
+    out = torch.empty_like(rp)
+    fwd_f, train_f = unet_flops(nx, ny, nz)
+
+    def timed(fn, k):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_apply = timed(lambda: net.apply(rp, lnk, out), args.steps)
+    ms_train = timed(lambda: net.train_batch([rp] * 8, [lnk] * 8, [tgt] * 8, 1e-4), args.steps) / 8
+    peak, src = tc_peak()
+    line = {"workload": "unet_128x128x64_base32_L4", "metric": "U-Net application and training step",
+            "apply_ms": round(ms_apply, 3), "apply_tflops": round(fwd_f / ms_apply * 1e-9, 1),
+            "train_step_ms": round(ms_train, 3), "train_tflops": round(train_f / ms_train * 1e-9, 1),
+            "flops_apply": fwd_f, "flops_train_step": train_f, "peak_bf16_tflops": peak, "peak_source": src,
+            "apply_frac_of_peak": round(fwd_f / ms_apply * 1e-9 / peak, 4),
+            "params": int(net.nparam), "dtype": "bf16 operands, fp32 accumulate"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_learned(args):
+    """The learned pressure stage on the 128x128x64 channelised workload.
+
+    Training: the pressure-stage inputs of plain FP64 FGMRES(30) + CPR solves of
+    ``--learned-train`` seeded systems (the first 40 CPR applications of each),
+    V-cycle targets, ``--learned-epochs`` epochs of Adam.  Evaluation on
+    ``--learned-eval`` unseen seeds: FP64 GMRES(30) + CPR (the V-cycle) against
+    FP64 FGMRES(30) + learned CPR (with its fallback) and FGMRES(30) + block ILU(0)
+    (the method without a pressure stage), each to rtol 1e-8; time = setup + solve.
+    """
+    import numpy as np
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+    from paper_1602_05901_gb300 import learned as Lr
+    grid = (128, 128, 64)
+    t0 = time.perf_counter()
+    samples, gen_s = [], 0.0
+    for q in range(args.learned_train):
+        tg = time.perf_counter()
+        p = synth.workload("learned_128x128x64", seed=20000 + q)
+        gen_s += time.perf_counter() - tg
+        rp, tgt = Lr.collect_samples(grid, p.vals, p.b, 40)
+        lnk = torch.tensor(p.lnk, device="cuda")
+        samples += [(rp[i], lnk, tgt[i]) for i in range(rp.shape[0])]
+        del p
+    collect_s = time.perf_counter() - t0 - gen_s
+    net = rsv.Unet(*grid, base=32, levels=4)
+    net.set_params(synth.unet_init(32, 4, seed=0))
+    _, train_f = unet_flops(*grid)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    losses = Lr.train(net, samples, args.learned_epochs, lr=3e-4, seed=0)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    steps = len(samples) * args.learned_epochs
+    rows = []
+    imit = None
+    for q in range(args.learned_eval):
+        p = synth.workload("learned_128x128x64", seed=30000 + q)
+        if q == 0:
+            rpe, tge = Lr.collect_samples(grid, p.vals, p.b, 20)
+            imit = float(Lr.imitation_error(net, rpe, torch.tensor(p.lnk, device="cuda"), tge).mean())
+            del rpe, tge
+        A = rsv.Matrix(*grid)
+        A.set_values(p.vals)
+        for solver, pc in (("gmres", "cpr"), ("fgmres", "cpr_learned"), ("fgmres", "bilu0")):
+            s = rsv.Solver(A, solver=solver, precision="fp64", rtol=1e-8, maxit=4000)
+            if pc == "cpr_learned":
+                # stall window of one restart cycle: plain CPR itself falls only ~2% per iteration
+                # on this workload, so the 10%-over-5 default would flag any preconditioner
+                s.set_learned(net, p.lnk, stall_window=30, stall_drop=0.10)
+            s.setup(pc)
+            x = np.zeros(3 * p.nb)
+            st, info = s.solve(p.b.copy(), x)
+            rows.append({"seed": 30000 + q, "solver": solver, "pc": pc, "status": st, "iters": info["iters"],
+                         "ms": round(info["ms_setup"] + info["ms_solve"], 1),
+                         "true_relres": info["true_relres"], "fallback_iter": info["fallback_iter"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del s
+        del A, p
+
+    def med(pc, key):
+        v = [r[key] for r in rows if r["pc"] == pc and r["status"] == 0]
+        return float(statistics.median(v)) if v else None
+
+    line = {"workload": "learned_128x128x64 (channelised sigma 2, 16 seeded wells)",
+            "metric": "time to rtol 1e-8 (FP64 true residual), median over unseen seeds", "unit": "ms",
+            "higher_is_better": False,
+            "plain_cpr_gmres_ms": med("cpr", "ms"), "learned_cpr_fgmres_ms": med("cpr_learned", "ms"),
+            "bilu0_fgmres_ms": med("bilu0", "ms"),
+            "plain_cpr_iters": med("cpr", "iters"), "learned_cpr_iters": med("cpr_learned", "iters"),
+            "bilu0_iters": med("bilu0", "iters"),
+            "learned_fallbacks": sum(1 for r in rows if r["pc"] == "cpr_learned" and r["fallback_iter"] >= 0),
+            "all_converged": all(r["status"] == 0 and r["true_relres"] <= 1e-8 for r in rows),
+            "stall_rule": "fall back when the implicit residual falls < 10% over 30 iterations",
+            "eval_seeds": args.learned_eval, "train_systems": args.learned_train, "train_samples": len(samples),
+            "epochs": args.learned_epochs, "loss_first_last_epoch": [losses[0], losses[-1]],
+            "imitation_error_unseen": imit,
+            "train_step_ms": round(train_ms / steps, 3), "train_tflops": round(train_f * steps / train_ms * 1e-9, 1),
+            "generation_s": round(gen_s, 1), "sample_collection_s": round(collect_s, 1), "runs": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_profile_mode(mode):
     """Small, self-checking runs of the hot path for ncu (no timing is reported)."""
     import torch
@@ -282,7 +446,11 @@ def main():
     ap.add_argument("--cpu-sample-iters", type=int, default=60)
     ap.add_argument("--ref-sample-iters", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "profile-solve", "profile-kernels", "batch"],
+    ap.add_argument("--learned-train", type=int, default=12, help="learned mode: training systems")
+    ap.add_argument("--learned-epochs", type=int, default=20, help="learned mode: epochs")
+    ap.add_argument("--learned-eval", type=int, default=4, help="learned mode: unseen evaluation seeds")
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "profile-solve", "profile-kernels", "batch", "unet", "learned"],
                     help="profile-solve: one short mixed GMRES(30)+BILU0 solve (60 inner iterations) on the "
                          "benchmark workload, for an ncu launch list; profile-kernels: set up the benchmark "
                          "workload and run each hot kernel (FP64/FP32 SpMV, FP32/FP64 ILU(0) apply) three times, "
@@ -292,6 +460,10 @@ def main():
     args = ap.parse_args()
     if args.mode == "batch":
         return run_batch(args)
+    if args.mode == "unet":
+        return run_unet(args)
+    if args.mode == "learned":
+        return run_learned(args)
     if args.mode != "bench":
         return run_profile_mode(args.mode)
     if args.warmup < 3 and args.impl == "rsv":

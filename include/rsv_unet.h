@@ -119,12 +119,14 @@ RSV_API rsv_status rsv_unet_train_batch(rsv_unet *u, int n, const double *const 
  * application runs the network on the restricted residual instead of the
  * V-cycle, until the solve falls back to the V-cycle for its remaining
  * iterations: when the network's output holds a NaN or Inf, or when the
- * implicit residual norm falls by less than 10% over 5 consecutive
- * iterations.  Both decisions are taken on the device; rsv_solve_info
+ * implicit residual norm falls by less than the fraction stall_drop over
+ * stall_window consecutive iterations (stall_window <= 0 selects 10% over 5;
+ * at most 64).  Both decisions are taken on the device; rsv_solve_info
  * .fallback_iter reports where.  Requirements: FP64 precision and the FGMRES
  * solver (the network is a nonlinear preconditioner), else RSV_ENOTSUP at
  * rsv_precond_setup. */
-RSV_API rsv_status rsv_solver_set_learned(rsv_solver *s, rsv_unet *u, const double *lnk, int on_device);
+RSV_API rsv_status rsv_solver_set_learned(rsv_solver *s, rsv_unet *u, const double *lnk, int on_device,
+                                          int stall_window, double stall_drop);
 
 /* rsv_solver_record_pressure: from now on, every FP64 CPR application
  * (RSV_PC_CPR) copies its restricted right-hand side r_p = Pi_r f (nb values)

@@ -100,7 +100,7 @@ _SIGS = {
     "rsv_unet_apply": (_I, [_P, _P, _P, _P]),
     "rsv_unet_train_step": (_I, [_P, _P, _P, _P, _F, ctypes.POINTER(_D)]),
     "rsv_unet_train_batch": (_I, [_P, _I, _P, _P, _P, _F, _P]),
-    "rsv_solver_set_learned": (_I, [_P, _P, _P, _I]),
+    "rsv_solver_set_learned": (_I, [_P, _P, _P, _I, _I, _D]),
     "rsv_solver_record_pressure": (_I, [_P, _P, _I]),
     "rsv_solver_recorded": (_I, [_P, ctypes.POINTER(_I)]),
 }
@@ -291,13 +291,17 @@ class Solver:
             check(st, "rsv_solve")
         return st, info.as_dict()
 
-    def set_learned(self, unet, lnk):
-        """Make ``unet`` (a Unet on this matrix's grid) the pressure stage of "cpr_learned"; lnk: ln k per cell."""
+    def set_learned(self, unet, lnk, stall_window=0, stall_drop=0.10):
+        """Make ``unet`` (a Unet on this matrix's grid) the pressure stage of "cpr_learned"; lnk: ln k per cell.
+
+        Fall back to the V-cycle when the residual falls by less than stall_drop over stall_window
+        iterations (stall_window <= 0: 10% over 5)."""
         on_dev = int(hasattr(lnk, "is_cuda") and lnk.is_cuda)
         if not on_dev:
             lnk = np.ascontiguousarray(lnk, dtype=np.float64)
         self._unet = unet   # the solver does not own the network: keep it alive
-        check(_lib.rsv_solver_set_learned(self.handle, unet.handle, _ptr(lnk), on_dev), "rsv_solver_set_learned")
+        check(_lib.rsv_solver_set_learned(self.handle, unet.handle, _ptr(lnk), on_dev, int(stall_window),
+                                          float(stall_drop)), "rsv_solver_set_learned")
 
     def record_pressure(self, buf, max_samples):
         """Record the restricted right-hand sides of FP64 CPR applications into buf (device [max][nb]); None stops."""

@@ -404,34 +404,42 @@ __global__ void __launch_bounds__(kThreads, 1)
 // of the weight gradient: out[d][c][f], f = ((z+1)(ny+2) + (y+1)) nx + x over
 // z in [-1, nz], y in [-1, ny]; out[d][c][f] = x[z, y, x + d - 1, c] when
 // nshift = 3 (d = 0, 1, 2), x[z, y, x, c] when nshift = 1; zero outside the grid.
+// One CTA per (padded row, 32 channels, 128-voxel chunk of the row): the chunk
+// and a one-voxel halo are read once, coalesced along the channels, and
+// written nshift times, coalesced along x.
+constexpr int kVmChunk = 128;
 __global__ void __launch_bounds__(256)
     to_voxel_major(const __nv_bfloat16 *__restrict__ src, int ld, int nch, int nx, int ny, int nz, int nshift,
                    int64_t vpad, __nv_bfloat16 *__restrict__ dst) {
-    __shared__ __nv_bfloat16 tile[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t f0 = (int64_t)blockIdx.x * 32;
+    __shared__ __nv_bfloat16 tile[kVmChunk + 2][33];
+    const int row = blockIdx.x;  // padded row index (zp * (ny + 2) + yp)
     const int c0 = blockIdx.y * 32;
-    const int d = blockIdx.z;
-    const int plane = (ny + 2) * nx;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int64_t f = f0 + ty + 8 * k;
-        __nv_bfloat16 v = __float2bfloat16(0.0f);
-        if (f < vpad && c0 + tx < nch) {
-            const int zp = (int)(f / plane), rem = (int)(f % plane);
-            const int z = zp - 1, y = rem / nx - 1;
-            const int x = rem % nx + (nshift == 3 ? d - 1 : 0);
-            if (z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx)
-                v = src[(((int64_t)z * ny + y) * nx + x) * ld + c0 + tx];
+    const int x0 = blockIdx.z * kVmChunk;
+    const int zp = row / (ny + 2), yp = row - zp * (ny + 2);
+    const int z = zp - 1, y = yp - 1;
+    const int w = min(kVmChunk, nx - x0);
+    const bool real = z >= 0 && z < nz && y >= 0 && y < ny;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    if (real) {
+        const int64_t base = ((int64_t)z * ny + y) * nx;
+        for (int i = threadIdx.x; i < (w + 2) * 32; i += 256) {
+            const int xl = i >> 5, c = i & 31;
+            const int x = x0 + xl - 1;
+            __nv_bfloat16 v = zero;
+            if (x >= 0 && x < nx && c0 + c < nch) v = src[(base + x) * ld + c0 + c];
+            tile[xl][c] = v;
         }
-        tile[ty + 8 * k][tx] = v;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = c0 + ty + 8 * k;
-        const int64_t f = f0 + tx;
-        if (c < nch && f < vpad) dst[((int64_t)d * nch + c) * vpad + f] = tile[tx][ty + 8 * k];
+    const int64_t f0 = (int64_t)row * nx + x0;
+    for (int d = 0; d < nshift; ++d) {
+        const int sh = nshift == 3 ? d - 1 : 0;
+        for (int i = threadIdx.x; i < 32 * w; i += 256) {
+            const int c = i / w, xl = i - c * w;
+            if (c0 + c >= nch) continue;
+            const __nv_bfloat16 v = real ? tile[xl + 1 + sh][c] : zero;
+            dst[((int64_t)d * nch + c0 + c) * vpad + f0 + xl] = v;
+        }
     }
 }
 
@@ -449,20 +457,32 @@ __global__ void wgrad_reduce(const float *__restrict__ partial, int splits, int 
     }
 }
 
-// gb[c] = sum over the padded voxel-major row c (pads are zero); one block per channel, fixed tree order.
+// gb[c] = sum over the padded voxel-major row c (pads are zero): each CTA sums one
+// of kBgChunks chunks of a row (fixed tree order), then bias_grad_final adds
+// the chunks in order.
+constexpr int kBgChunks = 32;
 __global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16 *__restrict__ gyt, int64_t vpad,
-                                                 float *__restrict__ gb) {
+                                                 float *__restrict__ part) {
     __shared__ float red[256];
     const __nv_bfloat16 *r = gyt + (int64_t)blockIdx.x * vpad;
+    const int64_t len = (vpad + kBgChunks - 1) / kBgChunks;
+    const int64_t a = blockIdx.y * len, b = min(vpad, a + len);
     float s = 0.0f;
-    for (int64_t f = threadIdx.x; f < vpad; f += 256) s += __bfloat162float(r[f]);
+    for (int64_t f = a + threadIdx.x; f < b; f += 256) s += __bfloat162float(r[f]);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) gb[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) part[blockIdx.x * kBgChunks + blockIdx.y] = red[0];
+}
+__global__ void bias_grad_final(const float *__restrict__ part, int co, float *__restrict__ gb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= co) return;
+    float s = 0.0f;
+    for (int k = 0; k < kBgChunks; ++k) s += part[c * kBgChunks + k];
+    gb[c] = s;
 }
 
 // Weights of the input gradient: wt[ci][t][co] = w[co][26 - t][ci].
@@ -648,11 +668,10 @@ rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, cons
     __nv_bfloat16 *gyt = (__nv_bfloat16 *)((char *)scratch + p.xt_bytes);
     float *part = (float *)((char *)scratch + p.xt_bytes + p.gyt_bytes);
     if (!aligned16(scratch)) return RSV_EINVAL;
-    const int fblocks = (int)((p.vpad + 31) / 32);
-    to_voxel_major<<<dim3(fblocks, ci / 32, p.nshift), 256, 0, st>>>(x, ldx, ci, v.nx, v.ny, v.nz, p.nshift, p.vpad,
-                                                                       xt);
+    const int prow = (v.nz + 2) * (v.ny + 2), xchunks = (v.nx + kVmChunk - 1) / kVmChunk;
+    to_voxel_major<<<dim3(prow, ci / 32, xchunks), 256, 0, st>>>(x, ldx, ci, v.nx, v.ny, v.nz, p.nshift, p.vpad, xt);
     RSV_CUDA_TRY(cudaGetLastError());
-    to_voxel_major<<<dim3(fblocks, co / 32, 1), 256, 0, st>>>(gy, ldgy, co, v.nx, v.ny, v.nz, 1, p.vpad, gyt);
+    to_voxel_major<<<dim3(prow, co / 32, xchunks), 256, 0, st>>>(gy, ldgy, co, v.nx, v.ny, v.nz, 1, p.vpad, gyt);
     RSV_CUDA_TRY(cudaGetLastError());
     CUtensorMap ma, mb;
     {
@@ -687,9 +706,11 @@ rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, cons
     RSV_CUDA_TRY(cudaGetLastError());
     int n = 4;
     if (gb) {
-        bias_grad<<<co, 256, 0, st>>>(gyt, p.vpad, gb);
+        // the partial sums of the weight gradient are consumed: reuse their buffer
+        bias_grad<<<dim3(co, kBgChunks), 256, 0, st>>>(gyt, p.vpad, part);
+        bias_grad_final<<<(co + 127) / 128, 128, 0, st>>>(part, co, gb);
         RSV_CUDA_TRY(cudaGetLastError());
-        n = 5;
+        n = 6;
     }
     count_launches(n);
     return RSV_OK;

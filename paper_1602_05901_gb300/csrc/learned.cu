@@ -10,8 +10,8 @@
 // trip:
 //   skip_net = done || fell_back,  skip_vcycle = done || !fell_back.
 // The solve falls back (for good) when the network's output holds a NaN or an
-// Inf, or when the implicit residual norm of FGMRES falls by less than 10%
-// over 5 consecutive iterations.
+// Inf, or when the implicit residual norm of FGMRES falls by less than a
+// fraction `drop` over `window` consecutive iterations (default 10% over 5).
 #include <cmath>
 
 #include "solver.cuh"
@@ -36,16 +36,19 @@ __global__ void check_finite(const double *__restrict__ x, int64_t n, int *fl, c
     if (atomicCAS(&fl[0], 0, 1) == 0) fl[4] = *iters;
 }
 
+constexpr int kHist = 64;  // ring of implicit residual norms; the stall window is at most kHist
+
 // After the Givens rotation of Arnoldi step j: the implicit residual |g[j+1]|.
-__global__ void watch_kernel(const DevState *ds, int j, int *fl, double *hist) {
+// Stall: it fell by less than the fraction `drop` over the last `window` steps.
+__global__ void watch_kernel(const DevState *ds, int j, int *fl, double *hist, int window, double drop) {
     if (ds->jend != j + 1 || fl[0]) return;  // the step did not run, or the solve already fell back
     const double r = fabs(ds->g[j + 1]);
     const int k = fl[3];
-    if (!isfinite(r) || (k >= 5 && r > 0.9 * hist[(k - 5) % 8])) {
+    if (!isfinite(r) || (k >= window && r > (1.0 - drop) * hist[(k - window) % kHist])) {
         fl[0] = 1;
         fl[4] = ds->iters;
     }
-    hist[k % 8] = r;
+    hist[k % kHist] = r;
     fl[3] = k + 1;
 }
 
@@ -108,7 +111,7 @@ cudaError_t cpr_apply_recording(rsv_solver *s, const double *f, double *x, const
 }
 
 cudaError_t learned_watch(rsv_solver *s, int j) {
-    watch_kernel<<<1, 1, 0, s->st>>>(s->ds, j, s->lflags, s->lhist);
+    watch_kernel<<<1, 1, 0, s->st>>>(s->ds, j, s->lflags, s->lhist, s->stall_window, s->stall_drop);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -140,20 +143,23 @@ void learned_free(rsv_solver *s) {
 
 using namespace rsv;
 
-extern "C" rsv_status rsv_solver_set_learned(rsv_solver *s, rsv_unet *u, const double *lnk, int on_device) {
-    if (!s || !u || !lnk) return RSV_EINVAL;
+extern "C" rsv_status rsv_solver_set_learned(rsv_solver *s, rsv_unet *u, const double *lnk, int on_device,
+                                             int stall_window, double stall_drop) {
+    if (!s || !u || !lnk || stall_window > kHist || !(stall_drop < 1.0)) return RSV_EINVAL;
     const rsv_mat *A = s->A;
     int nx, ny, nz;
     unet_dims(u, &nx, &ny, &nz);
     if (A->nsys != 1 || A->h_sys[0].nx != nx || A->h_sys[0].ny != ny || A->h_sys[0].nz != nz) return RSV_EINVAL;
     if (!s->lnk) RSV_CUDA_TRY(cudaMalloc((void **)&s->lnk, sizeof(double) * A->nb));
     if (!s->lflags) RSV_CUDA_TRY(cudaMalloc((void **)&s->lflags, sizeof(int) * 8));
-    if (!s->lhist) RSV_CUDA_TRY(cudaMalloc((void **)&s->lhist, sizeof(double) * 8));
+    if (!s->lhist) RSV_CUDA_TRY(cudaMalloc((void **)&s->lhist, sizeof(double) * kHist));
     RSV_CUDA_TRY(cudaMemcpyAsync(s->lnk, lnk, sizeof(double) * A->nb,
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
     RSV_TRY(learned_reset(s));
     RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
     s->unet = u;
+    s->stall_window = stall_window > 0 ? stall_window : 5;
+    s->stall_drop = stall_window > 0 ? stall_drop : 0.10;
     return RSV_OK;
 }
 

@@ -39,7 +39,9 @@ struct rsv_solver {
     rsv_unet *unet = nullptr;    // not owned
     double *lnk = nullptr;       // ln k of the cells, device
     int *lflags = nullptr;       // [0] fell back, [1] skip network, [2] skip V-cycle, [3] steps seen, [4] fallback iteration
-    double *lhist = nullptr;     // the last 8 implicit residual norms (ring)
+    double *lhist = nullptr;     // the last implicit residual norms (ring of 64)
+    int stall_window = 5;        // fall back when the residual fell by less than stall_drop
+    double stall_drop = 0.10;    // over stall_window iterations
     // recorder of the pressure stage's right-hand sides (RSV_PC_CPR, FP64)
     double *rec_buf = nullptr;
     int rec_max = 0;

@@ -96,28 +96,38 @@ __global__ void stats_final(const double *__restrict__ part, int nblk, int64_t n
     }
 }
 
-// in[v][2t + c] = standardised channel c at voxel v + off_t (zero outside), t < 27; channels 54..63 zero.
-__global__ void __launch_bounds__(256) im2col_inputs(const double *__restrict__ rp, const double *__restrict__ lnk,
-                                                     const double *__restrict__ stats, int nx, int ny, int nz,
-                                                     __nv_bfloat16 *__restrict__ in, const int *gate) {
+// xs[v] = (bf16(rp[v] / s), bf16((lnk[v] - mu) / sd)): the two standardised input channels.
+__global__ void __launch_bounds__(256) standardise_inputs(const double *__restrict__ rp, const double *__restrict__ lnk,
+                                                          const double *__restrict__ stats, int64_t V,
+                                                          __nv_bfloat162 *__restrict__ xs, const int *gate) {
     if (gate && *gate) return;
-    const int64_t V = (int64_t)nx * ny * nz;
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= V * 32) return;
-    const int64_t v = gid >> 5;
-    const int t = (int)(gid & 31);
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= V) return;
     const double s = stats[3], mu = stats[4], sd = stats[5];
-    float c0 = 0.0f, c1 = 0.0f;
+    const float c0 = s > 0.0 ? (float)(rp[v] / s) : 0.0f;
+    const float c1 = sd > 0.0 ? (float)((lnk[v] - mu) / sd) : 0.0f;
+    xs[v] = __floats2bfloat162_rn(c0, c1);
+}
+
+// in[v][2t + c] = xs[v + off_t].c (zero outside the grid) for t < 27; channels 54..63 zero.
+// Thread (v, t), t in [0, 32): one 4-byte store each, coalesced.
+__global__ void __launch_bounds__(256) im2col_inputs(const __nv_bfloat162 *__restrict__ xs, int nx, int ny, int nz,
+                                                     __nv_bfloat162 *__restrict__ in, const int *gate) {
+    if (gate && *gate) return;
+    const int plane = nx * ny;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t V = (int64_t)plane * nz;
+    if (gid >= V * 32) return;
+    const int v = (int)(gid >> 5);
+    const int t = (int)(gid & 31);
+    __nv_bfloat162 val = __floats2bfloat162_rn(0.0f, 0.0f);
     if (t < 27) {
-        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        const int z = v / plane, r = v - z * plane;
+        const int y = r / nx, x = r - y * nx;
         const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
-        if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz) {
-            const int64_t u = ((int64_t)zz * ny + yy) * nx + xx;
-            if (s > 0.0) c0 = (float)(rp[u] / s);
-            if (sd > 0.0) c1 = (float)((lnk[u] - mu) / sd);
-        }
+        if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz) val = xs[zz * plane + yy * nx + xx];
     }
-    ((__nv_bfloat162 *)in)[gid] = __floats2bfloat162_rn(c0, c1);
+    in[gid] = val;
 }
 
 // out[v'][c] = bf16(mean of the 8 children of v'), child values src[v][off + c] (ld lds).
@@ -316,6 +326,7 @@ struct rsv_unet {
     __nv_bfloat16 *pw = nullptr, *w1c = nullptr, *wflip = nullptr;
     float *g1c = nullptr;
     __nv_bfloat16 *in = nullptr, *ebL = nullptr;
+    __nv_bfloat162 *xs = nullptr;  // the two standardised input channels per voxel
     __nv_bfloat16 *ea[kMaxNetLevels] = {}, *cat[kMaxNetLevels] = {}, *da[kMaxNetLevels] = {}, *db[kMaxNetLevels] = {},
                   *pool[kMaxNetLevels] = {};
     __nv_bfloat16 *gA[kMaxNetLevels] = {}, *gB[kMaxNetLevels] = {}, *gcat[kMaxNetLevels] = {}, *gp[kMaxNetLevels] = {};
@@ -391,6 +402,7 @@ rsv_status unet_alloc(rsv_unet *u) {
     RSV_TRY(u->alloc(&u->wflip, flip));
     // activations and gradients
     RSV_TRY(u->alloc(&u->in, (size_t)u->V[0] * 64));
+    RSV_TRY(u->alloc(&u->xs, (size_t)u->V[0]));
     for (int l = 0; l < L; ++l) {
         const size_t V = (size_t)u->V[l], c = (size_t)u->ch[l];
         RSV_TRY(u->alloc(&u->ea[l], V * c));
@@ -445,10 +457,11 @@ rsv_status forward(rsv_unet *u, const double *rp, const double *lnk, double *cor
     stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 0, u->stats, gate);
     stats_partial<<<kRedBlk, 256, 0, st>>>(rp, lnk, V0, 1, u->stats, u->part, gate);
     stats_final<<<1, 32, 0, st>>>(u->part, kRedBlk, V0, 1, u->stats, gate);
-    im2col_inputs<<<blocks_for(V0 * 32, 256, 1 << 30), 256, 0, st>>>(rp, lnk, u->stats, u->nx, u->ny, u->nz, u->in,
-                                                                     gate);
+    standardise_inputs<<<blocks_for(V0, 256, 1 << 30), 256, 0, st>>>(rp, lnk, u->stats, V0, u->xs, gate);
+    im2col_inputs<<<blocks_for(V0 * 32, 256, 1 << 30), 256, 0, st>>>(u->xs, u->nx, u->ny, u->nz,
+                                                                     (__nv_bfloat162 *)u->in, gate);
     RSV_CUDA_TRY(cudaGetLastError());
-    count_launches(5);
+    count_launches(6);
     // first layer: 1x1x1 GEMM over the im2col channels
     RSV_TRY(conv_fwd(st, u->vol[0], 1, 64, u->ch[0], u->in, 64, u->w1c, u->B(0), 1, nullptr, 0, u->ea[0], u->ch[0],
                      nullptr, u->err, kTimeoutNs, gate));

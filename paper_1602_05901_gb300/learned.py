@@ -40,7 +40,7 @@ def collect_samples(grid, vals, b, max_samples, restart=30):
     return rp, tgt
 
 
-def train(net: Unet, samples, epochs, lr=1e-3, seed=0, chunk=64):
+def train(net: Unet, samples, epochs, lr=3e-4, seed=0, chunk=64):
     """Adam over the samples [(rp, lnk, target) CUDA tensors], shuffled each epoch (seeded).
 
     Returns the mean loss of each epoch.

@@ -130,7 +130,7 @@ def test_recorder_captures_pressure_stage_inputs(rsv, prob):
 
 
 def test_trained_network_gains_over_the_method_without_it(rsv):
-    """Train on recorded pressure-stage samples of 6 systems; evaluate on an unseen one.
+    """Train on recorded pressure-stage samples of 10 systems; evaluate on an unseen one.
 
     "Without it" is the same FGMRES + CPR with the network removed: a zero
     pressure correction leaves block ILU(0) alone.  The trained network must
@@ -141,19 +141,19 @@ def test_trained_network_gains_over_the_method_without_it(rsv):
     from paper_1602_05901_gb300 import learned as Lr
     grid = (64, 32, 16)
     samples = []
-    for q in range(6):
+    for q in range(10):
         p = synth.make_problem(*grid, seed=100 + q, perm="lognormal", sigma=1.0, wells="seeded")
         rp, tgt = Lr.collect_samples(grid, p.vals, p.b, 40)
         lnk = torch.tensor(p.lnk, device="cuda")
         samples += [(rp[i], lnk, tgt[i]) for i in range(rp.shape[0])]
-    assert len(samples) == 240
+    assert len(samples) == 400
     net = rsv.Unet(*grid, base=32, levels=3)
     net.set_params(synth.unet_init(32, 3, seed=1))
     pe = synth.make_problem(*grid, seed=200, perm="lognormal", sigma=1.0, wells="seeded")
     rpe, tge = Lr.collect_samples(grid, pe.vals, pe.b, 30)
     lnke = torch.tensor(pe.lnk, device="cuda")
     err0 = Lr.imitation_error(net, rpe, lnke, tge).mean()
-    losses = Lr.train(net, samples, 20, lr=1e-3, seed=0)
+    losses = Lr.train(net, samples, 40, lr=3e-4, seed=0)
     err1 = Lr.imitation_error(net, rpe, lnke, tge).mean()
     assert losses[-1] < losses[0] and err1 < 0.75 * err0, (losses, err0, err1)
     A = rsv.Matrix(*grid)
