@@ -400,6 +400,34 @@ def run_learned(args):
     return 0
 
 
+def run_profile_conv():
+    """One launch of each hot convolution on the network's finest level (128x128x64, 32 and 96 channels),
+    for ncu captures; checks that the outputs are finite.  Prints no benchmark line."""
+    import ctypes
+
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    nx, ny, nz = 128, 128, 64
+    V = nx * ny * nz
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = (torch.randn(V, 96, device="cuda", generator=g)).to(torch.bfloat16)
+    w = (torch.randn(32, 27, 96, device="cuda", generator=g) * 0.02).to(torch.bfloat16)
+    y = torch.empty(V, 32, dtype=torch.bfloat16, device="cuda")
+    gw = torch.empty(32, 27, 96, device="cuda")
+    gb = torch.empty(32, device="cuda")
+    gx = torch.empty(V, 96, dtype=torch.bfloat16, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    rsv.check(rsv.rsv_conv3d_fwd(None, nx, ny, nz, 27, 32, 32, p(x), 96, p(w), None, 1, None, 0, p(y), 32, None))
+    rsv.check(rsv.rsv_conv3d_fwd(None, nx, ny, nz, 27, 96, 32, p(x), 96, p(w), None, 1, None, 0, p(y), 32, None))
+    rsv.check(rsv.rsv_conv3d_dgrad(None, nx, ny, nz, 96, 32, p(y), 32, p(w), None, 0, p(gx), 96, None))
+    rsv.check(rsv.rsv_conv3d_wgrad(None, nx, ny, nz, 27, 96, 32, p(x), 96, p(y), 32, p(gw), p(gb)))
+    torch.cuda.synchronize()
+    assert torch.isfinite(y.float()).all() and torch.isfinite(gx.float()).all() and torch.isfinite(gw).all()
+    print("profile-conv done", flush=True)
+    return 0
+
+
 def run_profile_mode(mode):
     """Small, self-checking runs of the hot path for ncu (no timing is reported)."""
     import torch
@@ -450,7 +478,7 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=20, help="learned mode: epochs")
     ap.add_argument("--learned-eval", type=int, default=4, help="learned mode: unseen evaluation seeds")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "profile-solve", "profile-kernels", "batch", "unet", "learned"],
+                    choices=["bench", "profile-solve", "profile-kernels", "profile-conv", "batch", "unet", "learned"],
                     help="profile-solve: one short mixed GMRES(30)+BILU0 solve (60 inner iterations) on the "
                          "benchmark workload, for an ncu launch list; profile-kernels: set up the benchmark "
                          "workload and run each hot kernel (FP64/FP32 SpMV, FP32/FP64 ILU(0) apply) three times, "
@@ -462,6 +490,8 @@ def main():
         return run_batch(args)
     if args.mode == "unet":
         return run_unet(args)
+    if args.mode == "profile-conv":
+        return run_profile_conv()
     if args.mode == "learned":
         return run_learned(args)
     if args.mode != "bench":

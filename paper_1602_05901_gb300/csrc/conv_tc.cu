@@ -399,6 +399,205 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 2) tmem_dealloc(tmem, TCOLS);
 }
 
+// ------------------------------------------------------------------ weight gradient, MN-major operands
+// The same reduction over voxels as conv_wgrad_tc, read straight from the
+// channels-last tensors: a TMA box of 64 voxels x (32 or 64) channels lands
+// in shared memory as 64 rows (K = voxels) of consecutive channels (M or N),
+// i.e. an MN-major operand.  Every tap shift (dz, dy, dx) is a plain TMA
+// coordinate offset on the voxel axes, with zero fill outside the grid, so no
+// copy of the activations is made.
+//   A columns: tpt taps x cblk channels = 128 rows of M, in columns of colA
+//   (64 or 32) channels; B columns: BN output channels in columns of colB.
+struct WgMnArgs {
+    int bw, bh, bd;                  // voxel box of one K chunk (bw * bh * bd = 64)
+    int kcx, kcy, nchunks, cps;      // chunk grid (x, y; z implied), chunks per split
+    int taps, ci, cblk, tpt, ncb, colA;  // ci: channels of the row (tap-shifted) operand
+    int co, colB;                    // co: channels of the column operand
+    int sgn;                         // +1: rows read at v + off_t; -1: at v - off_t
+    float *partial;                  // [splits][taps][ci][co] in the row / column channel roles
+    int *err;
+    uint64_t timeout_ns;
+};
+
+template <int BN>
+struct WgMnSmem {
+    static constexpr uint32_t A = 128 * 64 * 2, B = BN * 64 * 2, STAGE = A + B;
+    static constexpr uint32_t BARS = kStages * STAGE;
+    static constexpr uint32_t BYTES = BARS + 256 + 1024;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_wgrad_mn(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmG, const WgMnArgs a) {
+    using L = WgMnSmem<BN>;
+    constexpr uint32_t TCOLS = tmem_cols_for(BN);
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t *full = (uint64_t *)(sm + L::BARS);
+    uint64_t *empty = full + kStages;
+    uint64_t *done = empty + kStages;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    int *flags = (int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tg = blockIdx.x / a.ncb, cb = blockIdx.x % a.ncb;
+    const int n0 = blockIdx.y * BN;
+    const int q0 = blockIdx.z * a.cps;
+    const int q1 = min(a.nchunks, q0 + a.cps);
+    const int nk = max(0, q1 - q0);
+    const int ntap = min(a.tpt, a.taps - tg * a.tpt);
+    const int colsA = 128 / a.colA, colsB = BN / a.colB;  // columns per operand
+    const int colsPerTap = a.cblk / a.colA;
+    const uint32_t rowA = a.colA * 2, rowB = a.colB * 2;  // bytes per K row of a column
+    const uint64_t deadline = now_ns() + a.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        flags[0] = flags[1] = flags[2] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) tmem_alloc(tmem_slot, TCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_map(&tmX);
+        prefetch_map(&tmG);
+        const uint32_t bytes = (uint32_t)(ntap * colsPerTap) * 64 * rowA + (uint32_t)colsB * 64 * rowB;
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (kk >= kStages && !mbar_wait(&empty[s], ((kk / kStages) + 1) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            const int q = q0 + kk;
+            const int x0 = (q % a.kcx) * a.bw, y0 = ((q / a.kcx) % a.kcy) * a.bh, z0 = (q / (a.kcx * a.kcy)) * a.bd;
+            uint8_t *st = sm + s * L::STAGE;
+            mbar_expect_tx(&full[s], bytes);
+            for (int g = 0; g < ntap; ++g) {
+                const int tap = tg * a.tpt + g;
+                int dz = 0, dy = 0, dx = 0;
+                if (a.taps == 27) {
+                    dz = tap / 9 - 1;
+                    dy = (tap / 3) % 3 - 1;
+                    dx = tap % 3 - 1;
+                }
+                for (int j = 0; j < colsPerTap; ++j)
+                    tma_load_4d(st + (g * colsPerTap + j) * 64 * rowA, &tmX, cb * a.cblk + j * a.colA,
+                                x0 + a.sgn * dx, y0 + a.sgn * dy, z0 + a.sgn * dz, &full[s]);
+            }
+            for (int j = 0; j < colsB; ++j)
+                tma_load_4d(st + L::A + j * 64 * rowB, &tmG, n0 + j * a.colB, x0, y0, z0, &full[s]);
+        }
+        flags[1] = kk;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_bf16(128, BN, true, true);
+        const int swzA = a.colA == 64 ? 128 : 64, swzB = a.colB == 64 ? 128 : 64;
+        const uint32_t colbA = 64 * rowA, colbB = 64 * rowB, grpA = 8 * rowA, grpB = 8 * rowB;
+        (void)colsA;
+        int kk = 0;
+        for (; kk < nk; ++kk) {
+            const int s = kk % kStages;
+            if (!mbar_wait(&full[s], (kk / kStages) & 1, deadline)) {
+                flags[0] = 1;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t sa = smem_u32(sm + s * L::STAGE), sb = sa + L::A;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)  // 4 x K = 16 rows = the 64 voxels of the chunk
+                mma_bf16(tmem, mnmajor_desc(sa + j * 2 * grpA, swzA, colbA, grpA),
+                         mnmajor_desc(sb + j * 2 * grpB, swzB, colbB, grpB), idesc, (kk > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        flags[2] = kk;
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, deadline + a.timeout_ns);
+    fence_after_sync();
+    const int row = warp * 32 + lane;
+    const int g = row / a.cblk, c = row % a.cblk;
+    const int tap = tg * a.tpt + g;
+    const bool valid = ok && g < ntap && !flags[0];
+    float *out = a.partial + (((int64_t)blockIdx.z * a.taps + tap) * a.ci + cb * a.cblk + c) * a.co + n0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float acc[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c0, acc);
+        if (!valid) continue;
+        if (nk == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.0f;
+        }
+        float4 *o = (float4 *)(out + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0 && (flags[0] || !ok)) {
+        raise(a.err, RSV_ETIMEOUT);
+        for (int kk = flags[2]; kk < flags[1]; ++kk)
+            mbar_wait(&full[kk % kStages], (kk / kStages) & 1, now_ns() + a.timeout_ns);
+    }
+    __syncthreads();
+    if (warp == 2) tmem_dealloc(tmem, TCOLS);
+}
+
+// gb[c] partial sums from the channels-last gradient: CTA b sums its chunk of
+// voxels for every channel (lane l owns channels l, l + 32, ...; warps stride
+// the voxels), warps added in order.  part[b][co].
+__global__ void __launch_bounds__(256) bias_grad_cl(const __nv_bfloat16 *__restrict__ gy, int ld, int co, int64_t V,
+                                                    float *__restrict__ part) {
+    __shared__ float red[8][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t len = (V + gridDim.x - 1) / gridDim.x;
+    const int64_t v0 = blockIdx.x * len, v1 = min(V, v0 + len);
+    const int nq = (co + 31) / 32;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t v = v0 + warp;
+    for (; v + 24 < v1; v += 32)  // four voxels in flight per warp
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nq && lane + 32 * q < co) {
+                const int c = lane + 32 * q;
+                const float a0 = __bfloat162float(gy[v * ld + c]), a1 = __bfloat162float(gy[(v + 8) * ld + c]);
+                const float a2 = __bfloat162float(gy[(v + 16) * ld + c]), a3 = __bfloat162float(gy[(v + 24) * ld + c]);
+                acc[q] += (a0 + a1) + (a2 + a3);
+            }
+    for (; v < v1; v += 8)
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nq && lane + 32 * q < co) acc[q] += __bfloat162float(gy[v * ld + lane + 32 * q]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (lane + 32 * q < co) red[warp][lane + 32 * q] = acc[q];
+    __syncthreads();
+    for (int c = threadIdx.x; c < co; c += 256) {
+        float t = 0.0f;
+        for (int w = 0; w < 8; ++w) t += red[w][c];
+        part[(int64_t)blockIdx.x * co + c] = t;
+    }
+}
+__global__ void bias_grad_cl_final(const float *__restrict__ part, int nblk, int co, float *__restrict__ gb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= co) return;
+    float t = 0.0f;
+    for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * co + c];
+    gb[c] = t;
+}
+
 // ------------------------------------------------------------------ helper kernels
 // Voxel-major copy of a channels-last volume into the zero-padded flat layout
 // of the weight gradient: out[d][c][f], f = ((z+1)(ny+2) + (y+1)) nx + x over
@@ -443,16 +642,19 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// gw[co][t][ci] = sum over splits of partial[s][t][ci][co], in split order.
+// gw[co][t][ci] = sum over splits of the partials, in split order.  The partials are
+// [s][t][ci][co] (swap = 0), or [s][t][co][ci] (swap = 1: rows were output channels).
 __global__ void wgrad_reduce(const float *__restrict__ partial, int splits, int taps, int ci, int co,
-                             float *__restrict__ gw) {
+                             float *__restrict__ gw, int swap) {
     const int64_t total = (int64_t)taps * ci * co;
+    const int ra = swap ? co : ci, rb = swap ? ci : co;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int o = (int)(i / ((int64_t)taps * ci));
         const int t = (int)((i / ci) % taps);
         const int c = (int)(i % ci);
+        const int row = swap ? o : c, col = swap ? c : o;
         float s = 0.0f;
-        for (int q = 0; q < splits; ++q) s += partial[(((int64_t)q * taps + t) * ci + c) * co + o];
+        for (int q = 0; q < splits; ++q) s += partial[(((int64_t)q * taps + t) * ra + row) * rb + col];
         gw[i] = s;
     }
 }
@@ -555,34 +757,75 @@ cudaError_t launch_wg(int bn, cudaStream_t st, dim3 grid, const CUtensorMap &ma,
     }
 }
 
+template <int BN>
+cudaError_t launch_wgmn_t(cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb,
+                          const WgMnArgs &a) {
+    using L = WgMnSmem<BN>;
+    static cudaError_t attr = set_smem(conv_wgrad_mn<BN>, L::BYTES);
+    if (attr != cudaSuccess) return attr;
+    conv_wgrad_mn<BN><<<grid, kThreads, L::BYTES, st>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgmn(int bn, cudaStream_t st, dim3 grid, const CUtensorMap &ma, const CUtensorMap &mb,
+                        const WgMnArgs &a) {
+    switch (bn) {
+        case 32: return launch_wgmn_t<32>(st, grid, ma, mb, a);
+        case 64: return launch_wgmn_t<64>(st, grid, ma, mb, a);
+        case 96: return launch_wgmn_t<96>(st, grid, ma, mb, a);
+        case 128: return launch_wgmn_t<128>(st, grid, ma, mb, a);
+        case 192: return launch_wgmn_t<192>(st, grid, ma, mb, a);
+        default: return launch_wgmn_t<256>(st, grid, ma, mb, a);
+    }
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 struct WgPlan {
     int64_t vpad;
     int nchunks, cblk, tpt, ncb, mtiles, bn, ntiles, splits, cps, nshift;
-    size_t xt_bytes, gyt_bytes, part_bytes;
+    size_t xt_bytes, gyt_bytes, part_bytes, bias_bytes;
+    bool mn;                 // MN-major path: operands read straight from the channels-last tensors
+    bool swap;               // MN path with rows = (tap, output channel): the gradient is the shifted operand
+    int bw, bh, bd, kcx, kcy;
 };
+
+constexpr int kBiasBlocks = 1024;
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 WgPlan wg_plan(ConvVol v, int taps, int ci, int co) {
     WgPlan p{};
+    p.bw = std::min(v.nx, 64);
+    p.bh = std::min(v.ny, 64 / p.bw);
+    p.bd = 64 / (p.bw * p.bh);
+    p.mn = p.bw * p.bh * p.bd == 64 && p.bd <= v.nz;
     p.vpad = (int64_t)(v.nz + 2) * (v.ny + 2) * v.nx;
-    p.nchunks = (int)((p.vpad + 63) / 64);
-    p.cblk = ci % 128 == 0 ? 128 : ci % 64 == 0 ? 64 : 32;
+    if (p.mn) {
+        p.kcx = (v.nx + p.bw - 1) / p.bw;
+        p.kcy = (v.ny + p.bh - 1) / p.bh;
+        p.nchunks = p.kcx * p.kcy * ((v.nz + p.bd - 1) / p.bd);
+    } else {
+        p.nchunks = (int)((p.vpad + 63) / 64);
+    }
+    // the wider channel count becomes the MMA's N when both operands are read channels-last
+    p.swap = p.mn && ci > co;
+    const int ra = p.swap ? co : ci, rb = p.swap ? ci : co;
+    p.cblk = ra % 128 == 0 ? 128 : ra % 64 == 0 ? 64 : 32;
     p.tpt = 128 / p.cblk;
-    p.ncb = ci / p.cblk;
+    p.ncb = ra / p.cblk;
     p.mtiles = ((taps + p.tpt - 1) / p.tpt) * p.ncb;
-    p.bn = pick_bn(co);
-    p.ntiles = p.bn ? co / p.bn : 0;
+    p.bn = pick_bn(rb);
+    p.ntiles = p.bn ? rb / p.bn : 0;
     const int ctas = std::max(1, p.mtiles * p.ntiles);
     int splits = std::max(1, std::min(p.nchunks, (2 * 152 + ctas - 1) / ctas));
     p.cps = (p.nchunks + splits - 1) / splits;
     p.splits = (p.nchunks + p.cps - 1) / p.cps;
     p.nshift = taps == 27 ? 3 : 1;
-    p.xt_bytes = round256((size_t)p.nshift * ci * p.vpad * 2);
-    p.gyt_bytes = round256((size_t)co * p.vpad * 2);
+    p.xt_bytes = p.mn ? 0 : round256((size_t)p.nshift * ci * p.vpad * 2);
+    p.gyt_bytes = p.mn ? 0 : round256((size_t)co * p.vpad * 2);
     p.part_bytes = round256((size_t)p.splits * taps * ci * co * 4);
+    p.bias_bytes = round256((size_t)kBiasBlocks * co * 4);
     return p;
 }
 
@@ -654,7 +897,7 @@ rsv_status conv_flip(cudaStream_t st, int ci, int co, const __nv_bfloat16 *w, __
 
 size_t conv_wgrad_scratch(ConvVol v, int taps, int ci, int co) {
     const WgPlan p = wg_plan(v, taps, ci, co);
-    return p.xt_bytes + p.gyt_bytes + p.part_bytes;
+    return p.xt_bytes + p.gyt_bytes + p.part_bytes + p.bias_bytes;
 }
 
 rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, const __nv_bfloat16 *x, int ldx,
@@ -664,10 +907,68 @@ rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, cons
         co <= 0 || co % 32 || !x || !gy || !gw || !scratch || ldx < ci || ldgy < co)
         return RSV_EINVAL;
     const WgPlan p = wg_plan(v, taps, ci, co);
+    if (!aligned16(scratch)) return RSV_EINVAL;
+    if (p.mn) {
+        if (!aligned16(x) || !aligned16(gy) || ldx % 8 || ldgy % 8) return RSV_EINVAL;
+        float *part = (float *)((char *)scratch + p.xt_bytes + p.gyt_bytes);
+        float *bpart = (float *)((char *)part + p.part_bytes);
+        WgMnArgs a{};
+        a.bw = p.bw;
+        a.bh = p.bh;
+        a.bd = p.bd;
+        a.kcx = p.kcx;
+        a.kcy = p.kcy;
+        a.nchunks = p.nchunks;
+        a.cps = p.cps;
+        a.taps = taps;
+        a.ci = p.swap ? co : ci;
+        a.cblk = p.cblk;
+        a.tpt = p.tpt;
+        a.ncb = p.ncb;
+        a.colA = p.cblk >= 64 ? 64 : 32;
+        a.co = p.swap ? ci : co;
+        a.colB = p.bn % 64 == 0 ? 64 : 32;
+        a.sgn = p.swap ? -1 : 1;
+        a.partial = part;
+        a.err = err;
+        a.timeout_ns = timeout_ns;
+        // row operand: the tap-shifted one (x, or gy when swapped); column operand: the other
+        const __nv_bfloat16 *rowp = p.swap ? gy : x, *colp = p.swap ? x : gy;
+        const int rowld = p.swap ? ldgy : ldx, colld = p.swap ? ldx : ldgy;
+        CUtensorMap mx, mg;
+        {
+            const uint64_t dims[4] = {(uint64_t)a.ci, (uint64_t)v.nx, (uint64_t)v.ny, (uint64_t)v.nz};
+            const uint64_t strides[3] = {(uint64_t)rowld * 2, (uint64_t)v.nx * rowld * 2,
+                                         (uint64_t)v.nx * v.ny * rowld * 2};
+            const uint32_t box[4] = {(uint32_t)a.colA, (uint32_t)p.bw, (uint32_t)p.bh, (uint32_t)p.bd};
+            RSV_TRY(make_map(&mx, rowp, 4, dims, strides, box, a.colA * 2));
+        }
+        {
+            const uint64_t dims[4] = {(uint64_t)a.co, (uint64_t)v.nx, (uint64_t)v.ny, (uint64_t)v.nz};
+            const uint64_t strides[3] = {(uint64_t)colld * 2, (uint64_t)v.nx * colld * 2,
+                                         (uint64_t)v.nx * v.ny * colld * 2};
+            const uint32_t box[4] = {(uint32_t)a.colB, (uint32_t)p.bw, (uint32_t)p.bh, (uint32_t)p.bd};
+            RSV_TRY(make_map(&mg, colp, 4, dims, strides, box, a.colB * 2));
+        }
+        RSV_CUDA_TRY(launch_wgmn(p.bn, st, dim3(p.mtiles, p.ntiles, p.splits), mx, mg, a));
+        const int64_t total = (int64_t)taps * ci * co;
+        wgrad_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(part, p.splits, taps, ci, co,
+                                                                                       gw, p.swap ? 1 : 0);
+        RSV_CUDA_TRY(cudaGetLastError());
+        int n = 2;
+        if (gb) {
+            const int64_t V = (int64_t)v.nx * v.ny * v.nz;
+            bias_grad_cl<<<kBiasBlocks, 256, 0, st>>>(gy, ldgy, co, V, bpart);
+            bias_grad_cl_final<<<(co + 127) / 128, 128, 0, st>>>(bpart, kBiasBlocks, co, gb);
+            RSV_CUDA_TRY(cudaGetLastError());
+            n = 4;
+        }
+        count_launches(n);
+        return RSV_OK;
+    }
     __nv_bfloat16 *xt = (__nv_bfloat16 *)scratch;
     __nv_bfloat16 *gyt = (__nv_bfloat16 *)((char *)scratch + p.xt_bytes);
     float *part = (float *)((char *)scratch + p.xt_bytes + p.gyt_bytes);
-    if (!aligned16(scratch)) return RSV_EINVAL;
     const int prow = (v.nz + 2) * (v.ny + 2), xchunks = (v.nx + kVmChunk - 1) / kVmChunk;
     to_voxel_major<<<dim3(prow, ci / 32, xchunks), 256, 0, st>>>(x, ldx, ci, v.nx, v.ny, v.nz, p.nshift, p.vpad, xt);
     RSV_CUDA_TRY(cudaGetLastError());
@@ -702,7 +1003,8 @@ rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, cons
     a.timeout_ns = timeout_ns;
     RSV_CUDA_TRY(launch_wg(p.bn, st, dim3(p.mtiles, p.ntiles, p.splits), ma, mb, a));
     const int64_t total = (int64_t)taps * ci * co;
-    wgrad_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(part, p.splits, taps, ci, co, gw);
+    wgrad_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(part, p.splits, taps, ci, co, gw,
+                                                                                   0);
     RSV_CUDA_TRY(cudaGetLastError());
     int n = 4;
     if (gb) {

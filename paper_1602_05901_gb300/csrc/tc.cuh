@@ -111,10 +111,21 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, int swz) {
            ((uint64_t)(swz == 128 ? 2 : 4) << 61);
 }
 
+// Shared-memory matrix descriptor of an MN-major, swizzled operand tile: each
+// row (one K index) holds 64 (128-byte swizzle) or 32 (64-byte swizzle)
+// consecutive M/N elements; 8 rows form one swizzle atom (grp bytes apart
+// along K: stride offset), and atoms along M/N sit col bytes apart (leading
+// offset).
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t saddr, int swz, uint32_t col, uint32_t grp) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((col >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((grp >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(swz == 128 ? 2 : 4) << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
-// both operands K-major, shape M x N (M = 128).
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// shape M x N; operands K-major unless a_mn / b_mn (bits 15 and 16).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn = false, bool b_mn = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T for one K = 16 slice.

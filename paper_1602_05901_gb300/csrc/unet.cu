@@ -220,35 +220,72 @@ __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16 *__restrict_
 }
 
 // Loss and the head's gradients.  d = out - target / s; loss = mean d^2;
-// gout = 2 d / V; G[v][c] = bf16(gout wh[c] (top > 0)); partial sums of
-// gout * top[v][c] (c < C), of gout (slot C) and of d^2 (slot C + 1) per block.
-__global__ void __launch_bounds__(128) head_bwd(const __nv_bfloat16 *__restrict__ top, int C, int64_t V,
+// gout = 2 d / V; G[v][c] = bf16(gout wh[c] (top > 0)).  Each CTA owns a
+// contiguous chunk of voxels and each warp 32 consecutive voxels at a time:
+// lane l first forms d and gout of voxel l (the FP64 part, once per voxel),
+// then the warp walks the 32 voxels with lane l on channels l, l + 32, ...
+// (C <= 128), so each voxel's row is read and written coalesced.  Per-CTA
+// sums of gout * top[v][c] (c < C), of gout (slot C) and of d^2 (slot C + 1)
+// go to part[blockIdx.x][C + 2], warps added in order; head_final adds the
+// CTAs in order.
+__global__ void __launch_bounds__(256) head_bwd(const __nv_bfloat16 *__restrict__ top, int C, int64_t V,
                                                 const float *__restrict__ wh, const float *__restrict__ out,
                                                 const double *__restrict__ tgt, const double *__restrict__ stats,
                                                 __nv_bfloat16 *__restrict__ G, double *__restrict__ part) {
-    extern __shared__ double red[];  // [128][C + 2]
-    const int S = C + 2;
-    for (int k = 0; k < S; ++k) red[threadIdx.x * S + k] = 0.0;
+    __shared__ double red[8][130];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t len = (V + gridDim.x - 1) / gridDim.x;
+    const int64_t v0 = blockIdx.x * len, v1 = min(V, v0 + len);
     const double s = stats[3];
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-        const double t = s > 0.0 ? tgt[v] / s : 0.0;
-        const double d = (double)out[v] - t;
-        const float g = (float)(2.0 * d / (double)V);
-        for (int c = 0; c < C; ++c) {
-            const float a = bfv(top[v * C + c]);
-            G[v * C + c] = tobf(a > 0.0f ? g * wh[c] : 0.0f);
-            red[threadIdx.x * S + c] += (double)g * a;
+    const double inv_s = s > 0.0 ? 1.0 / s : 0.0, two_over_v = 2.0 / (double)V;
+    float w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = lane + 32 * q < C ? wh[lane + 32 * q] : 0.0f;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    double gsum = 0.0, dsum = 0.0;
+    for (int64_t b = v0 + 32 * warp; b < v1; b += 256) {
+        const int64_t vl = b + lane;
+        float g = 0.0f;
+        if (vl < v1) {
+            const double d = (double)out[vl] - tgt[vl] * inv_s;
+            g = (float)(d * two_over_v);
+            gsum += g;
+            dsum += d * d;
         }
-        red[threadIdx.x * S + C] += g;
-        red[threadIdx.x * S + C + 1] += d * d;
+        const int nv = v1 - b < 32 ? (int)(v1 - b) : 32;
+        for (int j = 0; j < nv; ++j) {
+            const float gj = __shfl_sync(0xffffffffu, g, j);
+            const int64_t v = b + j;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = lane + 32 * q;
+                if (c < C) {
+                    const float a = bfv(top[v * C + c]);
+                    G[v * C + c] = tobf(a > 0.0f ? gj * w[q] : 0.0f);
+                    acc[q] = fmaf(gj, a, acc[q]);
+                }
+            }
+        }
+    }
+    // warp sums of the per-voxel scalars, then per-CTA sums over the warps in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gsum += __shfl_down_sync(0xffffffffu, gsum, o);
+        dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (lane + 32 * q < C) red[warp][lane + 32 * q] = acc[q];
+    if (lane == 0) {
+        red[warp][C] = gsum;
+        red[warp][C + 1] = dsum;
     }
     __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < S; ++k) red[threadIdx.x * S + k] += red[(threadIdx.x + w) * S + k];
-        __syncthreads();
+    if (threadIdx.x < C + 2) {
+        double t = 0.0;
+        for (int wv = 0; wv < 8; ++wv) t += red[wv][threadIdx.x];
+        part[(int64_t)blockIdx.x * (C + 2) + threadIdx.x] = t;
     }
-    if (threadIdx.x < S) part[(int64_t)blockIdx.x * S + threadIdx.x] = red[threadIdx.x];
 }
 
 // Head gradients into the flat gradient array, and the loss: grad[gw + c], grad[gw + C], loss.
@@ -436,8 +473,6 @@ rsv_status unet_alloc(rsv_unet *u) {
     RSV_TRY(u->alloc(&u->loss, 1));
     RSV_TRY(u->alloc(&u->err, 1));
     RSV_CUDA_TRY(cudaMemsetAsync(u->err, 0, sizeof(int), u->st));
-    RSV_CUDA_TRY(cudaFuncSetAttribute(head_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(128 * (u->ch[0] + 2) * sizeof(double))));
     return RSV_OK;
 }
 
@@ -513,8 +548,7 @@ rsv_status backward(rsv_unet *u, const double *target) {
     const int64_t V0 = u->V[0];
     const int C0 = u->ch[0];
     const Layer &hd = u->layers[u->head()];
-    head_bwd<<<kRedBlk, 128, 128 * (C0 + 2) * sizeof(double), st>>>(u->top(), C0, V0, u->p + hd.woff, u->out, target,
-                                                                     u->stats, u->gB[0], u->part);
+    head_bwd<<<kRedBlk, 256, 0, st>>>(u->top(), C0, V0, u->p + hd.woff, u->out, target, u->stats, u->gB[0], u->part);
     head_final<<<1, (C0 + 2 + 31) / 32 * 32, 0, st>>>(u->part, kRedBlk, C0, V0, u->g + hd.woff, u->loss);
     RSV_CUDA_TRY(cudaGetLastError());
     count_launches(2);

@@ -113,7 +113,10 @@ WG_CASES = [
     (8, 8, 4, 27, 96, 32),
     (16, 4, 4, 1, 64, 32),
     (16, 16, 8, 27, 128, 256),
-    (24, 5, 3, 27, 64, 96),
+    (24, 5, 3, 27, 64, 96),      # no 64-voxel box fits: the voxel-major copy path
+    (16, 8, 8, 27, 192, 64),     # ci > co: rows = (tap, output channel), N = 192
+    (16, 8, 4, 27, 384, 128),    # ci > co: two N tiles of 192
+    (32, 4, 3, 27, 96, 32),      # ci > co with ragged z chunks
 ]
 
 
