@@ -419,10 +419,12 @@ struct WgMnArgs {
     uint64_t timeout_ns;
 };
 
+// Pipeline depth per N tile: the deepest ring that still lets two CTAs share an SM.
 template <int BN>
 struct WgMnSmem {
     static constexpr uint32_t A = 128 * 64 * 2, B = BN * 64 * 2, STAGE = A + B;
-    static constexpr uint32_t BARS = kStages * STAGE;
+    static constexpr int S = STAGE * 4 <= 100 * 1024 ? 4 : STAGE * 3 <= 100 * 1024 ? 3 : 2;
+    static constexpr uint32_t BARS = S * STAGE;
     static constexpr uint32_t BYTES = BARS + 256 + 1024;
 };
 
@@ -435,8 +437,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     uint64_t *full = (uint64_t *)(sm + L::BARS);
-    uint64_t *empty = full + kStages;
-    uint64_t *done = empty + kStages;
+    uint64_t *empty = full + L::S;
+    uint64_t *done = empty + L::S;
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     int *flags = (int *)(tmem_slot + 1);
 
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t deadline = now_ns() + a.timeout_ns;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < L::S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -473,8 +475,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t bytes = (uint32_t)(ntap * colsPerTap) * 64 * rowA + (uint32_t)colsB * 64 * rowB;
         int kk = 0;
         for (; kk < nk; ++kk) {
-            const int s = kk % kStages;
-            if (kk >= kStages && !mbar_wait(&empty[s], ((kk / kStages) + 1) & 1, deadline)) {
+            const int s = kk % L::S;
+            if (kk >= L::S && !mbar_wait(&empty[s], ((kk / L::S) + 1) & 1, deadline)) {
                 flags[0] = 1;
                 break;
             }
@@ -505,8 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         (void)colsA;
         int kk = 0;
         for (; kk < nk; ++kk) {
-            const int s = kk % kStages;
-            if (!mbar_wait(&full[s], (kk / kStages) & 1, deadline)) {
+            const int s = kk % L::S;
+            if (!mbar_wait(&full[s], (kk / L::S) & 1, deadline)) {
                 flags[0] = 1;
                 break;
             }
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && (flags[0] || !ok)) {
         raise(a.err, RSV_ETIMEOUT);
         for (int kk = flags[2]; kk < flags[1]; ++kk)
-            mbar_wait(&full[kk % kStages], (kk / kStages) & 1, now_ns() + a.timeout_ns);
+            mbar_wait(&full[kk % L::S], (kk / L::S) & 1, now_ns() + a.timeout_ns);
     }
     __syncthreads();
     if (warp == 2) tmem_dealloc(tmem, TCOLS);
@@ -590,12 +592,15 @@ __global__ void __launch_bounds__(256) bias_grad_cl(const __nv_bfloat16 *__restr
         part[(int64_t)blockIdx.x * co + c] = t;
     }
 }
+// One warp per channel: lane l adds the blocks l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void bias_grad_cl_final(const float *__restrict__ part, int nblk, int co, float *__restrict__ gb) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= co) return;
     float t = 0.0f;
-    for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * co + c];
-    gb[c] = t;
+    for (int b = lane; b < nblk; b += 32) t += part[(int64_t)b * co + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) gb[c] = t;
 }
 
 // ------------------------------------------------------------------ helper kernels
@@ -790,7 +795,7 @@ struct WgPlan {
     int bw, bh, bd, kcx, kcy;
 };
 
-constexpr int kBiasBlocks = 1024;
+constexpr int kBiasBlocks = 512;
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -818,7 +823,9 @@ WgPlan wg_plan(ConvVol v, int taps, int ci, int co) {
     p.bn = pick_bn(rb);
     p.ntiles = p.bn ? rb / p.bn : 0;
     const int ctas = std::max(1, p.mtiles * p.ntiles);
-    int splits = std::max(1, std::min(p.nchunks, (2 * 152 + ctas - 1) / ctas));
+    // two resident CTAs per SM: split the voxels so that the grid is at most one wave of 2 x 152
+    // (a second, nearly empty wave would double the time)
+    int splits = std::max(1, std::min(p.nchunks, (2 * 152) / ctas));
     p.cps = (p.nchunks + splits - 1) / splits;
     p.splits = (p.nchunks + p.cps - 1) / p.cps;
     p.nshift = taps == 27 ? 3 : 1;
@@ -959,7 +966,7 @@ rsv_status conv_wgrad(cudaStream_t st, ConvVol v, int taps, int ci, int co, cons
         if (gb) {
             const int64_t V = (int64_t)v.nx * v.ny * v.nz;
             bias_grad_cl<<<kBiasBlocks, 256, 0, st>>>(gy, ldgy, co, V, bpart);
-            bias_grad_cl_final<<<(co + 127) / 128, 128, 0, st>>>(bpart, kBiasBlocks, co, gb);
+            bias_grad_cl_final<<<(co + 7) / 8, 256, 0, st>>>(bpart, kBiasBlocks, co, gb);
             RSV_CUDA_TRY(cudaGetLastError());
             n = 4;
         }
