@@ -782,8 +782,12 @@ int or_refine(or_system *outer, or_system *inner, const double *b, double *x, in
         ++outer_steps;
         memset(d, 0, sizeof(double) * n);
         double ist[4] = {0, 0, 0, 0};
-        int is = (solver == 0) ? or_gmres(inner, r, d, m, inner_rtol, maxit - inner_total, 0, ist)
-                               : or_bicgstab(inner, r, d, inner_rtol, 1e-30, maxit - inner_total, ist);
+        /* inner tolerance relative to ||r||: inner_rtol, or less strict on the last step,
+           which only needs to bring ||r|| below rtol ||b|| (with a factor 2 of margin) */
+        double itol = 0.5 * rtol * bnorm / rn;
+        if (itol < inner_rtol) itol = inner_rtol;
+        int is = (solver == 0) ? or_gmres(inner, r, d, m, itol, maxit - inner_total, 0, ist)
+                               : or_bicgstab(inner, r, d, itol, 1e-30, maxit - inner_total, ist);
         inner_total += (int)ist[0];
         if (is != OR_OK && is != OR_ENOCONV) { st = is; break; }
         axpby(n, 1.0, d, 1.0, x);

@@ -275,14 +275,23 @@ __global__ void b_update_xr(int64_t n, BatchDev d, const int32_t *__restrict__ s
 
 // Start of an inner solve: per-system tolerance and scalars; systems marked
 // finished by the outer loop stay frozen.
-__global__ void b_init(BatchDev d, int nsys, double rtol_or_inner, int mixed) {
+__global__ void b_init(BatchDev d, int nsys, double rtol_or_inner, int mixed, double rtol) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     d.rho[s] = d.alpha[s] = d.omega[s] = 1.0;
     d.half[s] = 0;
     d.rhn[s] = d.red[6 * nsys + s];
-    // FP64 mode: tol = rtol ||b||; mixed: the inner right-hand side has unit norm
-    d.tol[s] = mixed ? rtol_or_inner : rtol_or_inner * d.bnorm[s];
+    // FP64 mode: tol = rtol ||b||.  Mixed: the inner right-hand side has unit norm; the
+    // inner tolerance is inner_rtol, or less strict on the system's last outer step,
+    // which only needs ||r|| below rtol ||b|| (factor 2 of margin).
+    if (mixed) {
+        const double rn = d.red[7 * nsys + s];
+        double t = rtol_or_inner;
+        if (rn > 0.0) t = fmax(t, 0.5 * rtol * d.bnorm[s] / rn);
+        d.tol[s] = t;
+    } else {
+        d.tol[s] = rtol_or_inner * d.bnorm[s];
+    }
     d.done[s] = d.outer[s];
     d.best[s] = d.red[6 * nsys + s];
     d.stall[s] = 0;
@@ -418,7 +427,7 @@ rsv_status bicg_inner(rsv_solver *s, BatchState *B, const T *rhs, T *x, double t
     // ||r|| and <rh, r> of the starting residual (no system is frozen yet for this sweep)
     RSV_CUDA_TRY(seg_dot<T>(s, B, r, r, rh, d.red + 6 * nsys, d.red + 0 * nsys, 1, 0, nullptr));
     count_launches(2);
-    b_init<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, tol_param, mixed);
+    b_init<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, tol_param, mixed, s->p.rtol);
     b_count_done<<<1, 256, 0, s->st>>>(d, nsys);
     RSV_CUDA_TRY(cudaGetLastError());
     const int gi = sizeof(T) == 8 ? 0 : 1;

@@ -402,9 +402,11 @@ rsv_status solve_mixed(rsv_solver *s, const double *b, double *x, double tol, rs
         ++outer;
         RSV_CUDA_TRY(launch_to_f32_scaled(s->st, n, s->r64, &ds->red[13], s->rf));
         RSV_CUDA_TRY(cudaMemsetAsync(s->df, 0, sizeof(float) * n, s->st));
-        rsv_status ist = (s->p.solver == RSV_BICGSTAB) ? bicgstab_run<float>(s, s->rf, s->df, s->p.inner_rtol)
-                                                        : gmres_run<float>(s, s->rf, s->df, s->p.inner_rtol,
-                                                                           &cycles, false);
+        // inner tolerance relative to ||r||: inner_rtol, or less strict on the last step, which
+        // only needs to bring ||r|| below tol (factor 2 of margin)
+        const double itol = std::max(s->p.inner_rtol, 0.5 * tol / rn);
+        rsv_status ist = (s->p.solver == RSV_BICGSTAB) ? bicgstab_run<float>(s, s->rf, s->df, itol)
+                                                        : gmres_run<float>(s, s->rf, s->df, itol, &cycles, false);
         if (ist != RSV_OK && ist != RSV_ENOCONV && ist != RSV_EBREAKDOWN) { result = ist; break; }
         if (ist == RSV_EBREAKDOWN) {
             // a breakdown of the inner solve still leaves a usable correction;
