@@ -42,7 +42,12 @@ namespace rsv {
 namespace {
 
 constexpr int TJ = 8, TK = 4;
-constexpr int NSE = 3;  // edge ring stages: neighbour values are copied NSE - 1 steps ahead
+// Edge ring stages: neighbour values are copied NSE - 1 steps ahead.  Each step of
+// look-ahead is a step of lag per tile hand-off on the sweep's critical path, so
+// the ring is one step deep (measured on 100x100x50: 546 us per FP32 apply with
+// two steps of look-ahead, 480 us with one; plain register loads one step ahead,
+// without TMA, were slower still: 577 us).
+constexpr int NSE = 2;
 
 template <typename T> struct Bits;
 template <> struct Bits<double> {
