@@ -225,17 +225,15 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         }
         const bool edges = pj >= 0 || pk >= 0;
         const unsigned edge_bytes = (pj >= 0 ? St::EJB : 0u) + (pk >= 0 ? St::EKB : 0u);
-        auto issue = [&](int s) {
-            const int st = s % NSD;
+        auto issue_at = [&](int s, int st) {  // step s into data stage st (= s % NSD)
             T *dst = ring + st * St::SIZE;
             mbar_expect(&bars[st], St::FB + St::VB);
             tma_load_1d(dst, Ft + (size_t)s * St::F, St::FB, &bars[st]);
             tma_load_1d(dst + St::F, Vt + (size_t)s * St::V, St::VB, &bars[st]);
             pending |= 1u << st;
         };
-        auto issue_edges = [&](int s) {
+        auto issue_edges_at = [&](int s, int st) {  // step s into edge stage st (= s % NSE)
             if (!edges) return;
-            const int st = s % NSE;
             T *dst = ering + st * St::ESIZE;
             mbar_expect(&ebars[st], edge_bytes);
             if (pj >= 0) tma_load_1d(dst, EJsrc + (size_t)s * St::EJ, St::EJB, &ebars[st]);
@@ -255,20 +253,35 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         };
         if (lane == 0) {
             fence_proxy_async();
-            for (int q = 0; q < NSD - 1 && q < S; ++q) issue(q);
-            for (int q = 0; q < NSE - 1 && q < S; ++q) issue_edges(q);
+            for (int q = 0; q < NSD - 1 && q < S; ++q) issue_at(q, q);
+            for (int q = 0; q < NSE - 1 && q < S; ++q) issue_edges_at(q, q);
         }
         T prev[3] = {T(0), T(0), T(0)};
+        // Per-step state kept incrementally, so that a step holds no division and no 64-bit
+        // index product: the ring stages of this step and of the next copies, the cell index
+        // along x, and the addresses this lane reads or writes.
+        int st = 0, est = 0;
+        int ist = (NSD - 1) % NSD, iest = (NSE - 1) % NSE;
+        int i = FWD ? -off : (nx - 1 + off);
+        T *yout = FWD ? P.Vnext + ((tile0 + (S - 1)) * 32 + lane) * 4 : P.z + 3 * (base + i);
+        const ptrdiff_t ystep = FWD ? -(ptrdiff_t)(32 * 4) : -3;
+        T *pubj = P.EJ + ((ptrdiff_t)tile0 - (TJ - 1)) * St::EJ + b * 4;  // row of step s - (TJ - 1)
+        T *pubk = P.EK + ((ptrdiff_t)tile0 - (TK - 1)) * St::EK + a * 4;
+        const T *pollj = P.EJ + rowj * St::EJ + b * 4;  // the j producer's row of step s
+        const T *pollk = P.EK + rowk * St::EK + a * 4;
 
         for (int s0 = 0; s0 < S; s0 += 4) {
 #pragma unroll 1
             for (int s = s0; s < s0 + 4 && s < S; ++s) {
+                // lane 0 refills the stages the previous step used (every lane finished that
+                // step: __syncwarp at its end)
                 if (lane == 0) {
                     fence_proxy_async();
-                    if (s + NSD - 1 < S) issue(s + NSD - 1);
-                    if (s + NSE - 1 < S) issue_edges(s + NSE - 1);
+                    if (s + NSD - 1 < S) issue_at(s + NSD - 1, ist);
+                    if (s + NSE - 1 < S) issue_edges_at(s + NSE - 1, iest);
                 }
-                const int i = FWD ? (s - off) : (nx - 1 - (s - off));
+                ist = ist + 1 == NSD ? 0 : ist + 1;
+                iest = iest + 1 == NSE ? 0 : iest + 1;
                 const bool valid = jk_ok && i >= 0 && i < nx;
                 const bool has_i = FWD ? (i > 0) : (i < nx - 1);
                 // in-tile neighbours: previous step's results of the adjacent lanes
@@ -282,14 +295,16 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     own[e] = has_i ? prev[e] : T(0);
                 }
                 // wait for this step's stages
-                wait_stage(&bars[s % NSD], s % NSD);
-                if (edges) wait_stage(&ebars[s % NSE], NSD + s % NSE);
-                const T *stg = ring + (s % NSD) * St::SIZE;
-                const T *estg = ering + (s % NSE) * St::ESIZE;
+                wait_stage(&bars[st], st);
+                if (edges) wait_stage(&ebars[est], NSD + est);
+                const T *stg = ring + st * St::SIZE;
+                const T *estg = ering + est * St::ESIZE;
+                st = st + 1 == NSD ? 0 : st + 1;
+                est = est + 1 == NSE ? 0 : est + 1;
                 if (valid && edge_j && has_j) {
                     const T *e4 = estg + b * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(P.EJ + (rowj + s) * St::EJ + b * 4, v3, deadline)) failed = true;
+                    if (!poll3(pollj, v3, deadline)) failed = true;
                     nj[0] = v3[0];
                     nj[1] = v3[1];
                     nj[2] = v3[2];
@@ -297,11 +312,13 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                 if (valid && edge_k && has_k) {
                     const T *e4 = estg + St::EJ + a * 4;
                     T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(P.EK + (rowk + s) * St::EK + a * 4, v3, deadline)) failed = true;
+                    if (!poll3(pollk, v3, deadline)) failed = true;
                     nk[0] = v3[0];
                     nk[1] = v3[1];
                     nk[2] = v3[2];
                 }
+                pollj += St::EJ;
+                pollk += St::EK;
                 // factor row and input of this lane
                 T f[NQP];
                 {
@@ -356,31 +373,24 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     res[e] = FWD ? d : (vin[e] - d);
                 }
                 if (valid) {
-                    if (FWD) {
-                        T *o = P.Vnext + ((tile0 + (S - 1 - s)) * 32 + lane) * 4;
-                        o[0] = res[0];
-                        o[1] = res[1];
-                        o[2] = res[2];
-                    } else {
-                        T *o = P.z + 3 * (base + i);
-                        o[0] = res[0];
-                        o[1] = res[1];
-                        o[2] = res[2];
+                    yout[0] = res[0];
+                    yout[1] = res[1];
+                    yout[2] = res[2];
+                    if (pub_j && s >= TJ - 1) {
+                        st_relaxed(pubj, res[0]);
+                        st_relaxed(pubj + 1, res[1]);
+                        st_relaxed(pubj + 2, res[2]);
                     }
-                    const int sj = s - (TJ - 1), sk = s - (TK - 1);
-                    if (pub_j && sj >= 0) {
-                        T *o = P.EJ + ((tile0 + sj) * TK + b) * 4;
-                        st_relaxed(o, res[0]);
-                        st_relaxed(o + 1, res[1]);
-                        st_relaxed(o + 2, res[2]);
-                    }
-                    if (pub_k && sk >= 0) {
-                        T *o = P.EK + ((tile0 + sk) * TJ + a) * 4;
-                        st_relaxed(o, res[0]);
-                        st_relaxed(o + 1, res[1]);
-                        st_relaxed(o + 2, res[2]);
+                    if (pub_k && s >= TK - 1) {
+                        st_relaxed(pubk, res[0]);
+                        st_relaxed(pubk + 1, res[1]);
+                        st_relaxed(pubk + 2, res[2]);
                     }
                 }
+                yout += ystep;
+                pubj += St::EJ;
+                pubk += St::EK;
+                i += FWD ? 1 : -1;
 #pragma unroll
                 for (int e = 0; e < 3; ++e) prev[e] = valid ? res[e] : T(0);
                 __syncwarp();
