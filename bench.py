@@ -139,6 +139,17 @@ def dist_init():
     return rank, ws, local, dist
 
 
+def max_over_ranks(ms, dist, dev=None):
+    """The slowest rank's time (every rank gets it), then a barrier; ms itself when single-process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def cpu_baseline(p, gpu_iters, sample_iters, solver="gmres", pc="bilu0"):
     """Time the oracle (as it stands, one thread) on the first `sample_iters` Krylov
     iterations of the workload and scale its solve time to `gpu_iters` iterations."""
@@ -541,12 +552,7 @@ def main():
         infos = [step(solver) for _ in range(steps)]
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms_ = e0.elapsed_time(e1) / steps
-        if dist is not None:
-            t = torch.tensor([ms_], dtype=torch.float64, device=dev if dist.get_backend() == "nccl" else "cpu")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
-            dist.barrier()
+        ms_ = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
         return ms_, infos[-1], rsv.rsv_kernel_launches() - l0
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
