@@ -47,6 +47,29 @@ __device__ __forceinline__ void block_partial(double v, double *sm, double *part
     __syncthreads();
 }
 
+// Block-reduce kg values per thread at once into partial[(slot0 + i) * grid + block]:
+// warp sums by shuffles, one shared-memory exchange and one barrier pair for
+// the whole group; thread i < kg adds the warps' sums in warp order (fixed
+// order: deterministic).
+template <int G>
+__device__ __forceinline__ void block_partial_group(const double (&v)[G], int kg, double (*sm)[kRedThreads / 32],
+                                                    double *partial, int slot0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+        if (i < kg) {
+            const double t = warp_sum(v[i]);
+            if (lane == 0) sm[i][warp] = t;
+        }
+    __syncthreads();
+    if (threadIdx.x < kg) {
+        double s = 0.0;
+        for (int q = 0; q < kRedThreads / 32; ++q) s += sm[threadIdx.x][q];
+        partial[(int64_t)(slot0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // out[i] = <w, V_i> for i < k; if self_nrm, also out[k] = <w, w> and *self_nrm = ||w||.
 // Final reduction in the last CTA: warp w sums the gridDim.x partials of
 // outputs w, w + 8, ...; each lane adds a fixed strided subset, then a
@@ -65,6 +88,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
     if (is_done(done) || is_done(skip)) return;
     using VT = Vec<T>;
     __shared__ double sm[kRedThreads / 32];
+    __shared__ double smg[kGroup][kRedThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (self_nrm) {
@@ -114,9 +138,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
                     if (i < kg) acc[i].add(wr, V[(int64_t)(g0 + i) * ldv + r]);
             }
         }
+        double vals[kGroup];
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < kg) block_partial(acc[i].value(), sm, partial, g0 + i);
+        for (int i = 0; i < kGroup; ++i) vals[i] = i < kg ? acc[i].value() : 0.0;
+        block_partial_group<kGroup>(vals, kg, smg, partial, g0);
     }
     if (last_cta(counter)) {
         const int kk = self_nrm ? k + 1 : k;
