@@ -57,23 +57,23 @@ struct DevState {
 };
 
 struct TileSys {  // one grid of the tile sweeps
-    int nx, ny, nz, nTJ, nTK, S, poff, pad;  // S: steps per tile; poff: first position of the grid
+    int nx, ny, nz, nTJ, nTK, S, poff, Sp;  // S: steps per tile (Sp: padded to the step group); poff: first position
     int64_t cell0;
 };
 
 struct IluTiles {  // packed factor and buffers of the persistent tile sweeps (ilu_tiles.cu)
     int nT = 0, maxS = 0, grid = 0, elem = 0;  // elem: 8 (FP64) or 4 (FP32)
-    int64_t rows = 0;         // step rows of all tiles
+    int64_t rows = 0;         // step rows of all tiles (maxS, rows: padded step counts)
     size_t smem = 0;
     TileSys *tsys = nullptr;  // per grid
     int *tile_sys = nullptr;  // position -> grid
     int64_t *tile_row0 = nullptr;  // position -> first step row
     int2 *order = nullptr;    // tile (J, K) per processing position
     int *pos_of = nullptr;    // grid poff + J * nTK + K -> position
-    void *Ff = nullptr;       // forward factor rows  [nT][S][32][NQP]
-    void *Fb = nullptr;       // backward factor rows [nT][S][32][NQP]
-    void *Vf = nullptr;       // forward input in tile order [nT][S][32][4]
-    void *Vb = nullptr;       // backward input (y) in tile order [nT][S][32][4]
+    void *Ff = nullptr;       // forward factor rows  [nT][Sp][32][NQP]
+    void *Fb = nullptr;       // backward factor rows [nT][Sp][32][NQP]
+    void *Vf = nullptr;       // forward input in tile order [nT][Sp][32][4]
+    void *Vb = nullptr;       // backward input (y) in tile order [nT][Sp][32][4]
     void *EJf = nullptr, *EKf = nullptr;  // forward edge hand-off buffers
     void *EJb = nullptr, *EKb = nullptr;  // backward edge hand-off buffers
 };

@@ -11,18 +11,26 @@
 // previous result.
 //
 // Everything else a step needs arrives through shared-memory rings filled by
-// TMA bulk copies (cp.async.bulk + mbarrier): a deep data ring (NSD - 1 steps
-// ahead, hiding HBM latency) and a shallow edge ring (NSE - 1 steps ahead):
+// TMA bulk copies (cp.async.bulk + mbarrier):
 //   * the factor row of each lane (three off-diagonal blocks and D^{-1}, 36
-//     values, packed at setup in exactly the order the warp reads them);
-//   * the input vector, gathered into the same tile order before the sweep;
-//   * the values of neighbouring tiles' edge cells.  A tile publishes the
-//     results of its last j-row and last k-layer into small per-tile edge
-//     buffers indexed by the step at which the neighbour will need them.  The
-//     buffers hold a signalling-NaN sentinel until written (arithmetic never
-//     produces one), so a consumer that finds the sentinel in its staged copy
-//     re-reads the value from global memory until it appears (bounded by a
-//     time limit that ends the sweep with RSV_ETIMEOUT).
+//     values, packed at setup in exactly the order the warp reads them) and
+//     the input vector, gathered into the same tile order before the sweep.
+//     These come in groups of GS steps (one mbarrier, two copies per group)
+//     through a ring of NG groups, so a copy is issued NG - 1 groups ahead;
+//   * the values of neighbouring tiles' edge cells, ELA steps ahead.  A tile
+//     publishes the results of its last j-row and last k-layer into small
+//     per-tile edge buffers indexed by the step at which the neighbour will
+//     need them.  The buffers hold a signalling-NaN sentinel until written
+//     (arithmetic never produces one), so a consumer that finds the sentinel
+//     in its staged copy re-reads the value from global memory until it
+//     appears (bounded by a time limit that ends the sweep with
+//     RSV_ETIMEOUT).
+//
+// A step is written for few instructions on its dependency chain: GS steps are
+// unrolled so every ring offset is a constant, the lead lane's edge copies are
+// predicated instead of branched around (a divergent branch cost waiting tiles
+// more than it saved), the sentinel test is one warp vote, and results leave in
+// 16-byte stores.
 //
 // The backward sweep z_c = y_c - D_c^{-1} (A_{c,+x} z_{+x} + A_{c,+y} z_{+y} +
 // A_{c,+z} z_{+z}) is the mirror image (lane (a, b) visits
@@ -42,39 +50,52 @@ namespace rsv {
 namespace {
 
 constexpr int TJ = 8, TK = 4;
-// Edge ring stages: neighbour values are copied NSE - 1 steps ahead.  Each step of
+// Edge ring: NSE stages, neighbour values copied ELA steps ahead.  Each step of
 // look-ahead is a step of lag per tile hand-off on the sweep's critical path, so
-// the ring is one step deep (measured on 100x100x50: 546 us per FP32 apply with
-// two steps of look-ahead, 480 us with one; plain register loads one step ahead,
-// without TMA, were slower still: 577 us).
-constexpr int NSE = 2;
+// the copies run one step ahead (measured on 100x100x50, FP32 apply: 379 us with
+// one step, 406 us with two, 462 us with three; per-lane relaxed register loads
+// instead of TMA: 595 us).  With four stages, the stage a step refills was last
+// read three steps earlier, long after its values were consumed, so the refill
+// needs no proxy fence (a fence there waits for the warp's outstanding stores:
+// 398 us with it).
+constexpr int NSE = 4, ELA = 1;
+// Steps per data group.  A tile's step count is padded to a multiple of GS (the
+// padded steps hold no valid cell), so every group is full and, GS being a
+// multiple of NSE, every edge stage is a constant of the unrolled step.
+constexpr int GS = 4;
+static_assert(GS % NSE == 0 && ELA >= 1 && ELA < NSE, "edge stages are fixed per unrolled step");
 
 template <typename T> struct Bits;
 template <> struct Bits<double> {
     using U = unsigned long long;
     static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;  // signalling NaN
     static constexpr int NQP = 38;                    // padded factor row: conflict-free 16-byte reads
-    static constexpr int NSD = 6;                     // data ring stages (copies NSD - 1 steps ahead)
+    static constexpr int NG = 2;                      // data ring groups (copies one group ahead)
 };
 template <> struct Bits<float> {
     using U = unsigned int;
     static constexpr U SENT = 0x7FA5C0DEu;
     static constexpr int NQP = 36;
-    static constexpr int NSD = 10;
+    static constexpr int NG = 3;
 };
 
-// Data ring stage: factor [32][NQP] | vector [32][4].  Edge ring stage: edge j [4][4] | edge k [8][4].
-// The data ring runs deep (hides HBM latency); the edge ring runs shallow, so that
-// neighbour values are copied as late as possible and are mostly already published.
+// Data stage of one step: factor [32][NQP] and vector [32][4]; a data group holds
+// the factor of its GS steps, then their vectors (two contiguous copies).
+// Edge stage: edge j [TK][4] | edge k [TJ][4].
 template <typename T> struct Stage {
     static constexpr int F = 32 * Bits<T>::NQP;
     static constexpr int V = 32 * 4;
     static constexpr int EJ = TK * 4;
     static constexpr int EK = TJ * 4;
-    static constexpr int SIZE = F + V;
+    static constexpr int GSIZE = GS * (F + V);
     static constexpr int ESIZE = EJ + EK;
     static constexpr unsigned FB = F * sizeof(T), VB = V * sizeof(T), EJB = EJ * sizeof(T), EKB = EK * sizeof(T);
 };
+
+template <typename T> constexpr size_t sweep_smem() {
+    return (size_t)(Bits<T>::NG * Stage<T>::GSIZE + NSE * Stage<T>::ESIZE) * sizeof(T) +
+           (Bits<T>::NG + NSE) * sizeof(uint64_t);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -90,6 +111,22 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Edge rows of one step into an edge stage, by the lanes whose `go` is set (the
+// lead lane): the byte count, then the j row and/or the k row.  Predicated, so
+// the warp takes no branch around it.
+__device__ __forceinline__ void edge_issue(unsigned go, unsigned goj, unsigned gok, uint64_t *bar, unsigned bytes,
+                                           void *dj, const void *sj, unsigned bj, void *dk, const void *sk,
+                                           unsigned bk) {
+    asm volatile(
+        "{\n .reg .pred p, pj, pk;\n"
+        " setp.ne.u32 p, %0, 0;\n setp.ne.u32 pj, %1, 0;\n setp.ne.u32 pk, %2, 0;\n"
+        " @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%3], %4;\n"
+        " @pj cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%5], [%6], %7, [%3];\n"
+        " @pk cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%8], [%9], %10, [%3];\n}" ::"r"(go),
+        "r"(goj), "r"(gok), "r"(smem_u32(bar)), "r"(bytes), "r"(smem_u32(dj)), "l"(sj), "r"(bj), "r"(smem_u32(dk)),
+        "l"(sk), "r"(bk)
         : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
@@ -117,16 +154,44 @@ __device__ __forceinline__ unsigned ld_relaxed(const float *p) {
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_relaxed(double *p, double v) {
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v)) : "memory");
+// A cell's three results (and a zero pad) as one 16-byte edge-buffer entry.
+__device__ __forceinline__ void st_relaxed3(float *p, const float v[3]) {
+    asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(0.f)
+                 : "memory");
 }
-__device__ __forceinline__ void st_relaxed(float *p, float v) {
-    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
+__device__ __forceinline__ void st_relaxed3(double *p, const double v[3]) {
+    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v[0]), "d"(v[1]) : "memory");
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p + 2), "l"(__double_as_longlong(v[2])) : "memory");
 }
 __device__ __forceinline__ unsigned long long bits_of(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ unsigned bits_of(float v) { return __float_as_uint(v); }
 __device__ __forceinline__ double value_of(unsigned long long v) { return __longlong_as_double((long long)v); }
 __device__ __forceinline__ float value_of(unsigned v) { return __uint_as_float(v); }
+template <typename T> __device__ __forceinline__ bool is_sent3(const T v[3]) {
+    return bits_of(v[0]) == Bits<T>::SENT || bits_of(v[1]) == Bits<T>::SENT || bits_of(v[2]) == Bits<T>::SENT;
+}
+// Three values of a 16-byte-aligned shared-memory entry.
+__device__ __forceinline__ void lds3(const float *p, float v[3]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+}
+__device__ __forceinline__ void lds3(const double *p, double v[3]) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = p[2];
+}
+// y entry of the backward sweep's tile order (value, value, value, pad).
+__device__ __forceinline__ void st3pad(float *p, const float v[3]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void st3pad(double *p, const double v[3]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], 0.0);
+}
 
 template <typename T>
 struct SweepArgs {
@@ -136,61 +201,58 @@ struct SweepArgs {
     const int64_t *tile_row0;  // position -> first step row of the tile in the packed arrays
     const int2 *order;         // position -> tile (J, K) inside its grid
     const int *pos_of;         // grid's poff + J * nTK + K -> position
-    const T *F;          // factor rows [nT][S][32][NQP]
-    const T *V;          // input vector in tile order [nT][S][32][4]
-    T *Vnext;            // forward: y in backward tile order [nT][S][32][4]; backward: null
+    const T *F;          // factor rows [nT][Sp][32][NQP]
+    const T *V;          // input vector in tile order [nT][Sp][32][4]
+    T *Vnext;            // forward: y in backward tile order [nT][Sp][32][4]; backward: null
     T *z;                // backward: output in natural order; forward: null
-    T *EJ, *EK;          // edge buffers this sweep publishes [nT][S][TK][4], [nT][S][TJ][4]
+    T *EJ, *EK;          // edge buffers this sweep publishes [nT][Sp][TK][4], [nT][Sp][TJ][4]
     T *EJnext, *EKnext;  // forward: the backward sweep's edge buffers (reset to the sentinel)
     const int *done;
     int *status;
     unsigned long long timeout_ns;
 };
 
-// Re-read a staged neighbour value that was still the sentinel.
-template <typename T>
-__device__ __forceinline__ bool poll3(const T *g, T v[3], uint64_t deadline) {
-    using U = typename Bits<T>::U;
-    unsigned spins = 0;
-    for (;;) {
-        U b0 = bits_of(v[0]), b1 = bits_of(v[1]), b2 = bits_of(v[2]);
-        if (b0 != Bits<T>::SENT && b1 != Bits<T>::SENT && b2 != Bits<T>::SENT) return true;
-        b0 = ld_relaxed(g);
-        b1 = ld_relaxed(g + 1);
-        b2 = ld_relaxed(g + 2);
-        v[0] = value_of(b0);
-        v[1] = value_of(b1);
-        v[2] = value_of(b2);
-        if ((++spins & 63u) == 0 && global_timer() > deadline) return false;
-    }
-}
-
 template <typename T, bool FWD>
 __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     using St = Stage<T>;
+    using U = typename Bits<T>::U;
     constexpr int NQP = Bits<T>::NQP;
-    constexpr int NSD = Bits<T>::NSD;
+    constexpr int NG = Bits<T>::NG;
     if (P.done && *(volatile const int *)P.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    T *ring = reinterpret_cast<T *>(smem);                       // NSD data stages
-    T *ering = ring + NSD * St::SIZE;                            // NSE edge stages
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ering + NSE * St::ESIZE);  // NSD data + NSE edge barriers
-    uint64_t *ebars = bars + NSD;
+    T *ring = reinterpret_cast<T *>(smem);                                   // NG data groups
+    T *ering = ring + NG * St::GSIZE;                                        // NSE edge stages
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ering + NSE * St::ESIZE);  // NG data + NSE edge barriers
+    uint64_t *ebars = bars + NG;
     const int lane = threadIdx.x;
     const int a = lane & 7, b = lane >> 3;
-    if (lane == 0) {
-        for (int q = 0; q < NSD + NSE; ++q) mbar_init(&bars[q], 1);
+    const unsigned lead = lane == 0;
+    if (lead) {
+        for (int q = 0; q < NG + NSE; ++q) mbar_init(&bars[q], 1);
         fence_barrier_init();
     }
     __syncwarp();
-    unsigned phase = 0, pending = 0;  // bit q: data stage q; bit NSD + q: edge stage q
+    unsigned phase = 0, pending = 0;  // bit q: data group stage q; bit NG + q: edge stage q
     const uint64_t deadline = global_timer() + P.timeout_ns;
     bool failed = false;
+
+    auto wait_bar = [&](uint64_t *bar, int bit) {
+        unsigned spins = 0;
+        while (!mbar_try_wait(bar, (phase >> bit) & 1u)) {
+            if ((++spins & 1023u) == 0 && global_timer() > deadline) {
+                failed = true;
+                return;
+            }
+        }
+        phase ^= 1u << bit;
+        pending &= ~(1u << bit);
+    };
 
     for (int t = blockIdx.x; t < P.nT && !failed; t += gridDim.x) {
         const int tt = FWD ? t : (P.nT - 1 - t);
         const TileSys G = P.tsys[P.tile_sys[tt]];
-        const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S, nTJ = G.nTJ, nTK = G.nTK;
+        const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S, Sp = G.Sp, nTJ = G.nTJ, nTK = G.nTK;
+        const int ngr = Sp / GS;
         const int2 JK = P.order[tt];
         // producers of this tile's edge inputs (same grid)
         const int pj = FWD ? (JK.x > 0 ? P.pos_of[G.poff + (JK.x - 1) * nTK + JK.y] : -1)
@@ -199,8 +261,9 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                            : (JK.y + 1 < nTK ? P.pos_of[G.poff + JK.x * nTK + JK.y + 1] : -1);
         const int j = JK.x * TJ + a, k = JK.y * TK + b;
         const bool jk_ok = (j < ny) && (k < nz);
-        const bool has_j = FWD ? (j > 0) : (j + 1 < ny);
-        const bool has_k = FWD ? (k > 0) : (k + 1 < nz);
+        // Lanes on the tile's lower j (k) face take that neighbour from the edge stage,
+        // which holds zeros where the tile has no producer; inner lanes take it from the
+        // adjacent lane, whose previous result is zero where it held no cell.
         const bool edge_j = FWD ? (a == 0) : (a == TJ - 1);
         const bool edge_k = FWD ? (b == 0) : (b == TK - 1);
         const bool pub_j = FWD ? (a == TJ - 1) : (a == 0);  // this lane's results feed the next tile in j
@@ -213,116 +276,91 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         const size_t rowj = pj >= 0 ? (size_t)P.tile_row0[pj] : 0, rowk = pk >= 0 ? (size_t)P.tile_row0[pk] : 0;
         const T *Ft = P.F + tile0 * St::F;
         const T *Vt = P.V + tile0 * St::V;
-        const T *EJsrc = pj >= 0 ? P.EJ + rowj * St::EJ : nullptr;
-        const T *EKsrc = pk >= 0 ? P.EK + rowk * St::EK : nullptr;
-        if (FWD) {
-            // this tile's backward-sweep edge buffers start at the sentinel
-            using U = typename Bits<T>::U;
-            U *ej = reinterpret_cast<U *>(P.EJnext + tile0 * St::EJ);
-            U *ek = reinterpret_cast<U *>(P.EKnext + tile0 * St::EK);
-            for (int q = lane; q < S * St::EJ; q += 32) ej[q] = Bits<T>::SENT;
-            for (int q = lane; q < S * St::EK; q += 32) ek[q] = Bits<T>::SENT;
-        }
         const bool edges = pj >= 0 || pk >= 0;
         const unsigned edge_bytes = (pj >= 0 ? St::EJB : 0u) + (pk >= 0 ? St::EKB : 0u);
-        auto issue_at = [&](int s, int st) {  // step s into data stage st (= s % NSD)
-            T *dst = ring + st * St::SIZE;
-            mbar_expect(&bars[st], St::FB + St::VB);
-            tma_load_1d(dst, Ft + (size_t)s * St::F, St::FB, &bars[st]);
-            tma_load_1d(dst + St::F, Vt + (size_t)s * St::V, St::VB, &bars[st]);
-            pending |= 1u << st;
-        };
-        auto issue_edges_at = [&](int s, int st) {  // step s into edge stage st (= s % NSE)
-            if (!edges) return;
-            T *dst = ering + st * St::ESIZE;
-            mbar_expect(&ebars[st], edge_bytes);
-            if (pj >= 0) tma_load_1d(dst, EJsrc + (size_t)s * St::EJ, St::EJB, &ebars[st]);
-            if (pk >= 0) tma_load_1d(dst + St::EJ, EKsrc + (size_t)s * St::EK, St::EKB, &ebars[st]);
-            pending |= 1u << (NSD + st);
-        };
-        auto wait_stage = [&](uint64_t *bar, int bit) {
-            unsigned spins = 0;
-            while (!mbar_try_wait(bar, (phase >> bit) & 1u)) {
-                if ((++spins & 1023u) == 0 && global_timer() > deadline) {
-                    failed = true;
-                    return;
-                }
-            }
-            phase ^= 1u << bit;
-            pending &= ~(1u << bit);
-        };
-        if (lane == 0) {
+        __syncwarp();  // the previous tile's reads of the rings are done
+        if (FWD) {
+            // this tile's backward-sweep edge buffers start at the sentinel
+            U *ej = reinterpret_cast<U *>(P.EJnext + tile0 * St::EJ);
+            U *ek = reinterpret_cast<U *>(P.EKnext + tile0 * St::EK);
+            for (int q = lane; q < Sp * St::EJ; q += 32) ej[q] = Bits<T>::SENT;
+            for (int q = lane; q < Sp * St::EK; q += 32) ek[q] = Bits<T>::SENT;
+        }
+        // faces without a producer read zeros from the edge stages (no copy writes them)
+        if (pj < 0)
+            for (int q = lane; q < NSE * St::EJ; q += 32) ering[(q / St::EJ) * St::ESIZE + q % St::EJ] = T(0);
+        if (pk < 0)
+            for (int q = lane; q < NSE * St::EK; q += 32) ering[(q / St::EK) * St::ESIZE + St::EJ + q % St::EK] = T(0);
+        __syncwarp();
+        if (lead) {
             fence_proxy_async();
-            for (int q = 0; q < NSD - 1 && q < S; ++q) issue_at(q, q);
-            for (int q = 0; q < NSE - 1 && q < S; ++q) issue_edges_at(q, q);
+            for (int q = 0; q < NG - 1 && q < ngr; ++q) {
+                T *dst = ring + q * St::GSIZE;
+                mbar_expect(&bars[q], GS * (St::FB + St::VB));
+                tma_load_1d(dst, Ft + (size_t)q * GS * St::F, GS * St::FB, &bars[q]);
+                tma_load_1d(dst + GS * St::F, Vt + (size_t)q * GS * St::V, GS * St::VB, &bars[q]);
+                pending |= 1u << q;
+            }
+            if (edges)
+                for (int q = 0; q < ELA && q < Sp; ++q) {
+                    T *dst = ering + q * St::ESIZE;
+                    mbar_expect(&ebars[q], edge_bytes);
+                    if (pj >= 0) tma_load_1d(dst, P.EJ + (rowj + q) * St::EJ, St::EJB, &ebars[q]);
+                    if (pk >= 0) tma_load_1d(dst + St::EJ, P.EK + (rowk + q) * St::EK, St::EKB, &ebars[q]);
+                    pending |= 1u << (NG + q);
+                }
         }
         T prev[3] = {T(0), T(0), T(0)};
-        // Per-step state kept incrementally, so that a step holds no division and no 64-bit
-        // index product: the ring stages of this step and of the next copies, the cell index
-        // along x, and the addresses this lane reads or writes.
-        int st = 0, est = 0;
-        int ist = (NSD - 1) % NSD, iest = (NSE - 1) % NSE;
-        int i = FWD ? -off : (nx - 1 + off);
+        int i = FWD ? -off : (nx - 1 + off);  // this lane's cell along x at the current step
+        // Per-group running addresses; a step adds a constant offset to each.
         T *yout = FWD ? P.Vnext + ((tile0 + (S - 1)) * 32 + lane) * 4 : P.z + 3 * (base + i);
-        const ptrdiff_t ystep = FWD ? -(ptrdiff_t)(32 * 4) : -3;
+        constexpr ptrdiff_t ystep = FWD ? -(ptrdiff_t)(32 * 4) : -3;
         T *pubj = P.EJ + ((ptrdiff_t)tile0 - (TJ - 1)) * St::EJ + b * 4;  // row of step s - (TJ - 1)
         T *pubk = P.EK + ((ptrdiff_t)tile0 - (TK - 1)) * St::EK + a * 4;
         const T *pollj = P.EJ + rowj * St::EJ + b * 4;  // the j producer's row of step s
         const T *pollk = P.EK + rowk * St::EK + a * 4;
+        const T *ejsrc = P.EJ + (rowj + ELA) * St::EJ;  // edge rows of step s + ELA
+        const T *eksrc = P.EK + (rowk + ELA) * St::EK;
+        const unsigned goj = lead && pj >= 0, gok = lead && pk >= 0, go = goj | gok;
+        int gst = 0;  // data group stage of the current group
 
-        for (int s0 = 0; s0 < S; s0 += 4) {
-#pragma unroll 1
-            for (int s = s0; s < s0 + 4 && s < S; ++s) {
-                // lane 0 refills the stages the previous step used (every lane finished that
-                // step: __syncwarp at its end)
-                if (lane == 0) {
-                    fence_proxy_async();
-                    if (s + NSD - 1 < S) issue_at(s + NSD - 1, ist);
-                    if (s + NSE - 1 < S) issue_edges_at(s + NSE - 1, iest);
-                }
-                ist = ist + 1 == NSD ? 0 : ist + 1;
-                iest = iest + 1 == NSE ? 0 : iest + 1;
-                const bool valid = jk_ok && i >= 0 && i < nx;
-                const bool has_i = FWD ? (i > 0) : (i < nx - 1);
+        for (int g = 0; g < ngr; ++g) {
+            // refill the stage the previous group used (every lane is past it) with group g + NG - 1
+            __syncwarp();
+            if (lead && g + NG - 1 < ngr) {
+                const int q = gst == 0 ? NG - 1 : gst - 1;
+                T *dst = ring + q * St::GSIZE;
+                fence_proxy_async();
+                mbar_expect(&bars[q], GS * (St::FB + St::VB));
+                tma_load_1d(dst, Ft + (size_t)(g + NG - 1) * GS * St::F, GS * St::FB, &bars[q]);
+                tma_load_1d(dst + GS * St::F, Vt + (size_t)(g + NG - 1) * GS * St::V, GS * St::VB, &bars[q]);
+                pending |= 1u << q;
+            }
+            wait_bar(&bars[gst], gst);
+            const T *grp = ring + gst * St::GSIZE;
+            gst = gst + 1 == NG ? 0 : gst + 1;
+            const bool last = g + 1 == ngr;
+#pragma unroll
+            for (int u = 0; u < GS; ++u) {
+                // refill the edge stage of step s + ELA - NSE (done) with the edge rows of step s + ELA
+                __syncwarp();
+                const int eq = (u + ELA) % NSE;
+                const unsigned more = (u + ELA < GS || !last) && edges;
+                edge_issue(go & more, goj & more, gok & more, &ebars[eq], edge_bytes, ering + eq * St::ESIZE,
+                           ejsrc + u * St::EJ, St::EJB, ering + eq * St::ESIZE + St::EJ, eksrc + u * St::EK, St::EKB);
+                if (lead && more) pending |= 1u << (NG + eq);
+                const bool valid = jk_ok && (unsigned)i < (unsigned)nx;
                 // in-tile neighbours: previous step's results of the adjacent lanes
-                T nj[3], nk[3], own[3];
+                T nj[3], nk[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    const T vj = __shfl_sync(0xffffffffu, prev[e], lane_j);
-                    const T vk = __shfl_sync(0xffffffffu, prev[e], lane_k);
-                    nj[e] = has_j ? vj : T(0);
-                    nk[e] = has_k ? vk : T(0);
-                    own[e] = has_i ? prev[e] : T(0);
+                    nj[e] = __shfl_sync(0xffffffffu, prev[e], lane_j);
+                    nk[e] = __shfl_sync(0xffffffffu, prev[e], lane_k);
                 }
-                // wait for this step's stages
-                wait_stage(&bars[st], st);
-                if (edges) wait_stage(&ebars[est], NSD + est);
-                const T *stg = ring + st * St::SIZE;
-                const T *estg = ering + est * St::ESIZE;
-                st = st + 1 == NSD ? 0 : st + 1;
-                est = est + 1 == NSE ? 0 : est + 1;
-                if (valid && edge_j && has_j) {
-                    const T *e4 = estg + b * 4;
-                    T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(pollj, v3, deadline)) failed = true;
-                    nj[0] = v3[0];
-                    nj[1] = v3[1];
-                    nj[2] = v3[2];
-                }
-                if (valid && edge_k && has_k) {
-                    const T *e4 = estg + St::EJ + a * 4;
-                    T v3[3] = {e4[0], e4[1], e4[2]};
-                    if (!poll3(pollk, v3, deadline)) failed = true;
-                    nk[0] = v3[0];
-                    nk[1] = v3[1];
-                    nk[2] = v3[2];
-                }
-                pollj += St::EJ;
-                pollk += St::EK;
                 // factor row and input of this lane
                 T f[NQP];
                 {
-                    const T *row = stg + lane * NQP;
+                    const T *row = grp + u * St::F + lane * NQP;
                     if (sizeof(T) == 4) {
 #pragma unroll
                         for (int q = 0; q < 9; ++q) {
@@ -342,15 +380,41 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     }
                 }
                 T vin[3];
-                {
-                    const T *v4 = stg + St::F + lane * 4;
-                    vin[0] = v4[0];
-                    vin[1] = v4[1];
-                    vin[2] = v4[2];
+                lds3(grp + GS * St::F + u * St::V + lane * 4, vin);
+                // neighbours from other tiles
+                T ej[3] = {T(0), T(0), T(0)}, ek[3] = {T(0), T(0), T(0)};
+                if (edges) {
+                    wait_bar(&ebars[u % NSE], NG + u % NSE);
+                    const T *estg = ering + (u % NSE) * St::ESIZE;
+                    lds3(estg + b * 4, ej);
+                    lds3(estg + St::EJ + a * 4, ek);
+                    const bool bad = valid && ((edge_j && is_sent3(ej)) || (edge_k && is_sent3(ek)));
+                    if (__any_sync(0xffffffffu, bad) && bad) {
+                        // not yet published when the copy ran: re-read until it appears
+                        const T *gj = pollj + u * St::EJ, *gk = pollk + u * St::EK;
+                        unsigned spins = 0;
+                        for (;;) {
+                            const bool mj = edge_j && is_sent3(ej), mk = edge_k && is_sent3(ek);
+                            if (!mj && !mk) break;
+                            if (mj)
+                                for (int e = 0; e < 3; ++e) ej[e] = value_of(ld_relaxed(gj + e));
+                            if (mk)
+                                for (int e = 0; e < 3; ++e) ek[e] = value_of(ld_relaxed(gk + e));
+                            if ((++spins & 63u) == 0 && global_timer() > deadline) {
+                                failed = true;
+                                break;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    nj[e] = edge_j ? ej[e] : nj[e];
+                    nk[e] = edge_k ? ek[e] : nk[e];
                 }
                 // slots: forward [0] -z [1] -y [2] -x ; backward [0] +x [1] +y [2] +z
-                const T *x0 = FWD ? nk : own;
-                const T *x2 = FWD ? own : nk;
+                const T *x0 = FWD ? nk : prev;
+                const T *x2 = FWD ? prev : nk;
                 T acc[3];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
@@ -373,28 +437,28 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                     res[e] = FWD ? d : (vin[e] - d);
                 }
                 if (valid) {
-                    yout[0] = res[0];
-                    yout[1] = res[1];
-                    yout[2] = res[2];
-                    if (pub_j && s >= TJ - 1) {
-                        st_relaxed(pubj, res[0]);
-                        st_relaxed(pubj + 1, res[1]);
-                        st_relaxed(pubj + 2, res[2]);
+                    if (FWD) {
+                        st3pad(yout + u * ystep, res);
+                    } else {
+                        T *zo = yout + u * ystep;
+                        zo[0] = res[0];
+                        zo[1] = res[1];
+                        zo[2] = res[2];
                     }
-                    if (pub_k && s >= TK - 1) {
-                        st_relaxed(pubk, res[0]);
-                        st_relaxed(pubk + 1, res[1]);
-                        st_relaxed(pubk + 2, res[2]);
-                    }
+                    if (pub_j) st_relaxed3(pubj + u * St::EJ, res);
+                    if (pub_k) st_relaxed3(pubk + u * St::EK, res);
                 }
-                yout += ystep;
-                pubj += St::EJ;
-                pubk += St::EK;
                 i += FWD ? 1 : -1;
 #pragma unroll
                 for (int e = 0; e < 3; ++e) prev[e] = valid ? res[e] : T(0);
-                __syncwarp();
             }
+            yout += GS * ystep;
+            pubj += GS * St::EJ;
+            pubk += GS * St::EK;
+            pollj += GS * St::EJ;
+            pollk += GS * St::EK;
+            ejsrc += GS * St::EJ;
+            eksrc += GS * St::EK;
             if (__any_sync(0xffffffffu, failed)) {
                 failed = true;
                 break;
@@ -402,11 +466,11 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
         }
     }
     if (failed) {
-        if (lane == 0) {
+        if (lead) {
             atomicCAS(P.status, 0, (int)RSV_ETIMEOUT);
             // let copies still in flight land before the CTA exits (bounded)
             const uint64_t limit = global_timer() + 1000000000ull;
-            for (int q = 0; q < NSD + NSE; ++q)
+            for (int q = 0; q < NG + NSE; ++q)
                 if (pending & (1u << q))
                     while (!mbar_try_wait(&bars[q], (phase >> q) & 1u) && global_timer() < limit) {
                     }
@@ -426,9 +490,9 @@ __global__ void pack_tiles(const TileSys *__restrict__ tsys, const int *__restri
     constexpr int NQP = Bits<T>::NQP;
     const int t = blockIdx.y;
     const TileSys G = tsys[tile_sys[t]];
-    const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)S * 32) return;
+    if (gid >= (int64_t)G.Sp * 32) return;
     const int lane = (int)(gid & 31);
     const int s = (int)(gid >> 5);
     const int a = lane & 7, b = lane >> 3;
@@ -468,9 +532,9 @@ __global__ void gather_tiles(const TileSys *__restrict__ tsys, const int *__rest
     using U = typename Bits<T>::U;
     const int t = blockIdx.y;
     const TileSys G = tsys[tile_sys[t]];
-    const int nx = G.nx, ny = G.ny, nz = G.nz, S = G.S;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)S * 32) return;
+    if (gid >= (int64_t)G.Sp * 32) return;
     const int lane = (int)(gid & 31);
     const int s = (int)(gid >> 5);
     const int a = lane & 7, b = lane >> 3;
@@ -517,9 +581,10 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
             ts.nTJ = (sg.ny + TJ - 1) / TJ;
             ts.nTK = (sg.nz + TK - 1) / TK;
             ts.S = sg.nx + TJ + TK - 2;
+            ts.Sp = (ts.S + GS - 1) / GS * GS;
             ts.cell0 = sg.cell0;
             ts.poff = (int)order.size();
-            maxS = std::max(maxS, ts.S);
+            maxS = std::max(maxS, ts.Sp);
             pos.resize(order.size() + (size_t)ts.nTJ * ts.nTK);
             for (int d = 0; d <= ts.nTJ + ts.nTK - 2; ++d)
                 for (int J = 0; J < ts.nTJ; ++J) {
@@ -529,7 +594,7 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
                     order.push_back(make_int2(J, K));
                     tile_sys.push_back(g);
                     row0.push_back(rows);
-                    rows += ts.S;
+                    rows += ts.Sp;
                 }
             sys.push_back(ts);
         }
@@ -571,8 +636,7 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
         int dev = 0, sms = 0, per_f = 0, per_b = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = (Bits<T>::NSD * St::SIZE + NSE * St::ESIZE) * sizeof(T) +
-                            (Bits<T>::NSD + NSE) * sizeof(uint64_t);
+        const size_t smem = sweep_smem<T>();
         if ((e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
