@@ -57,10 +57,10 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA cores) from the pool's nominal table
 # DRAM bytes per launch (read + write) measured by one ncu capture of the current kernels on this
 # workload (profiles/ilu_apply_mid_100x100x50.md).  Set an entry to None whenever its kernel changes.
 NCU_TRAFFIC = {
-    "ilu_apply_f32": None,      # gather_tiles + forward + backward sweep, FP32
-    "ilu_apply_f64": None,
+    "ilu_apply_f32": 206.8e6,   # gather_tiles + forward + backward sweep, FP32
+    "ilu_apply_f64": 462.4e6,
     "spmv_f32": 148.0e6,
-    "spmv_f64": 284.0e6,
+    "spmv_f64": 284.2e6,
 }
 
 
