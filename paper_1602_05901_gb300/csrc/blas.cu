@@ -219,6 +219,96 @@ __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *
     }
 }
 
+// Classical Gram-Schmidt with reorthogonalisation, the first pass's update fused with the
+// second pass's projections (Section "Algebraic Operations": the orthogonalisation of
+// GMRES is dot products and vector updates).  For each row block a thread loads the k
+// basis values once into registers, forms w' = w - sum_i c_i V_i with the same FMA order
+// as maxpy_kernel, stores it, and accumulates <w', V_i> and <w', w'> from those registers:
+// the second pass's projections cost no second read of the basis.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kRedThreads, 1) maxpy_mdot_kernel(int64_t n, T *w, const T *__restrict__ V,
+                                                                 int64_t ldv, int k, const double *c,
+                                                                 double *partial, double *proj, double *nrm,
+                                                                 unsigned *counter, const int *done) {
+    if (is_done(done)) return;
+    using VT = Vec<T>;
+    constexpr int KF = kFuseMax<T>;
+    __shared__ T sc[KF];
+    __shared__ double smg[kGroup][kRedThreads / 32];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = (T)(-c[i]);
+    __syncthreads();
+    Acc<T> ss, acc[KF];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tail = 0;
+    if (VEC) {
+        const int64_t nv = n / VT::N;
+        for (int64_t r = tid; r < nv; r += stride) {
+            typename VT::V vr[KF];
+#pragma unroll
+            for (int i = 0; i < KF; ++i)
+                if (i < k) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)i * ldv)[r];
+            typename VT::V o = reinterpret_cast<const typename VT::V *>(w)[r];
+#pragma unroll
+            for (int i = 0; i < KF; ++i)
+                if (i < k) {
+#pragma unroll
+                    for (int q = 0; q < VT::N; ++q) VT::set(o, q, fma(sc[i], VT::get(vr[i], q), VT::get(o, q)));
+                }
+            reinterpret_cast<typename VT::V *>(w)[r] = o;
+#pragma unroll
+            for (int q = 0; q < VT::N; ++q) ss.add(VT::get(o, q), VT::get(o, q));
+#pragma unroll
+            for (int i = 0; i < KF; ++i)
+                if (i < k) {
+#pragma unroll
+                    for (int q = 0; q < VT::N; ++q) acc[i].add(VT::get(o, q), VT::get(vr[i], q));
+                }
+        }
+        tail = nv * VT::N;
+    }
+    for (int64_t r = tail + tid; r < n; r += stride) {
+        T vr[KF];
+#pragma unroll
+        for (int i = 0; i < KF; ++i)
+            if (i < k) vr[i] = V[(int64_t)i * ldv + r];
+        T o = w[r];
+#pragma unroll
+        for (int i = 0; i < KF; ++i)
+            if (i < k) o = fma(sc[i], vr[i], o);
+        w[r] = o;
+        ss.add(o, o);
+#pragma unroll
+        for (int i = 0; i < KF; ++i)
+            if (i < k) acc[i].add(o, vr[i]);
+    }
+#pragma unroll
+    for (int g0 = 0; g0 < KF; g0 += kGroup) {
+        if (g0 < k) {
+            double vals[kGroup];
+#pragma unroll
+            for (int i = 0; i < kGroup; ++i) vals[i] = g0 + i < k ? acc[g0 + i].value() : 0.0;
+            block_partial_group<kGroup>(vals, min(kGroup, k - g0), smg, partial, g0);
+        }
+    }
+    {
+        double v1[kGroup] = {ss.value()};
+        block_partial_group<kGroup>(v1, 1, smg, partial, k);
+    }
+    if (last_cta(counter)) {
+        for (int i = threadIdx.x >> 5; i <= k; i += kRedThreads / 32) {
+            const double s = final_sum(partial, i);
+            if ((threadIdx.x & 31) == 0) {
+                if (i < k)
+                    proj[i] = s;
+                else
+                    *nrm = sqrt(s);
+            }
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__restrict__ x,
                                                           const T *__restrict__ y, double *partial, double *out,
@@ -323,6 +413,21 @@ cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, 
 }
 
 template <typename T>
+cudaError_t launch_maxpy_mdot(cudaStream_t st, int64_t n, T *w, const T *V, int64_t ldv, int k, const double *c,
+                              double *partial, double *proj, double *nrm, unsigned *counter, const int *done) {
+    if (k < 1 || k > kFuseMax<T>) return cudaErrorInvalidValue;
+    rsv::count_launches(1);
+    constexpr int grid = kRedBlocks / 2;  // one CTA per SM: the basis values of a row block live in registers
+    if (vec_ok<T>(ldv, {w, V}))
+        maxpy_mdot_kernel<T, true><<<grid, kRedThreads, 0, st>>>(n, w, V, ldv, k, c, partial, proj, nrm, counter,
+                                                                 done);
+    else
+        maxpy_mdot_kernel<T, false><<<grid, kRedThreads, 0, st>>>(n, w, V, ldv, k, c, partial, proj, nrm, counter,
+                                                                  done);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,
                        unsigned *counter, int sqrt_out, const int *done) {
     rsv::count_launches(1);
@@ -368,6 +473,8 @@ cudaError_t launch_add_f32_scaled(cudaStream_t st, int64_t n, const float *df, c
                                         double *, unsigned *, const int *, double *, const int *);                 \
     template cudaError_t launch_maxpy<T>(cudaStream_t, int64_t, const T *, const T *, int64_t, int, const double *, \
                                          double, T *, double *, double *, unsigned *, const int *, const int *);    \
+    template cudaError_t launch_maxpy_mdot<T>(cudaStream_t, int64_t, T *, const T *, int64_t, int, const double *,  \
+                                              double *, double *, double *, unsigned *, const int *);              \
     template cudaError_t launch_dot<T>(cudaStream_t, int64_t, const T *, const T *, double *, double *, unsigned *, \
                                        int, const int *);                                                           \
     template cudaError_t launch_axpby<T>(cudaStream_t, int64_t, T, const T *, T, const T *, T *);                  \

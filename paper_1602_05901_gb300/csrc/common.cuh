@@ -153,6 +153,15 @@ template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
                          double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done,
                          const int *skip = nullptr);
+// Classical Gram-Schmidt, the first pass's update fused with the second pass's projections:
+// w -= sum_i c[i] V_i (in place, in the vector precision), then proj[i] = <w, V_i> for i < k
+// and *nrm = ||w||_2.  Each basis value is read once.  Returns cudaErrorInvalidValue (nothing
+// launched) when k > kFuseMax<T>; the caller then runs launch_maxpy and launch_mdot.  The k
+// basis values of a row block stay in registers: 32 FP32 float4s, or 16 FP64 double2s.
+template <typename T> constexpr int kFuseMax = sizeof(T) == 4 ? 32 : 16;
+template <typename T>
+cudaError_t launch_maxpy_mdot(cudaStream_t st, int64_t n, T *w, const T *V, int64_t ldv, int k, const double *c,
+                              double *partial, double *proj, double *nrm, unsigned *counter, const int *done);
 // *out = ||x||_2 (sqrt_out=1) or <x,y>
 template <typename T>
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,

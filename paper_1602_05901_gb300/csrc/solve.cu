@@ -44,32 +44,48 @@ __device__ __forceinline__ void raise_status(DevState *ds, int code) {
 
 // Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
 // previous Givens rotations, a new rotation and the residual estimate |g_{j+1}|.
+// The block stages the column and the rotations in shared memory, so the serial
+// chain of rotations (thread 0) runs at shared-memory latency.
 __global__ void gmres_givens(DevState *ds, int j, int m) {
     if (ds->done) return;
+    __shared__ double col[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart];
     double *H = ds->H;
-    for (int i = 0; i <= j; ++i) H[i * m + j] = ds->h1[i] + ds->h2[i];
-    H[(j + 1) * m + j] = ds->hn;
-    for (int i = 0; i < j; ++i) {
-        const double a = H[i * m + j], b = H[(i + 1) * m + j];
-        H[i * m + j] = ds->cs[i] * a + ds->sn[i] * b;
-        H[(i + 1) * m + j] = -ds->sn[i] * a + ds->cs[i] * b;
+    const int t = threadIdx.x;
+    for (int i = t; i <= j; i += blockDim.x) col[i] = ds->h1[i] + ds->h2[i];
+    for (int i = t; i < j; i += blockDim.x) {
+        cs[i] = ds->cs[i];
+        sn[i] = ds->sn[i];
     }
-    const double a = H[j * m + j], b = H[(j + 1) * m + j];
-    const double rho = hypot(a, b);
-    if (!isfinite(rho) || !isfinite(ds->hn)) return raise_status(ds, RSV_ENAN);
-    if (!(rho > 0.0)) return raise_status(ds, RSV_EBREAKDOWN);
-    ds->cs[j] = a / rho;
-    ds->sn[j] = b / rho;
-    H[j * m + j] = rho;
-    H[(j + 1) * m + j] = 0.0;
-    ds->g[j + 1] = -ds->sn[j] * ds->g[j];
-    ds->g[j] = ds->cs[j] * ds->g[j];
-    ds->jend = j + 1;
-    ds->iters += 1;
-    const bool lucky = !(ds->hn > 0.0);
-    const bool met = fabs(ds->g[j + 1]) <= ds->tol;
-    if (met || lucky) ds->conv = 1;
-    if (met || ds->iters >= ds->maxit || lucky || j + 1 == m) ds->done = 1;
+    if (t == 0) col[j + 1] = ds->hn;
+    __syncthreads();
+    if (t == 0) {
+        for (int i = 0; i < j; ++i) {
+            const double a = col[i], b = col[i + 1];
+            col[i] = cs[i] * a + sn[i] * b;
+            col[i + 1] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = col[j], b = col[j + 1];
+        const double rho = hypot(a, b);
+        if (!isfinite(rho) || !isfinite(ds->hn)) {
+            raise_status(ds, RSV_ENAN);
+        } else if (!(rho > 0.0)) {
+            raise_status(ds, RSV_EBREAKDOWN);
+        } else {
+            ds->cs[j] = a / rho;
+            ds->sn[j] = b / rho;
+            H[j * m + j] = rho;
+            H[(j + 1) * m + j] = 0.0;
+            ds->g[j + 1] = -ds->sn[j] * ds->g[j];
+            ds->g[j] = ds->cs[j] * ds->g[j];
+            ds->jend = j + 1;
+            ds->iters += 1;
+            const bool lucky = !(ds->hn > 0.0);
+            const bool met = fabs(ds->g[j + 1]) <= ds->tol;
+            if (met || lucky) ds->conv = 1;
+            if (met || ds->iters >= ds->maxit || lucky || j + 1 == m) ds->done = 1;
+        }
+    }
+    for (int i = t; i < j; i += blockDim.x) H[i * m + j] = col[i];
 }
 
 // After the first Gram-Schmidt pass: keep its result when ||w'|| >= ||w|| / sqrt(2),
@@ -273,16 +289,24 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
             // more than 1 - 1/sqrt(2) of the norm ("twice is enough")
             RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done,
                                         &ds->wnorm));
-            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, &ds->hn,
-                                         &ds->counter[1], &ds->done));
-            rsv::count_launches(1);
-            gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0], &ds->done,
-                                        nullptr, &ds->skip2));
+            if (j + 1 <= kFuseMax<T>) {
+                // the first pass's update also forms the second pass's projections
+                RSV_CUDA_TRY(launch_maxpy_mdot<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, s->partial, ds->h2, &ds->hn,
+                                                  &ds->counter[1], &ds->done));
+                rsv::count_launches(1);
+                gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
+            } else {
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, &ds->hn,
+                                             &ds->counter[1], &ds->done));
+                rsv::count_launches(1);
+                gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
+                RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0],
+                                            &ds->done, nullptr, &ds->skip2));
+            }
             RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
                                          &ds->counter[1], &ds->done, &ds->skip2));
             rsv::count_launches(1);
-            gmres_givens<<<1, 1, 0, s->st>>>(ds, j, m);
+            gmres_givens<<<1, kMaxRestart, 0, s->st>>>(ds, j, m);
             if (s->pc_type == RSV_PC_CPR_LEARNED) RSV_CUDA_TRY(learned_watch(s, j));
             RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, wj, &ds->hn, &ds->done));
         }
