@@ -2,13 +2,15 @@
 // y = a x + b y, <x,y>, ||x||), fused where a solver step allows it.
 //
 // Vectors are FP64, or FP32 in the inner solves of mixed precision.  Every
-// reduction is FP64-accurate: FP64 vectors accumulate with FP64 FMAs; FP32
+// reduction is far more accurate than its vectors: FP64 vectors accumulate with
+// FP64 FMAs (FP64-accurate sums); FP32
 // vectors accumulate each thread's products in double-float form (an FP32
 // pair hi + lo updated with error-free transformations: the exact rounding
 // error of each product from an FMA, and of each addition from Knuth's
 // two-sum), which GB300 runs on its FP32 pipes instead of its much narrower
-// FP64 pipe.  Each thread's pair is then widened to FP64 for the block and
-// grid reductions.
+// FP64 pipe.  The warp trees add those pairs as double-float sums too; one
+// value per warp is widened to FP64 for the block and grid reductions.  An FP32
+// vector's sums so keep about 46 bits, against the 24 of its entries.
 //
 // Reductions are deterministic: every CTA writes one partial per output, and
 // the last CTA to finish (ticket counter) sums the partials in CTA order.
@@ -34,10 +36,13 @@ __device__ __forceinline__ bool last_cta(unsigned *counter) {
     return am_last;
 }
 
-// Block-reduce `v` (one value per thread per output slot) into partial[slot * grid + block].
-__device__ __forceinline__ void block_partial(double v, double *sm, double *partial, int slot) {
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+// Block-reduce one partial sum per thread into partial[slot * grid + block]: a warp
+// tree in the accumulator's form, then the warps' sums in FP64 in warp order.
+template <typename T>
+__device__ __forceinline__ void block_partial(Part<T> v, double *sm, double *partial, int slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v.add(v.xor_shfl(o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v.value();
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -47,20 +52,31 @@ __device__ __forceinline__ void block_partial(double v, double *sm, double *part
     __syncthreads();
 }
 
-// Block-reduce kg values per thread at once into partial[(slot0 + i) * grid + block]:
-// warp sums by shuffles, one shared-memory exchange and one barrier pair for
-// the whole group; thread i < kg adds the warps' sums in warp order (fixed
-// order: deterministic).
-template <int G>
-__device__ __forceinline__ void block_partial_group(const double (&v)[G], int kg, double (*sm)[kRedThreads / 32],
+// Block-reduce kGroup partial sums per thread (the first kg are kept) into
+// partial[(slot0 + i) * grid + block].  The warp stage is a butterfly: at each of
+// the first four levels a lane keeps half of its values, sends the other half to
+// its partner and adds what it receives, so a lane ends with one value, the sum
+// over 16 lanes of value (lane >> 1); the fifth level adds the partner's.  That is
+// 16 exchanges and additions per lane instead of 5 per value.  Then the warps'
+// sums are added in FP64 in warp order (fixed order: deterministic).
+template <typename T>
+__device__ __forceinline__ void block_partial_group(Part<T> (&v)[kGroup], int kg, double (*sm)[kRedThreads / 32],
                                                     double *partial, int slot0) {
+    static_assert(kGroup == 16, "the butterfly halves 16 values four times");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < G; ++i)
-        if (i < kg) {
-            const double t = warp_sum(v[i]);
-            if (lane == 0) sm[i][warp] = t;
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool up = (lane & (2 * h)) != 0;  // this lane keeps the upper half
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const Part<T> send = up ? v[i] : v[i + h];
+            Part<T> keep = up ? v[i + h] : v[i];
+            keep.add(send.xor_shfl(2 * h));
+            v[i] = keep;
         }
+    }
+    v[0].add(v[0].xor_shfl(1));
+    if ((lane & 1) == 0 && (lane >> 1) < kg) sm[lane >> 1][warp] = v[0].value();
     __syncthreads();
     if (threadIdx.x < kg) {
         double s = 0.0;
@@ -104,7 +120,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
         } else {
             for (int64_t r = tid; r < n; r += stride) a.add(w[r], w[r]);
         }
-        block_partial(a.value(), sm, partial, k);
+        block_partial<T>(Part<T>::of(a), sm, partial, k);
     }
     for (int g0 = 0; g0 < k; g0 += kGroup) {
         Acc<T> acc[kGroup];
@@ -138,10 +154,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
                     if (i < kg) acc[i].add(wr, V[(int64_t)(g0 + i) * ldv + r]);
             }
         }
-        double vals[kGroup];
+        Part<T> vals[kGroup];
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i) vals[i] = i < kg ? acc[i].value() : 0.0;
-        block_partial_group<kGroup>(vals, kg, smg, partial, g0);
+        for (int i = 0; i < kGroup; ++i) vals[i] = i < kg ? Part<T>::of(acc[i]) : Part<T>::zero();
+        block_partial_group<T>(vals, kg, smg, partial, g0);
     }
     if (last_cta(counter)) {
         const int kk = self_nrm ? k + 1 : k;
@@ -156,7 +172,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
     }
 }
 
-// out = base + sgn * sum_i c_i V_i, in the vector precision; ||out|| FP64-accurate.
+// out = base + sgn * sum_i c_i V_i, in the vector precision; ||out|| summed like the dot products.
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *base, const T *__restrict__ V,
                                                             int64_t ldv, int k, const double *c, double sgn, T *out,
@@ -207,7 +223,7 @@ __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *
         ss.add(acc, acc);
     }
     if (!nrm) return;
-    block_partial(ss.value(), sm, partial, 0);
+    block_partial<T>(Part<T>::of(ss), sm, partial, 0);
     if (last_cta(counter)) {
         if (threadIdx.x < 32) {
             const double s = final_sum(partial, 0);
@@ -285,16 +301,13 @@ __global__ void __launch_bounds__(kRedThreads, 1) maxpy_mdot_kernel(int64_t n, T
 #pragma unroll
     for (int g0 = 0; g0 < KF; g0 += kGroup) {
         if (g0 < k) {
-            double vals[kGroup];
+            Part<T> vals[kGroup];
 #pragma unroll
-            for (int i = 0; i < kGroup; ++i) vals[i] = g0 + i < k ? acc[g0 + i].value() : 0.0;
-            block_partial_group<kGroup>(vals, min(kGroup, k - g0), smg, partial, g0);
+            for (int i = 0; i < kGroup; ++i) vals[i] = g0 + i < k ? Part<T>::of(acc[g0 + i]) : Part<T>::zero();
+            block_partial_group<T>(vals, min(kGroup, k - g0), smg, partial, g0);
         }
     }
-    {
-        double v1[kGroup] = {ss.value()};
-        block_partial_group<kGroup>(v1, 1, smg, partial, k);
-    }
+    block_partial<T>(Part<T>::of(ss), &smg[0][0], partial, k);
     if (last_cta(counter)) {
         for (int i = threadIdx.x >> 5; i <= k; i += kRedThreads / 32) {
             const double s = final_sum(partial, i);
@@ -331,7 +344,7 @@ __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__
         tail = nv * VT::N;
     }
     for (int64_t r = tail + tid; r < n; r += stride) acc.add(x[r], y[r]);
-    block_partial(acc.value(), sm, partial, 0);
+    block_partial<T>(Part<T>::of(acc), sm, partial, 0);
     if (last_cta(counter)) {
         if (threadIdx.x < 32) {
             const double s = final_sum(partial, 0);

@@ -33,6 +33,44 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// A partial sum in its accumulator's form, for the warp reduction trees: an FP64
+// value, or a double-float pair (FP32 hi + lo) whose additions are Knuth
+// two-sums on the FP32 pipes.  GB300 runs FP64 arithmetic at a small fraction of
+// its FP32 rate, so FP32 vectors' sums stay off the FP64 pipe until one value per
+// warp is widened.  A double-float addition keeps about 46 bits of the sum.
+template <typename T> struct Part;
+template <> struct Part<double> {
+    double s;
+    __device__ __forceinline__ static Part of(const Acc<double> &a) { return {a.s}; }
+    __device__ __forceinline__ static Part zero() { return {0.0}; }
+    __device__ __forceinline__ Part xor_shfl(int o) const { return {__shfl_xor_sync(0xffffffffu, s, o)}; }
+    __device__ __forceinline__ void add(const Part &b) { s += b.s; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Part<float> {
+    float hi, lo;
+    __device__ __forceinline__ static Part of(const Acc<float> &a) { return {a.hi, a.lo}; }
+    __device__ __forceinline__ static Part zero() { return {0.f, 0.f}; }
+    __device__ __forceinline__ Part xor_shfl(int o) const {
+        return {__shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o)};
+    }
+    __device__ __forceinline__ void add(const Part &b) {
+        // two-sums of the high and of the low parts, then two renormalisations
+        const float s = __fadd_rn(hi, b.hi);
+        const float sb = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, sb)), __fsub_rn(b.hi, sb));
+        const float t = __fadd_rn(lo, b.lo);
+        const float tb = __fsub_rn(t, lo);
+        const float f = __fadd_rn(__fsub_rn(lo, __fsub_rn(t, tb)), __fsub_rn(b.lo, tb));
+        e = __fadd_rn(e, t);
+        const float h = __fadd_rn(s, e);
+        e = __fadd_rn(__fsub_rn(e, __fsub_rn(h, s)), f);
+        hi = __fadd_rn(h, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, h));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename T> struct Vec;
 template <> struct Vec<float> {
     using V = float4;
