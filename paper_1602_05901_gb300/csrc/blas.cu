@@ -107,8 +107,11 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
     __shared__ double smg[kGroup][kRedThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (self_nrm) {
-        Acc<T> a;
+    // <w, w> rides along with the first group of projections (w is read once); alone only when k == 0
+    const bool fold = self_nrm && k > 0;
+    Acc<T> ww;
+    if (self_nrm && !fold) {
+        Acc<T> &a = ww;
         if (VEC) {
             const int64_t nv = n / VT::N;
             for (int64_t r = tid; r < nv; r += stride) {
@@ -120,13 +123,13 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
         } else {
             for (int64_t r = tid; r < n; r += stride) a.add(w[r], w[r]);
         }
-        block_partial<T>(Part<T>::of(a), sm, partial, k);
     }
     for (int g0 = 0; g0 < k; g0 += kGroup) {
         Acc<T> acc[kGroup];
         const int kg = min(kGroup, k - g0);
         if (VEC) {
             const int64_t nv = n / VT::N;
+            const bool nw = fold && g0 == 0;
             for (int64_t r = tid; r < nv; r += stride) {
                 // issue every load of the group first, then accumulate (keeps kg loads in flight)
                 const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
@@ -134,6 +137,10 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i)
                     if (i < kg) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)(g0 + i) * ldv)[r];
+                if (nw) {
+#pragma unroll
+                    for (int q = 0; q < VT::N; ++q) ww.add(VT::get(wr, q), VT::get(wr, q));
+                }
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i)
                     if (i < kg) {
@@ -142,13 +149,16 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
                     }
             }
             for (int64_t r = nv * VT::N + tid; r < n; r += stride) {
+                if (nw) ww.add(w[r], w[r]);
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i)
                     if (i < kg) acc[i].add(w[r], V[(int64_t)(g0 + i) * ldv + r]);
             }
         } else {
+            const bool nw = fold && g0 == 0;
             for (int64_t r = tid; r < n; r += stride) {
                 const T wr = w[r];
+                if (nw) ww.add(wr, wr);
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i)
                     if (i < kg) acc[i].add(wr, V[(int64_t)(g0 + i) * ldv + r]);
@@ -159,6 +169,7 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
         for (int i = 0; i < kGroup; ++i) vals[i] = i < kg ? Part<T>::of(acc[i]) : Part<T>::zero();
         block_partial_group<T>(vals, kg, smg, partial, g0);
     }
+    if (self_nrm) block_partial<T>(Part<T>::of(ww), sm, partial, k);
     if (last_cta(counter)) {
         const int kk = self_nrm ? k + 1 : k;
         for (int i = threadIdx.x >> 5; i < kk; i += kRedThreads / 32) {
@@ -363,17 +374,39 @@ __global__ void axpby_kernel(int64_t n, T a, const T *x, T b, const T *y, T *z) 
         z[r] = (b == T(0)) ? a * x[r] : a * x[r] + b * y[r];
 }
 
-template <typename T>
+// The FP64 reciprocal of a device scalar, formed once per block (an FP64 division in
+// every thread costs more than the whole vector pass on GB300's narrow FP64 pipe).
+__device__ __forceinline__ double block_inverse(const double *s) {
+    __shared__ double f;
+    if (threadIdx.x == 0) f = 1.0 / *s;
+    __syncthreads();
+    return f;
+}
+
+template <typename T, bool VEC>
 __global__ void scale_inv_kernel(int64_t n, T *x, const double *s, const int *done) {
     if (is_done(done)) return;
-    const T f = (T)(1.0 / *s);
+    using VT = Vec<T>;
+    const T f = (T)block_inverse(s);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) x[r] *= f;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tail = 0;
+    if (VEC) {
+        const int64_t nv = n / VT::N;
+        for (int64_t r = tid; r < nv; r += stride) {
+            typename VT::V v = reinterpret_cast<typename VT::V *>(x)[r];
+#pragma unroll
+            for (int q = 0; q < VT::N; ++q) VT::set(v, q, VT::get(v, q) * f);
+            reinterpret_cast<typename VT::V *>(x)[r] = v;
+        }
+        tail = nv * VT::N;
+    }
+    for (int64_t r = tail + tid; r < n; r += stride) x[r] *= f;
 }
 
 // Mixed-precision glue: xf = (float)(x / *s); x += (*s) * (double)df.
 __global__ void to_f32_scaled(int64_t n, const double *__restrict__ x, const double *s, float *__restrict__ xf) {
-    const double f = 1.0 / *s;
+    const double f = block_inverse(s);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) xf[r] = (float)(x[r] * f);
 }
@@ -463,7 +496,10 @@ template <typename T>
 cudaError_t launch_scale_inv(cudaStream_t st, int64_t n, T *x, const double *s, const int *done) {
     if (n == 0) return cudaSuccess;
     rsv::count_launches(1);
-    scale_inv_kernel<T><<<elementwise_grid(n), 256, 0, st>>>(n, x, s, done);
+    if (vec_ok<T>(0, {x}))
+        scale_inv_kernel<T, true><<<elementwise_grid(n / Vec<T>::N + 1), 256, 0, st>>>(n, x, s, done);
+    else
+        scale_inv_kernel<T, false><<<elementwise_grid(n), 256, 0, st>>>(n, x, s, done);
     return cudaGetLastError();
 }
 
