@@ -9,7 +9,8 @@ Parity status of each routine (pins live in ``tests/test_oracle_pins.py``):
 SpMV, 3x3 inverse, dense solve, block Jacobi, block ILU(0), quasi-IMPES,
 Galerkin coarsening, red-black Gauss-Seidel, V-cycle, CPR, GMRES, FGMRES,
 BiCGSTAB and iterative refinement are each pinned against dense linear
-algebra, closed forms or invariants.
+algebra, closed forms or invariants; so are the CPR stage orders (FP, FPF,
+FFPF).
 """
 from __future__ import annotations
 
@@ -25,7 +26,9 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 OK, EINVAL, ENOMEM, ESINGULAR, EBREAKDOWN, ENOCONV, ENAN = 0, 1, 2, 5, 6, 7, 9
-PC = {"none": 0, "bjacobi": 1, "bilu0": 2, "cpr": 3}
+# "cpr" is CPR-PF (pressure stage, then full stage); the other orders follow the
+# paper's CPR-FP, CPR-FPF and CPR-FFPF algorithms
+PC = {"none": 0, "bjacobi": 1, "bilu0": 2, "cpr": 3, "cpr_fp": 5, "cpr_fpf": 6, "cpr_ffpf": 7}
 
 
 def build(force: bool = False) -> str:

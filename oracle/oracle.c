@@ -460,7 +460,8 @@ int or_gmg_vcycle(int nx, int ny, int nz, const double *a7, int max_levels, int 
 
 /* ------------------------------------------------------------ system + PCs */
 
-enum { PC_NONE = 0, PC_BJACOBI = 1, PC_BILU0 = 2, PC_CPR = 3 };
+enum { PC_NONE = 0, PC_BJACOBI = 1, PC_BILU0 = 2, PC_CPR = 3, PC_CPR_FP = 5, PC_CPR_FPF = 6, PC_CPR_FFPF = 7 };
+static int is_cpr(int pc) { return pc == PC_CPR || pc == PC_CPR_FP || pc == PC_CPR_FPF || pc == PC_CPR_FFPF; }
 
 typedef struct {
     int nx, ny, nz, nb;
@@ -500,7 +501,8 @@ void or_destroy(or_system *s) {
 }
 
 /* Preconditioner setup.  pc: 0 none, 1 block Jacobi, 2 block ILU(0),
- * 3 CPR (quasi-IMPES + GMG V-cycle pressure stage, then block ILU(0)).
+ * 3 CPR-PF (quasi-IMPES + GMG V-cycle pressure stage, then block ILU(0)),
+ * 5 CPR-FP, 6 CPR-FPF, 7 CPR-FFPF (the same two stages in the other orders).
  * float_round != 0 rounds the stored factors to float after setup. */
 int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweeps, int float_round) {
     int nb = s->nb;
@@ -512,7 +514,7 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
         if (float_round)
             for (size_t q = 0; q < 9 * (size_t)nb; ++q) s->dinv[q] = round_f32(s->dinv[q]);
     }
-    if (pc == PC_BILU0 || pc == PC_CPR) {
+    if (pc == PC_BILU0 || is_cpr(pc)) {
         s->lu = (double *)malloc(sizeof(double) * 9 * (size_t)s->rp[nb]);
         s->udinv = (double *)malloc(sizeof(double) * 9 * (size_t)nb);
         int64_t off = 0;
@@ -523,7 +525,7 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
         }
     }
     if (st) return st;
-    if (pc == PC_CPR) {
+    if (is_cpr(pc)) {
         s->w = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
         s->a7 = (double *)malloc(sizeof(double) * 7 * (size_t)nb);
         st = or_qi_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, s->w, s->a7);
@@ -560,6 +562,48 @@ static int cpr_apply(or_system *s, const double *f, double *x) {
     return OR_OK;
 }
 
+/* The CPR orders of Section "CPR-like preconditioners" (Algorithms CPR-FP,
+ * CPR-FPF, CPR-FFPF).  Notation: R(A)^{-1} is the full stage (RAS on one
+ * subdomain: block ILU(0) of A), M_g(A_pp)^{-1} the pressure solve (one GMG
+ * V-cycle), Pi_r / Pi_p the pressure restriction and prolongation.  Each
+ * algorithm starts with x = (first stage) f and then, for every later stage,
+ * forms r = f - A x and adds that stage applied to r:
+ *   FP:   x = R^{-1} f;  r = f - Ax;  x += Pi_p M_g^{-1} Pi_r r
+ *   FPF:  FP, then r = f - Ax;  x += R^{-1} r
+ *   FFPF: x = R^{-1} f;  r = f - Ax;  x += R^{-1} r;  r = f - Ax;
+ *         x += Pi_p M_g^{-1} Pi_r r;  r = f - Ax;  x += R^{-1} r
+ * `stages` spells the order, one letter per stage ('F' full, 'P' pressure). */
+static void stage_full(or_system *s, const double *r, double *y) {
+    or_bilu0_apply(s->nb, s->rp, s->ci, s->lu, s->udinv, r, y);
+}
+static int stage_pressure(or_system *s, const double *r, double *y) {
+    or_restrict_pressure(s->nb, s->w, r, s->gmg.b[0]);
+    int st = gmg_vcycle(&s->gmg, 0);
+    if (st) return st;
+    or_prolong_pressure(s->nb, s->gmg.x[0], y);
+    return OR_OK;
+}
+static int cpr_apply_order(or_system *s, const char *stages, const double *f, double *x) {
+    int64_t n = 3 * (int64_t)s->nb;
+    double *r = s->tmp_r, *y = s->tmp_x;
+    for (int q = 0; stages[q]; ++q) {
+        const double *src = f;
+        if (q > 0) { /* r = f - A x */
+            memcpy(r, f, sizeof(double) * (size_t)n);
+            or_spmv(s->nb, s->rp, s->ci, s->v, -1.0, x, 1.0, r);
+            src = r;
+        }
+        if (stages[q] == 'F') {
+            stage_full(s, src, y);
+        } else {
+            int st = stage_pressure(s, src, y);
+            if (st) return st;
+        }
+        for (int64_t i = 0; i < n; ++i) x[i] = (q == 0 ? 0.0 : x[i]) + y[i];
+    }
+    return OR_OK;
+}
+
 /* z = M^{-1} r for the configured preconditioner. */
 int or_pc_apply(or_system *s, const double *r, double *z) {
     int64_t n = 3 * (int64_t)s->nb;
@@ -569,6 +613,9 @@ int or_pc_apply(or_system *s, const double *r, double *z) {
     case PC_BJACOBI: or_bj_apply(s->nb, s->dinv, r, z); return OR_OK;
     case PC_BILU0: or_bilu0_apply(s->nb, s->rp, s->ci, s->lu, s->udinv, r, z); return OR_OK;
     case PC_CPR: return cpr_apply(s, r, z);
+    case PC_CPR_FP: return cpr_apply_order(s, "FP", r, z);
+    case PC_CPR_FPF: return cpr_apply_order(s, "FPF", r, z);
+    case PC_CPR_FFPF: return cpr_apply_order(s, "FFPF", r, z);
     }
     return OR_EINVAL;
 }

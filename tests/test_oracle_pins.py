@@ -305,6 +305,72 @@ def test_cpr_apply_matches_dense_two_stage_formula():
     assert st == 0 and np.allclose(x, ref, rtol=1e-9, atol=1e-12)
 
 
+CPR_ORDERS = [("cpr", "PF"), ("cpr_fp", "FP"), ("cpr_fpf", "FPF"), ("cpr_ffpf", "FFPF")]
+
+
+@pytest.mark.parametrize("pc,stages", CPR_ORDERS)
+def test_cpr_order_error_operator_is_product_of_stage_error_operators(pc, stages):
+    """Section "CPR-like preconditioners" (Algorithms CPR-FP, CPR-PF, CPR-FPF,
+    CPR-FFPF): every stage after the first acts on the residual f - A x and adds
+    to x, so the error operator I - M^{-1} A is the product of the stages' error
+    operators I - B A, the last stage leftmost.  The stage operators are formed
+    densely and independently of the oracle's apply: B_F = (LU)^{-1} from the
+    ILU(0) factors, B_P = Pi_p A_pp^{-1} Pi_r from the pressure stencil (one
+    level, so the V-cycle is an exact solve).  A stage in the wrong place, a
+    residual of the wrong sign or a stage that overwrites x fails."""
+    nx, ny, nz = 4, 3, 2
+    p = _prob((nx, ny, nz), seed=18)
+    s = oracle.System.from_problem(p, pc=pc, gmg_levels=1)
+    assert s.setup_status == 0 and s.gmg_levels() == 1
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    _, w, a7 = s.factors()
+    st, lu, udinv, _ = oracle.bilu0_setup(p.row_ptr, p.col_idx, p.vals)
+    assert st == 0
+    L, U = _ilu_dense(p, lu, udinv)
+    App = stencil_to_dense(nx, ny, nz, a7)
+    W = np.zeros((p.nb, p.n))
+    Pp = np.zeros((p.n, p.nb))
+    for c in range(p.nb):
+        W[c, 3 * c:3 * c + 3] = w[c]
+        Pp[3 * c, c] = 1.0
+    I = np.eye(p.n)
+    B = {"F": np.linalg.inv(L @ U), "P": Pp @ np.linalg.solve(App, W)}
+    E = I.copy()
+    for stage in stages:
+        E = (I - B[stage] @ A) @ E
+    Minv = np.zeros((p.n, p.n))
+    for i in range(p.n):
+        st, Minv[:, i] = s.pc_apply(I[i])
+        assert st == 0
+    assert np.allclose(I - Minv @ A, E, rtol=0, atol=1e-9 * max(1.0, np.abs(E).max()))
+
+
+@pytest.mark.parametrize("pc,stages", CPR_ORDERS)
+def test_cpr_orders_are_exact_where_ilu0_is_exact(pc, stages):
+    """On a one-cell-wide grid the matrix is block tridiagonal, ILU(0) is its exact
+    LU, and so every CPR order (each ends with a full stage, or starts with one
+    and the later stages see a zero residual) returns A^{-1} f."""
+    p = _prob((40, 1, 1), seed=19)
+    s = oracle.System.from_problem(p, pc=pc)
+    assert s.setup_status == 0
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    f = np.random.default_rng(20).standard_normal(p.n)
+    st, x = s.pc_apply(f)
+    assert st == 0
+    ref = np.linalg.solve(A, f)
+    assert np.allclose(x, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("pc", ["cpr_fp", "cpr_fpf", "cpr_ffpf"])
+def test_cpr_orders_precondition_gmres_to_the_dense_solution(pc):
+    p = _prob((10, 8, 4), seed=21)
+    s = oracle.System.from_problem(p, pc=pc)
+    st, x, info = s.gmres(p.b, rtol=1e-10, maxit=500)
+    assert st == 0
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    assert np.linalg.norm(A @ x - p.b) <= 1.0001e-10 * np.linalg.norm(p.b)
+
+
 # ----------------------------------------------------------------- Krylov
 
 def test_gmres_finite_termination():
