@@ -58,13 +58,27 @@ typedef enum {
 } rsv_status;
 
 /* RSV_PC_CPR_LEARNED: CPR whose pressure stage is a trained network (rsv_unet.h)
- * instead of the multigrid V-cycle; FP64 flexible GMRES only. */
+ * instead of the multigrid V-cycle; FP64 flexible GMRES only.
+ * The CPR stage orders (Section "CPR-like preconditioners", Algorithms CPR-FP,
+ * CPR-PF, CPR-FPF, CPR-FFPF).  F is the full stage (block ILU(0) of A: restricted
+ * additive Schwarz on one subdomain) and P the pressure stage (Pi_p, one GMG
+ * V-cycle on A_pp, Pi_r).  The first stage acts on f; every later stage acts on
+ * r = f - A x and adds to x:
+ *   RSV_PC_CPR      PF    (pressure, then full)
+ *   RSV_PC_CPR_FP   FP    (full, then pressure)
+ *   RSV_PC_CPR_FPF  FPF   (full, pressure, full)
+ *   RSV_PC_CPR_FFPF FFPF  (full, full, pressure, full)
+ * All four share one setup (quasi-IMPES weights, GMG hierarchy, ILU(0) factor)
+ * and run in FP64 or mixed precision, on single-grid matrices. */
 typedef enum {
     RSV_PC_NONE = 0,
     RSV_PC_BJACOBI = 1,
     RSV_PC_BILU0 = 2,
     RSV_PC_CPR = 3,
-    RSV_PC_CPR_LEARNED = 4
+    RSV_PC_CPR_LEARNED = 4,
+    RSV_PC_CPR_FP = 5,
+    RSV_PC_CPR_FPF = 6,
+    RSV_PC_CPR_FFPF = 7
 } rsv_pc_type;
 typedef enum { RSV_GMRES = 0, RSV_BICGSTAB = 1, RSV_FGMRES = 2 } rsv_solver_type;
 typedef enum { RSV_PREC_FP64 = 0, RSV_PREC_MIXED = 1 } rsv_precision;

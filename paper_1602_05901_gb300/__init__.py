@@ -29,10 +29,12 @@ _lib = ctypes.CDLL(LIB_PATH)
 RSV_OK, RSV_EINVAL, RSV_ENOMEM, RSV_ECUDA, RSV_ENOTSUP, RSV_ESINGULAR = 0, 1, 2, 3, 4, 5
 RSV_EBREAKDOWN, RSV_ENOCONV, RSV_ETIMEOUT, RSV_ENAN = 6, 7, 8, 9
 RSV_PC_NONE, RSV_PC_BJACOBI, RSV_PC_BILU0, RSV_PC_CPR, RSV_PC_CPR_LEARNED = 0, 1, 2, 3, 4
+RSV_PC_CPR_FP, RSV_PC_CPR_FPF, RSV_PC_CPR_FFPF = 5, 6, 7
 RSV_GMRES, RSV_BICGSTAB, RSV_FGMRES = 0, 1, 2
 RSV_PREC_FP64, RSV_PREC_MIXED = 0, 1
 PC_TYPES = {"none": RSV_PC_NONE, "bjacobi": RSV_PC_BJACOBI, "bilu0": RSV_PC_BILU0, "cpr": RSV_PC_CPR,
-            "cpr_learned": RSV_PC_CPR_LEARNED}
+            "cpr_learned": RSV_PC_CPR_LEARNED, "cpr_fp": RSV_PC_CPR_FP, "cpr_fpf": RSV_PC_CPR_FPF,
+            "cpr_ffpf": RSV_PC_CPR_FFPF}
 SOLVERS = {"gmres": RSV_GMRES, "bicgstab": RSV_BICGSTAB, "fgmres": RSV_FGMRES}
 
 

@@ -192,6 +192,18 @@ cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, con
                       int *status, unsigned long long timeout_ns);
 template <typename T>
 cudaError_t cpr_restrict(const rsv_mat *A, const Cpr &P, const T *f, const int *done);
+// The CPR stage orders: `stages` spells one, 'F' (full: block ILU(0)) or 'P' (pressure:
+// Pi_p V-cycle Pi_r) per stage; the first acts on f, every later one on f - A x and adds to x.
+template <typename T>
+cudaError_t cpr_apply_order(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const char *stages, const T *f,
+                            T *x, const int *done, int *status, unsigned long long timeout_ns);
+inline bool is_cpr_type(int pc) {
+    return pc == RSV_PC_CPR || pc == RSV_PC_CPR_LEARNED || pc == RSV_PC_CPR_FP || pc == RSV_PC_CPR_FPF ||
+           pc == RSV_PC_CPR_FFPF;
+}
+inline const char *cpr_stages(int pc) {
+    return pc == RSV_PC_CPR_FP ? "FP" : pc == RSV_PC_CPR_FPF ? "FPF" : pc == RSV_PC_CPR_FFPF ? "FFPF" : "PF";
+}
 template <typename T>
 cudaError_t cpr_pressure_vcycle(const rsv_mat *A, const Cpr &P, const int *gate);
 template <typename T>

@@ -319,6 +319,15 @@ __global__ void prolong_pressure_kernel(int64_t nb, const T *__restrict__ p, con
     r[3 * c + 2] = f[3 * c + 2];
 }
 
+// x_c += (p_c, 0, 0): a pressure-stage correction added to the iterate
+template <typename T>
+__global__ void prolong_add_pressure_kernel(int64_t nb, const T *__restrict__ p, T *__restrict__ x, const int *done) {
+    if (gated(done)) return;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nb) return;
+    x[3 * c] += p[c];
+}
+
 template <typename T>
 __global__ void add_kernel(int64_t n, const T *__restrict__ z, T *__restrict__ x, const int *done) {
     if (gated(done)) return;
@@ -487,6 +496,50 @@ cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, con
     return e;
 }
 
+// The CPR orders of Section "CPR-like preconditioners" (Algorithms CPR-FP, CPR-PF,
+// CPR-FPF, CPR-FFPF) as a string of stages.  The first stage writes x from f;
+// every later stage forms r = f - A x (a copy of f and one SpMV) and adds its
+// correction: F adds ILU0^{-1} r, P adds Pi_p V-cycle(Pi_r r).
+template <typename T>
+cudaError_t cpr_apply_order(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const char *stages, const T *f,
+                            T *x, const int *done, int *status, unsigned long long timeout_ns) {
+    cudaStream_t st = A->stream;
+    const int64_t nb = A->nb;
+    T *r = (T *)P.r, *z = (T *)P.z;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; stages[q] && e == cudaSuccess; ++q) {
+        const T *src = f;
+        if (q > 0) {
+            e = cudaMemcpyAsync(r, f, sizeof(T) * 3 * nb, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
+                                     : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
+            src = r;
+        }
+        if (e != cudaSuccess) break;
+        if (stages[q] == 'F') {
+            e = launch_ilu_apply_tiles<T>(A, tiles, src, q == 0 ? x : z, done, status, timeout_ns);
+            if (e == cudaSuccess && q > 0) {
+                count_launches(1);
+                add_kernel<T><<<blocks(3 * nb), 256, 0, st>>>(3 * nb, z, x, done);
+                e = cudaGetLastError();
+            }
+        } else {
+            e = cpr_restrict<T>(A, P, src, done);
+            if (e == cudaSuccess) e = vcycle<T>(P, 0, st, done);
+            if (e == cudaSuccess) {
+                count_launches(1);
+                if (q == 0)
+                    prolong_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.x[0], f, x, r, done);
+                else
+                    prolong_add_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.x[0], x, done);
+                e = cudaGetLastError();
+            }
+        }
+    }
+    return e;
+}
+
 template <typename T>
 cudaError_t cpr_vcycle(const rsv_mat *A, const Cpr &P, const T *b, T *x) {
     const int64_t n = A->nb;
@@ -500,6 +553,10 @@ template cudaError_t cpr_apply<double>(const rsv_mat *, const Cpr &, const IluTi
                                        const int *, int *, unsigned long long);
 template cudaError_t cpr_apply<float>(const rsv_mat *, const Cpr &, const IluTiles &, const float *, float *,
                                       const int *, int *, unsigned long long);
+template cudaError_t cpr_apply_order<double>(const rsv_mat *, const Cpr &, const IluTiles &, const char *,
+                                             const double *, double *, const int *, int *, unsigned long long);
+template cudaError_t cpr_apply_order<float>(const rsv_mat *, const Cpr &, const IluTiles &, const char *,
+                                            const float *, float *, const int *, int *, unsigned long long);
 template cudaError_t cpr_vcycle<double>(const rsv_mat *, const Cpr &, const double *, double *);
 template cudaError_t cpr_restrict<double>(const rsv_mat *, const Cpr &, const double *, const int *);
 template cudaError_t cpr_pressure_vcycle<double>(const rsv_mat *, const Cpr &, const int *);

@@ -527,10 +527,10 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
 void rsv_solver_destroy(rsv_solver *s) { solver_free(s); }
 
 rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params) {
-    if (!s || pc_type < RSV_PC_NONE || pc_type > RSV_PC_CPR_LEARNED) return RSV_EINVAL;
+    if (!s || pc_type < RSV_PC_NONE || pc_type > RSV_PC_CPR_FFPF) return RSV_EINVAL;
     if (pc_type == RSV_PC_CPR_LEARNED && (s->mixed || s->p.solver != RSV_FGMRES)) return RSV_ENOTSUP;
     if (pc_type == RSV_PC_CPR_LEARNED && !s->unet) return RSV_EINVAL;
-    const bool cpr = pc_type == RSV_PC_CPR || pc_type == RSV_PC_CPR_LEARNED;
+    const bool cpr = is_cpr_type(pc_type);
     rsv_pc_params pcp;
     rsv_pc_params_default(&pcp);
     if (params) pcp = *params;
@@ -594,7 +594,7 @@ rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z) {
 }
 
 rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, double *a7_host) {
-    if (!s || (s->pc_type != RSV_PC_CPR && s->pc_type != RSV_PC_CPR_LEARNED)) return RSV_EINVAL;
+    if (!s || !is_cpr_type(s->pc_type)) return RSV_EINVAL;
     const Cpr &P = s->cpr;
     if (nlev) *nlev = P.nlev;
     if (dims)
@@ -621,7 +621,7 @@ rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, dou
 }
 
 rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x) {
-    if (!s || !b || !x || b == x || (s->pc_type != RSV_PC_CPR && s->pc_type != RSV_PC_CPR_LEARNED) || s->mixed)
+    if (!s || !b || !x || b == x || !is_cpr_type(s->pc_type) || s->mixed)
         return RSV_EINVAL;
     RSV_CUDA_TRY(cpr_vcycle<double>(s->A, s->cpr, b, x));
     return RSV_OK;

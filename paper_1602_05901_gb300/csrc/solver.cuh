@@ -90,6 +90,11 @@ inline cudaError_t pc_apply(rsv_solver *s, const T *r, T *z, const int *done) {
     case RSV_PC_CPR_LEARNED:
         if (sizeof(T) == 8) return learned_cpr_apply(s, (const double *)r, (double *)z, done);
         return cudaErrorInvalidValue;
+    case RSV_PC_CPR_FP:
+    case RSV_PC_CPR_FPF:
+    case RSV_PC_CPR_FFPF:
+        return cpr_apply_order<T>(s->A, s->cpr, s->tiles, cpr_stages(s->pc_type), r, z, done, &s->ds->status,
+                                  (unsigned long long)s->p.watchdog * 1000ull);
     }
     return cudaErrorInvalidValue;
 }

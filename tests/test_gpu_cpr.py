@@ -142,3 +142,66 @@ def test_cpr_mid_full_size(rsv, torch):
         relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(
             p.b)
         assert relres <= 1e-8
+
+
+# ---- the other stage orders of Section "CPR-like preconditioners" (FP, FPF, FFPF)
+
+ORDERS = ["cpr_fp", "cpr_fpf", "cpr_ffpf"]
+
+
+def _setup_order(rsv, p, pc, precision="fp64"):
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, precision=precision)
+    s.setup(pc)
+    return A, s
+
+
+@pytest.mark.parametrize("pc", ORDERS)
+@pytest.mark.parametrize("dims", [(20, 20, 10), (13, 7, 5), (1, 1, 1), (40, 24, 16)])
+def test_cpr_order_apply_matches_oracle(rsv, torch, pc, dims):
+    p = synth.make_problem(*dims, seed=58)
+    A, s = _setup_order(rsv, p, pc)
+    o = oracle.System.from_problem(p, pc=pc)
+    f = np.random.default_rng(59).standard_normal(p.n)
+    st, z_or = o.pc_apply(f)
+    assert st == 0
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+
+
+@pytest.mark.parametrize("pc", ORDERS)
+def test_cpr_order_apply_fp32_matches_oracle(rsv, torch, pc):
+    p = synth.make_problem(33, 17, 9, seed=60)
+    A, s = _setup_order(rsv, p, pc, precision="mixed")
+    of = oracle.System.from_problem(p, pc=pc, float_round=True)
+    f = np.random.default_rng(61).standard_normal(p.n).astype(np.float32)
+    _, z_or = of.pc_apply(f.astype(np.float64))
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("pc", ORDERS)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cpr_order_gmres_solve(rsv, torch, pc, precision):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A, _ = _setup_order(rsv, p, "none")
+    s = rsv.Solver(A, solver="gmres", precision=precision, maxit=4000)
+    s.setup(pc)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_OK, (st, info)
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
+    if precision == "fp64":
+        o = oracle.System.from_problem(p, pc=pc)
+        ost, _, oinfo = o.gmres(p.b, maxit=4000)
+        assert ost == 0 and abs(info["iters"] - oinfo["iters"]) <= max(2, 0.1 * oinfo["iters"]), (info, oinfo)
