@@ -323,6 +323,50 @@ def run_unet(args):
     return 0
 
 
+def run_cpr_orders(args):
+    """The four CPR stage orders (PF, FP, FPF, FFPF) as GMRES(30) preconditioners on the
+    benchmark workload, FP64 and mixed precision: setup + solve to rtol 1e-8, CUDA events
+    on the solver stream, `--warmup` untimed and `--steps` timed solves per combination."""
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    p = synth.workload(WORKLOAD)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    A = rsv.Matrix(p.nx, p.ny, p.nz, stream=stream)
+    A.set_values(torch.from_numpy(p.vals).to(dev))
+    b = torch.from_numpy(p.b).to(dev)
+    x = torch.zeros_like(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for precision in ("fp64", "mixed"):
+        for pc in ("cpr", "cpr_fp", "cpr_fpf", "cpr_ffpf"):
+            s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision=precision)
+
+            def step():
+                s.setup(pc)
+                x.zero_()
+                st, info = s.solve(b, x)
+                if st != rsv.RSV_OK:
+                    raise RuntimeError(f"{pc} {precision}: {rsv.status_string(st)} {info}")
+                return info
+            for _ in range(max(1, args.warmup)):
+                step()
+            torch.cuda.synchronize(dev)
+            e0.record()
+            infos = [step() for _ in range(args.steps)]
+            e1.record()
+            torch.cuda.synchronize(dev)
+            rows.append({"pc": pc, "precision": precision, "ms": round(e0.elapsed_time(e1) / args.steps, 3),
+                         "iters": infos[-1]["iters"], "outer_iters": infos[-1].get("outer_iters", 0),
+                         "true_relres": infos[-1]["true_relres"]})
+    print(json.dumps({"mode": "cpr-orders", "workload": WORKLOAD, "solver": "gmres(30)", "rtol": 1e-8,
+                      "steps": args.steps, "warmup": args.warmup, "results": rows}))
+    return 0
+
+
 def run_learned(args):
     """The learned pressure stage on the 128x128x64 channelised workload.
 
@@ -489,7 +533,8 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=20, help="learned mode: epochs")
     ap.add_argument("--learned-eval", type=int, default=4, help="learned mode: unseen evaluation seeds")
     ap.add_argument("--mode", default="bench",
-                    choices=["bench", "profile-solve", "profile-kernels", "profile-conv", "batch", "unet", "learned"],
+                    choices=["bench", "profile-solve", "profile-kernels", "profile-conv", "batch", "unet", "learned",
+                             "cpr-orders"],
                     help="profile-solve: one short mixed GMRES(30)+BILU0 solve (60 inner iterations) on the "
                          "benchmark workload, for an ncu launch list; profile-kernels: set up the benchmark "
                          "workload and run each hot kernel (FP64/FP32 SpMV, FP32/FP64 ILU(0) apply) three times, "
@@ -503,6 +548,8 @@ def main():
         return run_unet(args)
     if args.mode == "profile-conv":
         return run_profile_conv()
+    if args.mode == "cpr-orders":
+        return run_cpr_orders(args)
     if args.mode == "learned":
         return run_learned(args)
     if args.mode != "bench":
