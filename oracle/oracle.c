@@ -251,19 +251,36 @@ static int stencil_slot(int di, int dj, int dk) {
  * experiments): with D = A_ii, w_i = (1, -D01/D11, -D02/D22).  The pressure
  * matrix is the pressure column of the weighted block rows,
  * (A_pp)_ij = sum_r w_i[r] A_ij[r][0], stored as a seven-point stencil. */
-int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v,
-                double *w, double *a7) {
+/* Decoupling weights and the pressure operator of CPR.  decoupling 0: the
+ * quasi-IMPES reading w_c = (1, -D01/D11, -D02/D22); 1: ABF (alternate block
+ * factorization, Section "Numerical experiments" names it beside quasi-IMPES),
+ * which premultiplies each block row by D^{-1}, so w_c is the first row of
+ * D^{-1} = adj(D) / det(D) (D = A_cc).  Either way A_pp(c, l) = w_c . A_cl[:, 0]. */
+int or_decouple_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v, int decoupling,
+                      double *w, double *a7) {
     int nb = nx * ny * nz;
     memset(a7, 0, sizeof(double) * 7 * (size_t)nb);
     for (int c = 0; c < nb; ++c) {
         int32_t pd = find_block(rp, ci, c, c);
         if (pd < 0) return OR_EINVAL;
         const double *d = v + 9 * (int64_t)pd;
-        if (!(fabs(d[4]) > 1e-300) || !(fabs(d[8]) > 1e-300)) return OR_ESINGULAR;
         double *wc = w + 3 * (int64_t)c;
-        wc[0] = 1.0;
-        wc[1] = -d[1] / d[4];
-        wc[2] = -d[2] / d[8];
+        if (decoupling == 1) {
+            /* first row of the adjugate: cofactors of the first column */
+            const double c0 = d[4] * d[8] - d[5] * d[7];
+            const double c1 = d[5] * d[6] - d[3] * d[8];
+            const double c2 = d[3] * d[7] - d[4] * d[6];
+            const double det = d[0] * c0 + d[1] * c1 + d[2] * c2;
+            if (!(fabs(det) > 1e-300)) return OR_ESINGULAR;
+            wc[0] = c0 / det;
+            wc[1] = (d[2] * d[7] - d[1] * d[8]) / det;
+            wc[2] = (d[1] * d[5] - d[2] * d[4]) / det;
+        } else {
+            if (!(fabs(d[4]) > 1e-300) || !(fabs(d[8]) > 1e-300)) return OR_ESINGULAR;
+            wc[0] = 1.0;
+            wc[1] = -d[1] / d[4];
+            wc[2] = -d[2] / d[8];
+        }
         int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
         for (int32_t p = rp[c]; p < rp[c + 1]; ++p) {
             int o = ci[p];
@@ -275,6 +292,10 @@ int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, co
         }
     }
     return OR_OK;
+}
+
+int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v, double *w, double *a7) {
+    return or_decouple_setup(nx, ny, nz, rp, ci, v, 0, w, a7);
 }
 
 /* Pi_r with the decoupling folded in: p_i = w_i . r_i. */
@@ -503,8 +524,9 @@ void or_destroy(or_system *s) {
 /* Preconditioner setup.  pc: 0 none, 1 block Jacobi, 2 block ILU(0),
  * 3 CPR-PF (quasi-IMPES + GMG V-cycle pressure stage, then block ILU(0)),
  * 5 CPR-FP, 6 CPR-FPF, 7 CPR-FFPF (the same two stages in the other orders).
- * float_round != 0 rounds the stored factors to float after setup. */
-int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweeps, int float_round) {
+ * float_round != 0 rounds the stored factors to float after setup; decoupling:
+ * 0 quasi-IMPES, 1 ABF (CPR only). */
+int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweeps, int float_round, int decoupling) {
     int nb = s->nb;
     s->pc = pc;
     int st = OR_OK;
@@ -528,7 +550,7 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
     if (is_cpr(pc)) {
         s->w = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
         s->a7 = (double *)malloc(sizeof(double) * 7 * (size_t)nb);
-        st = or_qi_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, s->w, s->a7);
+        st = or_decouple_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, decoupling, s->w, s->a7);
         if (st) return st;
         if (float_round) {
             for (size_t q = 0; q < 3 * (size_t)nb; ++q) s->w[q] = round_f32(s->w[q]);

@@ -305,6 +305,46 @@ def test_cpr_apply_matches_dense_two_stage_formula():
     assert st == 0 and np.allclose(x, ref, rtol=1e-9, atol=1e-12)
 
 
+@pytest.mark.parametrize("dims", [(4, 3, 2), (7, 5, 3)])
+def test_abf_weights_are_first_row_of_diagonal_block_inverse(dims):
+    """ABF premultiplies each block row by the inverse of its diagonal block, so the
+    pressure weights are the first row of D^{-1} (checked against numpy's inverse),
+    every pressure-matrix diagonal entry is exactly (D^{-1} D)_00 = 1 up to rounding,
+    and A_pp is the weighted product W A P."""
+    p = _prob(dims, seed=22)
+    nx, ny, nz = dims
+    st, w, a7 = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "abf")
+    assert st == 0
+    for c in range(p.nb):
+        q = next(q for q in range(p.row_ptr[c], p.row_ptr[c + 1]) if p.col_idx[q] == c)
+        assert np.allclose(w[c], np.linalg.inv(p.vals[q])[0], rtol=1e-12, atol=1e-14 * np.abs(w[c]).max())
+    assert np.allclose(a7[:, 3], 1.0, rtol=0, atol=1e-12)
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    W = np.zeros((p.nb, p.n))
+    for c in range(p.nb):
+        W[c, 3 * c:3 * c + 3] = w[c]
+    assert np.allclose(stencil_to_dense(nx, ny, nz, a7), W @ A[:, 0::3], rtol=1e-12, atol=1e-12)
+    # the quasi-IMPES reading is unchanged by the switch
+    st, wq, _ = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "qi")
+    st2, wq2, _ = oracle.qi_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals)
+    assert st == 0 and st2 == 0 and np.array_equal(wq, wq2)
+
+
+def test_abf_pressure_stage_exact_on_component_decoupled_system():
+    """Diagonal blocks: ABF weights are (1/D00, 0, 0), and the pressure stage with an
+    exact coarse solve returns the exact pressure."""
+    nx, ny, nz = 4, 3, 2
+    rp, ci, vals = kron_bsr(nx, ny, nz, np.diag([1.0, 0.5, 0.3]), np.diag([0.2, 0.4, 0.6]),
+                            trans=lambda r, c: 1.0 + ((r * 7 + c * 3) % 5))
+    s = oracle.System(nx, ny, nz, rp, ci, vals, pc="cpr", gmg_levels=1, decoupling="abf")
+    assert s.setup_status == 0
+    A = bsr_to_dense(rp, ci, vals)
+    f = np.random.default_rng(23).standard_normal(3 * nx * ny * nz)
+    st, x = s.pc_apply(f)
+    assert st == 0
+    assert np.allclose(x[0::3], np.linalg.solve(A[0::3, 0::3], f[0::3]), rtol=1e-10)
+
+
 CPR_ORDERS = [("cpr", "PF"), ("cpr_fp", "FP"), ("cpr_fpf", "FPF"), ("cpr_ffpf", "FFPF")]
 
 
