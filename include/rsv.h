@@ -106,11 +106,18 @@ typedef struct {
 
 /* Preconditioner parameters.  GMG defaults follow the paper's AMG defaults
  * (one V-cycle, at most 6 levels, 2 relaxation sweeps; Section "Algebraic
- * Multigrid Methods", default-parameter figure). */
+ * Multigrid Methods", default-parameter figure).  decoupling selects how the CPR
+ * orders weight the three equations of a cell into its pressure equation
+ * (Section "Numerical experiments" names quasi-IMPES and ABF):
+ *   0  quasi-IMPES: w_c = (1, -D01/D11, -D02/D22), D = A_cc (default);
+ *   1  ABF: w_c = first row of D^{-1} (each block row premultiplied by D^{-1});
+ *      RSV_ESINGULAR at setup when |det D| <= 1e-300.
+ * The pressure operator is A_pp(c, l) = w_c . A_cl[:, 0] either way. */
 typedef struct {
     int gmg_max_levels;    /* <= 8 */
     int gmg_max_coarse;    /* stop coarsening at or below this many cells */
     int gmg_sweeps;        /* red-black Gauss-Seidel sweeps before and after */
+    int decoupling;        /* 0 quasi-IMPES, 1 ABF */
 } rsv_pc_params;
 
 /* Filled by rsv_solve. */

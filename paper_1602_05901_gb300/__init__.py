@@ -46,7 +46,8 @@ class rsv_solver_params(ctypes.Structure):
 
 
 class rsv_pc_params(ctypes.Structure):
-    _fields_ = [("gmg_max_levels", ctypes.c_int), ("gmg_max_coarse", ctypes.c_int), ("gmg_sweeps", ctypes.c_int)]
+    _fields_ = [("gmg_max_levels", ctypes.c_int), ("gmg_max_coarse", ctypes.c_int), ("gmg_sweeps", ctypes.c_int),
+                ("decoupling", ctypes.c_int)]
 
 
 class rsv_solve_info(ctypes.Structure):
@@ -163,10 +164,14 @@ def solver_params(solver="gmres", restart=30, rtol=1e-8, atol=0.0, btol=1e-30, m
     return p
 
 
-def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2):
+DECOUPLING = {"qi": 0, "abf": 1}
+
+
+def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2, decoupling="qi"):
     p = rsv_pc_params()
     _lib.rsv_pc_params_default(ctypes.byref(p))
     p.gmg_max_levels, p.gmg_max_coarse, p.gmg_sweeps = gmg_max_levels, gmg_max_coarse, gmg_sweeps
+    p.decoupling = DECOUPLING[decoupling] if isinstance(decoupling, str) else decoupling
     return p
 
 

@@ -53,6 +53,7 @@ void rsv_pc_params_default(rsv_pc_params *p) {
     p->gmg_max_levels = 6;
     p->gmg_max_coarse = 512;
     p->gmg_sweeps = 2;
+    p->decoupling = 0;
 }
 
 const char *rsv_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }

@@ -185,7 +185,9 @@ cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const T *dinv, const T 
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status);
 
 // ---- implemented in cpr.cu
-cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, Cpr *P, int *status);
+// decoupling: 0 quasi-IMPES, 1 ABF (rsv_pc_params)
+cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling, Cpr *P,
+                      int *status);
 void free_cpr(Cpr *P);
 template <typename T>
 cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,

@@ -51,7 +51,7 @@ __device__ __forceinline__ int slot_of(int di, int dj, int dk) {
 
 // Quasi-IMPES weights and the pressure stencil of the block row of cell c.
 template <typename Tv>
-__global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *__restrict__ v,
+__global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *__restrict__ v, int decoupling,
                                 double *__restrict__ w, double *__restrict__ a7, int *status) {
     const int64_t n = g.n();
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -61,13 +61,31 @@ __global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *
     const bool has[7] = {k > 0, j > 0, i > 0, true, i < g.nx - 1, j < g.ny - 1, k < g.nz - 1};
     int slot_pos[7], q = 0;
     for (int s = 0; s < 7; ++s) slot_pos[s] = has[s] ? q++ : -1;
-    const Tv *d = v + 9 * ((int64_t)rp[c] + slot_pos[3]);
-    const double d11 = (double)d[4], d22 = (double)d[8];
-    if (!(fabs(d11) > 1e-300) || !(fabs(d22) > 1e-300)) {
-        atomicCAS(status, 0, (int)RSV_ESINGULAR);
-        return;
+    const Tv *dv = v + 9 * ((int64_t)rp[c] + slot_pos[3]);
+    double d[9];
+    for (int q = 0; q < 9; ++q) d[q] = (double)dv[q];
+    double w0, w1, w2;
+    if (decoupling == 1) {
+        // ABF: the first row of D^{-1} = adj(D) / det(D), from the cofactors of D's first column
+        const double c0 = d[4] * d[8] - d[5] * d[7];
+        const double det = d[0] * c0 + d[1] * (d[5] * d[6] - d[3] * d[8]) + d[2] * (d[3] * d[7] - d[4] * d[6]);
+        if (!(fabs(det) > 1e-300)) {
+            atomicCAS(status, 0, (int)RSV_ESINGULAR);
+            return;
+        }
+        w0 = c0 / det;
+        w1 = (d[2] * d[7] - d[1] * d[8]) / det;
+        w2 = (d[1] * d[5] - d[2] * d[4]) / det;
+    } else {
+        // quasi-IMPES: keep the pressure equation, cancel the diagonal coupling of the other two
+        if (!(fabs(d[4]) > 1e-300) || !(fabs(d[8]) > 1e-300)) {
+            atomicCAS(status, 0, (int)RSV_ESINGULAR);
+            return;
+        }
+        w0 = 1.0;
+        w1 = -d[1] / d[4];
+        w2 = -d[2] / d[8];
     }
-    const double w0 = 1.0, w1 = -(double)d[1] / d11, w2 = -(double)d[2] / d22;
     w[3 * c] = w0;
     w[3 * c + 1] = w1;
     w[3 * c + 2] = w2;
@@ -349,8 +367,8 @@ void free_cpr(Cpr *P) {
     *P = Cpr();
 }
 
-cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, Cpr *P,
-                      int *status) {
+cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling,
+                      Cpr *P, int *status) {
     free_cpr(P);
     cudaStream_t st = A->stream;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
@@ -395,9 +413,11 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
     G3 g0{A->nx, A->ny, A->nz};
     count_launches(1);
     if (mixed)
-        qi_setup_kernel<float><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v32, P->w64, P->a7[0], status);
+        qi_setup_kernel<float><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v32, decoupling, P->w64, P->a7[0],
+                                                           status);
     else
-        qi_setup_kernel<double><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v, P->w64, P->a7[0], status);
+        qi_setup_kernel<double><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v, decoupling, P->w64, P->a7[0],
+                                                            status);
     for (int l = 0; l + 1 < nl; ++l) {
         G3 f{P->dims[l][0], P->dims[l][1], P->dims[l][2]}, c{P->dims[l + 1][0], P->dims[l + 1][1], P->dims[l + 1][2]};
         count_launches(1);

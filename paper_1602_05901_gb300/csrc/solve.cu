@@ -535,7 +535,8 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     rsv_pc_params_default(&pcp);
     if (params) pcp = *params;
     if (pcp.gmg_max_levels < 1 || pcp.gmg_max_levels > kMaxLevels || pcp.gmg_max_coarse < 1 ||
-        pcp.gmg_max_coarse > 1024 || pcp.gmg_sweeps < 0 || pcp.gmg_sweeps > 16)
+        pcp.gmg_max_coarse > 1024 || pcp.gmg_sweeps < 0 || pcp.gmg_sweeps > 16 || pcp.decoupling < 0 ||
+        pcp.decoupling > 1)
         return RSV_EINVAL;
     rsv_mat *A = s->A;
     s->pc_type = -1;
@@ -558,8 +559,8 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     }
     if (cpr && A->nsys > 1) return RSV_ENOTSUP;
     if (cpr)
-        RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, &s->cpr,
-                               &s->ds->status));
+        RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, pcp.decoupling,
+                               &s->cpr, &s->ds->status));
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
     RSV_TRY(read_status(s, &status));

@@ -205,3 +205,56 @@ def test_cpr_order_gmres_solve(rsv, torch, pc, precision):
         o = oracle.System.from_problem(p, pc=pc)
         ost, _, oinfo = o.gmres(p.b, maxit=4000)
         assert ost == 0 and abs(info["iters"] - oinfo["iters"]) <= max(2, 0.1 * oinfo["iters"]), (info, oinfo)
+
+
+# ---- ABF decoupling (rsv_pc_params.decoupling = 1)
+
+@pytest.mark.parametrize("pc", ["cpr", "cpr_fpf"])
+@pytest.mark.parametrize("dims", [(20, 20, 10), (13, 7, 5), (1, 1, 1)])
+def test_abf_cpr_apply_matches_oracle(rsv, torch, pc, dims):
+    p = synth.make_problem(*dims, seed=62)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A)
+    s.setup(pc, decoupling="abf")
+    o = oracle.System.from_problem(p, pc=pc, decoupling="abf")
+    _, w_or, a7_or = o.factors()
+    levels, w, a7 = s.cpr_info()
+    assert np.allclose(w, w_or, rtol=1e-12, atol=1e-14 * np.abs(w_or).max())
+    f = np.random.default_rng(63).standard_normal(p.n)
+    st, z_or = o.pc_apply(f)
+    assert st == 0
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_abf_cpr_fpf_gmres_solve(rsv, torch, precision):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, solver="gmres", precision=precision, maxit=4000)
+    s.setup("cpr_fpf", decoupling="abf")
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_OK, (st, info)
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
+    if precision == "fp64":
+        o = oracle.System.from_problem(p, pc="cpr_fpf", decoupling="abf")
+        ost, _, oinfo = o.gmres(p.b, maxit=4000)
+        assert ost == 0 and abs(info["iters"] - oinfo["iters"]) <= max(2, 0.1 * oinfo["iters"]), (info, oinfo)
+
+
+def test_decoupling_argument_checked(rsv, torch):
+    p = synth.make_problem(4, 3, 2, seed=0)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A)
+    with pytest.raises(rsv.RsvError) as e:
+        s.setup("cpr", decoupling=2)
+    assert e.value.status == rsv.RSV_EINVAL
