@@ -324,9 +324,10 @@ def run_unet(args):
 
 
 def run_cpr_orders(args):
-    """The four CPR stage orders (PF, FP, FPF, FFPF) as GMRES(30) preconditioners on the
-    benchmark workload, FP64 and mixed precision: setup + solve to rtol 1e-8, CUDA events
-    on the solver stream, `--warmup` untimed and `--steps` timed solves per combination."""
+    """The four CPR stage orders (PF, FP, FPF, FFPF) with quasi-IMPES and ABF decoupling as
+    GMRES(30) preconditioners on the benchmark workload, FP64 and mixed precision: setup +
+    solve to rtol 1e-8, CUDA events on the solver stream, `--warmup` untimed and `--steps`
+    timed solves per combination."""
     import torch
 
     import paper_1602_05901_gb300 as rsv
@@ -341,27 +342,29 @@ def run_cpr_orders(args):
     x = torch.zeros_like(b)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rows = []
-    for precision in ("fp64", "mixed"):
-        for pc in ("cpr", "cpr_fp", "cpr_fpf", "cpr_ffpf"):
-            s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision=precision)
+    combos = [(d, pr, pc) for d in ("qi", "abf") for pr in ("fp64", "mixed")
+              for pc in ("cpr", "cpr_fp", "cpr_fpf", "cpr_ffpf")]
+    for decoupling, precision, pc in combos:
+        s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision=precision)
 
-            def step():
-                s.setup(pc)
-                x.zero_()
-                st, info = s.solve(b, x)
-                if st != rsv.RSV_OK:
-                    raise RuntimeError(f"{pc} {precision}: {rsv.status_string(st)} {info}")
-                return info
-            for _ in range(max(1, args.warmup)):
-                step()
-            torch.cuda.synchronize(dev)
-            e0.record()
-            infos = [step() for _ in range(args.steps)]
-            e1.record()
-            torch.cuda.synchronize(dev)
-            rows.append({"pc": pc, "precision": precision, "ms": round(e0.elapsed_time(e1) / args.steps, 3),
-                         "iters": infos[-1]["iters"], "outer_iters": infos[-1].get("outer_iters", 0),
-                         "true_relres": infos[-1]["true_relres"]})
+        def step():
+            s.setup(pc, decoupling=decoupling)
+            x.zero_()
+            st, info = s.solve(b, x)
+            if st != rsv.RSV_OK:
+                raise RuntimeError(f"{pc} {precision}: {rsv.status_string(st)} {info}")
+            return info
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        infos = [step() for _ in range(args.steps)]
+        e1.record()
+        torch.cuda.synchronize(dev)
+        rows.append({"pc": pc, "decoupling": decoupling, "precision": precision,
+                     "ms": round(e0.elapsed_time(e1) / args.steps, 3),
+                     "iters": infos[-1]["iters"], "outer_iters": infos[-1].get("outer_iters", 0),
+                     "true_relres": infos[-1]["true_relres"]})
     print(json.dumps({"mode": "cpr-orders", "workload": WORKLOAD, "solver": "gmres(30)", "rtol": 1e-8,
                       "steps": args.steps, "warmup": args.warmup, "results": rows}))
     return 0
