@@ -71,3 +71,34 @@ def test_unet_and_conv_argument_checks_without_gpu(lib):
     assert rsv.rsv_unet_create(None, 64, 16, 8, 32, 3, None) == rsv.RSV_EINVAL
     assert rsv.rsv_unet_apply(None, None, None, None) == rsv.RSV_EINVAL
     assert rsv.rsv_unet_train_step(None, None, None, None, 1e-3, None) == rsv.RSV_EINVAL
+
+
+def _header_enum(name):
+    """{member: value} of a `typedef enum {...} name;` in include/rsv.h."""
+    text = open(HEADERS[0]).read()
+    body = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return {m: int(v) for m, v in re.findall(r"(RSV_\w+)\s*=\s*(\d+)", body)}
+
+
+def _header_struct_fields(name):
+    text = open(HEADERS[0]).read()
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"\b(\w+)\s*;", body)
+
+
+def test_binding_constants_and_structs_match_the_header(lib):
+    """The binding's preconditioner and status codes and its ctypes mirror of
+    rsv_pc_params follow the header (field order and count: the struct is passed by pointer)."""
+    import paper_1602_05901_gb300 as rsv
+    pcs = _header_enum("rsv_pc_type")
+    assert pcs == {n: getattr(rsv, n) for n in pcs}
+    assert set(rsv.PC_TYPES.values()) == set(pcs.values())
+    statuses = _header_enum("rsv_status")
+    assert all(getattr(rsv, n) == v for n, v in statuses.items())
+    fields = _header_struct_fields("rsv_pc_params")
+    assert fields == [f for f, _ in rsv.rsv_pc_params._fields_]
+    p = rsv.pc_params()
+    assert (p.gmg_max_levels, p.gmg_max_coarse, p.gmg_sweeps, p.decoupling) == (6, 512, 2, 0)
+    assert rsv.pc_params(decoupling="abf").decoupling == 1
