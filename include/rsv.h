@@ -218,7 +218,12 @@ RSV_API void rsv_solver_destroy(rsv_solver *s);
  *  CPR:   two-stage (Section "CPR-like Preconditioners", CPR-PF): quasi-IMPES
  *         pressure restriction, geometric-multigrid V-cycle on the pressure
  *         matrix (Section "Algebraic Multigrid Methods"), then block ILU(0).
- * params may be NULL (defaults). */
+ *  CPR_FP, CPR_FPF, CPR_FFPF: the same stages in the paper's other orders
+ *         (see rsv_pc_type).  params->decoupling selects quasi-IMPES or ABF
+ *         weights for every CPR type, CPR_LEARNED included (a network trained on
+ *         pressure samples of one decoupling expects that decoupling).
+ *         RSV_ENOTSUP for a batch matrix (more than one grid).
+ * params may be NULL (defaults); RSV_EINVAL for a parameter out of range. */
 RSV_API rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params);
 /* z = M^{-1} r with the current preconditioner of an FP64 solver; device
  * float64[3*nb]; r and z must not overlap.  Returns before the GPU work ends
@@ -227,9 +232,9 @@ RSV_API rsv_status rsv_precond_apply(rsv_solver *s, const double *r, double *z);
 /* Same in FP32 for a mixed-precision solver (its preconditioner is built on
  * the FP32-rounded matrix and stores FP32 factors); device float32[3*nb]. */
 RSV_API rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z);
-/* Inspect a CPR preconditioner (Section "CPR-like Preconditioners"): the
- * number of multigrid levels, their grid dimensions (int[3*nlev]: nx, ny, nz
- * per level, finest first), the quasi-IMPES weights (host float64[nb][3]) and
+/* Inspect a CPR preconditioner of any order (Section "CPR-like Preconditioners"):
+ * the number of multigrid levels, their grid dimensions (int[3*nlev]: nx, ny, nz
+ * per level, finest first), the decoupling weights (host float64[nb][3]) and
  * the seven-point pressure stencils of every level, finest first,
  * concatenated (host float64[sum_l cells_l][7], slots -z, -y, -x, centre, +x,
  * +y, +z).  Any output may be NULL.  Synchronises the stream. */
