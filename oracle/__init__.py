@@ -23,7 +23,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_variant = "serial"
 
 OK, EINVAL, ENOMEM, ESINGULAR, EBREAKDOWN, ENOCONV, ENAN = 0, 1, 2, 5, 6, 7, 9
 # "cpr" is CPR-PF (pressure stage, then full stage); the other orders follow the
@@ -33,23 +35,38 @@ DECOUPLING = {"qi": 0, "abf": 1}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it.
+    """Compile oracle.c into liboracle.so (sequential: the parity oracle) and
+    liboracle_omp.so (the same source with OpenMP: the CPU timing baseline).
 
     -ffp-contract=off keeps every a*b+c as two rounded operations, so the oracle
     rounds identically on x86-64 and AArch64 hosts.
     """
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, path)
     return _LIB_PATH
+
+
+def use_threads(threads: int) -> int:
+    """Route every later oracle call through the OpenMP build with `threads`
+    threads (threads <= 1: the sequential build).  Returns the thread count in
+    use.  Parity tests keep the sequential build; the benchmark's CPU baseline
+    uses this."""
+    global _lib, _variant
+    want = "omp" if threads > 1 else "serial"
+    if want != _variant:
+        _lib, _variant = None, want
+    return lib().or_set_threads(max(1, threads))
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB_PATH)
+        L = ctypes.CDLL(_OMP_PATH if _variant == "omp" else _LIB_PATH)
         P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
         sig = {
             "or_dot": (D, [I64, P, P]), "or_norm2": (D, [I64, P]),
@@ -71,6 +88,7 @@ def lib():
             "or_gmres": (I, [P, P, P, I, D, I, I, P]),
             "or_bicgstab": (I, [P, P, P, D, D, I, P]),
             "or_refine": (I, [P, P, P, P, I, I, D, D, I, I, P]),
+            "or_set_threads": (I, [I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

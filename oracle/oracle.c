@@ -27,6 +27,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_OK 0
 #define OR_EINVAL 1
 #define OR_ENOMEM 2
@@ -35,11 +39,27 @@
 #define OR_ENOCONV 7
 #define OR_ENAN 9
 
+/* Threads of the OpenMP build (the timing baseline); the plain build is
+ * sequential and returns 1.  The OpenMP build runs the independent loops
+ * (SpMV rows, vector updates, one colour of Gauss-Seidel, stencil products)
+ * in parallel; the triangular ILU(0) sweeps stay sequential in natural order.
+ * Only its dot products round differently (reduction order). */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------ BLAS-1 */
 
 /* alpha = <x, y>  (Algebraic Operations) */
 double or_dot(int64_t n, const double *x, const double *y) {
     double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
     for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
     return s;
 }
@@ -49,6 +69,7 @@ double or_norm2(int64_t n, const double *x) { return sqrt(or_dot(n, x, x)); }
 
 /* y = alpha x + beta y */
 static void axpby(int64_t n, double a, const double *x, double b, double *y) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) y[i] = a * x[i] + b * y[i];
 }
 
@@ -58,6 +79,7 @@ static void axpby(int64_t n, double a, const double *x, double b, double *y) {
  * Blocks are row-major; a row's blocks are summed in ascending column order. */
 int or_spmv(int nb, const int32_t *rp, const int32_t *ci, const double *v,
             double alpha, const double *x, double beta, double *y) {
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < nb; ++r) {
         double acc[3] = {0.0, 0.0, 0.0};
         for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
@@ -300,6 +322,7 @@ int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, co
 
 /* Pi_r with the decoupling folded in: p_i = w_i . r_i. */
 void or_restrict_pressure(int nb, const double *w, const double *r, double *p) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nb; ++i)
         p[i] = w[3 * (int64_t)i] * r[3 * (int64_t)i] + w[3 * (int64_t)i + 1] * r[3 * (int64_t)i + 1] +
                w[3 * (int64_t)i + 2] * r[3 * (int64_t)i + 2];
@@ -307,6 +330,7 @@ void or_restrict_pressure(int nb, const double *w, const double *r, double *p) {
 
 /* Pi_p: x_i = (p_i, 0, 0). */
 void or_prolong_pressure(int nb, const double *p, double *x) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < nb; ++i) {
         x[3 * (int64_t)i] = p[i];
         x[3 * (int64_t)i + 1] = 0.0;
@@ -317,6 +341,7 @@ void or_prolong_pressure(int nb, const double *p, double *x) {
 /* y = a7 x  for a seven-point stencil on an nx*ny*nz grid. */
 void or_stencil_apply(int nx, int ny, int nz, const double *a7, const double *x, double *y) {
     int nb = nx * ny * nz;
+#pragma omp parallel for schedule(static)
     for (int c = 0; c < nb; ++c) {
         int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
         double s = 0.0;
@@ -355,6 +380,8 @@ void or_gmg_coarsen(int nx, int ny, int nz, const double *a7, double *ac7) {
 /* One Gauss-Seidel sweep over the cells of one colour ((i+j+k) mod 2),
  * visiting them in natural order. */
 void or_gs_colour(int nx, int ny, int nz, const double *a7, const double *b, double *x, int colour) {
+    /* cells of one colour couple only to the other colour, so the k-planes are independent */
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -444,6 +471,7 @@ static int gmg_vcycle(or_gmg *g, int l) {
         or_gs_colour(nx, ny, nz, g->a7[l], g->b[l], g->x[l], 1);
     }
     or_stencil_apply(nx, ny, nz, g->a7[l], g->x[l], g->r[l]);
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < n; ++c) g->r[l][c] = g->b[l][c] - g->r[l][c];
     int cx = g->nx[l + 1], cy = g->ny[l + 1];
     memset(g->b[l + 1], 0, sizeof(double) * (size_t)cx * cy * g->nz[l + 1]);
@@ -454,6 +482,7 @@ static int gmg_vcycle(or_gmg *g, int l) {
                     g->r[l][(int64_t)nx * ny * k + (int64_t)nx * j + i];
     int st = gmg_vcycle(g, l + 1);
     if (st) return st;
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
@@ -683,6 +712,7 @@ int or_gmres(or_system *s, const double *b, double *x, int m, double rtol, int m
         if (beta <= tol) { st = OR_OK; break; }
         if (iters >= maxit) { st = OR_ENOCONV; break; }
         ++cycles;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; ++q) V[q] = w[q] / beta;
         memset(g, 0, sizeof(double) * (m + 1));
         g[0] = beta;
@@ -717,8 +747,10 @@ int or_gmres(or_system *s, const double *b, double *x, int m, double rtol, int m
             g[j] = cs[j] * g[j];
             jend = j + 1;
             int lucky = !(hn > 0.0);
-            if (!lucky)
+            if (!lucky) {
+#pragma omp parallel for schedule(static)
                 for (int64_t q = 0; q < n; ++q) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+            }
             if (fabs(g[j + 1]) <= tol || iters >= maxit || lucky) break;
         }
         for (int i = jend - 1; i >= 0; --i) {
@@ -783,6 +815,7 @@ int or_bicgstab(or_system *s, const double *b, double *x, double rtol, double bt
         if (!isfinite(rho1)) { st = OR_ENAN; break; }
         if (fabs(rho1) <= btol * rhn * rn) { st = OR_EBREAKDOWN; break; }
         double beta = (rho1 / rho) * (alpha / omega);
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
         int ps = or_pc_apply(s, p, ph);
         if (ps) { st = ps; break; }
@@ -790,6 +823,7 @@ int or_bicgstab(or_system *s, const double *b, double *x, double rtol, double bt
         double rv = or_dot(n, rh, v);
         if (fabs(rv) <= btol * rhn * or_norm2(n, v)) { st = OR_EBREAKDOWN; break; }
         alpha = rho1 / rv;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; ++q) sv[q] = r[q] - alpha * v[q];
         double sn = or_norm2(n, sv);
         if (sn <= tol) {
@@ -805,6 +839,7 @@ int or_bicgstab(or_system *s, const double *b, double *x, double rtol, double bt
         if (!(tt > 0.0)) { st = OR_EBREAKDOWN; break; }
         omega = ts / tt;
         if (fabs(omega) <= btol) { st = OR_EBREAKDOWN; break; }
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; ++q) {
             x[q] += alpha * ph[q] + omega * sh[q];
             r[q] = sv[q] - omega * t[q];

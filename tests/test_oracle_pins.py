@@ -492,3 +492,43 @@ def test_mixed_refinement_reaches_fp64_tolerance():
     A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
     assert st == 0 and info["outer"] >= 2
     assert np.linalg.norm(p.b - A @ x) <= 1e-8 * np.linalg.norm(p.b)
+
+
+def _true_relres_scipy(p, x):
+    """||b - A x|| / ||b|| with scipy's BSR product (independent of the oracle's SpMV)."""
+    import scipy.sparse as sp
+    A = sp.bsr_matrix((p.vals, p.col_idx, p.row_ptr), shape=(p.n, p.n))
+    return np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b)
+
+
+def test_refinement_last_step_runs_only_to_what_the_target_needs():
+    """The refinement's inner tolerance is inner_rtol relative to the current outer
+    residual, except that a step whose residual is within 1/inner_rtol of the target
+    runs only to max(inner_rtol, 0.5 tol / ||r||).  With an unrounded inner system
+    (inner solves in exact FP64) that gives exactly two outer steps and a final
+    residual between tol/100 and tol: a fixed 1e-5 would land near 1e-10."""
+    p = synth.workload("tiny_20x20x10")
+    outer = oracle.System.from_problem(p, pc="none")
+    exact_inner = oracle.System.from_problem(p, pc="bilu0", float_round=False)
+    st, x, info = oracle.refine(outer, exact_inner, p.b, solver="gmres", rtol=1e-8, inner_rtol=1e-5)
+    rel = _true_relres_scipy(p, x)
+    assert st == 0 and info["outer"] == 2
+    assert 1e-10 < rel <= 1e-8, rel
+    # the float-rounded inner system of the mixed-precision model reaches the target too
+    inner = oracle.System.from_problem(p, pc="bilu0", float_round=True)
+    for solver in ("gmres", "bicgstab"):
+        st, x, info = oracle.refine(outer, inner, p.b, solver=solver, rtol=1e-8, inner_rtol=1e-5, maxit=6000)
+        assert st == 0 and _true_relres_scipy(p, x) <= 1e-8
+
+
+def test_recorded_refinement_solves_reach_the_target():
+    """The stored refinement solves (written by tests/golden/make_golden.py from the
+    oracle alone) end with status OK at a true residual at or below 1e-8."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "oracle_solves.json")))
+    keys = [k for k in gold if "/refine-" in k]
+    assert keys
+    for k in keys:
+        assert gold[k]["status"] == 0 and gold[k]["relres"] <= 1e-8, (k, gold[k])
