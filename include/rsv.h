@@ -85,6 +85,7 @@ typedef enum { RSV_PREC_FP64 = 0, RSV_PREC_MIXED = 1 } rsv_precision;
 
 typedef struct rsv_grid rsv_grid;
 typedef struct rsv_mat rsv_mat;
+typedef struct rsv_vec rsv_vec;
 typedef struct rsv_solver rsv_solver;
 
 /* Solver parameters (the paper's SOLVER fields rtol, atol, btol, maxit,
@@ -153,9 +154,17 @@ RSV_API rsv_status rsv_grid_create(int nx, int ny, int nz, rsv_grid **out);
 RSV_API void rsv_grid_destroy(rsv_grid *g);
 
 /* ---- matrix (Sections "Distributed Matrices", "Algebraic Operations") ---
- * Creates the seven-point 3x3-block BSR pattern of the grid on the device
- * (rows ascending, columns ascending: -z, -y, -x, self, +x, +y, +z).
- * Values start at zero.  The grid may be destroyed afterwards. */
+ * Creates the seven-point block BSR pattern of the grid on the device (rows
+ * ascending, columns ascending: -z, -y, -x, self, +x, +y, +z; the paper's
+ * distributed matrix with block size 3 and one process owning every row).
+ * Values start at zero.  The grid may be destroyed afterwards.
+ * block: unknowns per cell; only 3 is supported (RSV_ENOTSUP otherwise).
+ * prec: RSV_PREC_FP64 keeps the FP64 values only (solvers on it must be FP64;
+ * saves 36 bytes per block); RSV_PREC_MIXED also keeps an FP32 copy, made at
+ * every rsv_mat_set_values, for mixed-precision solvers.  RSV_EINVAL for a
+ * null grid/out or another prec.  All device work runs on `stream`. */
+RSV_API rsv_status rsv_mat_create_bsr(const rsv_grid *g, int block, int prec, void *stream, rsv_mat **out);
+/* Same as rsv_mat_create_bsr(g, 3, RSV_PREC_MIXED, stream, out). */
 RSV_API rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out);
 RSV_API void rsv_mat_destroy(rsv_mat *A);
 /* A batch of nsys independent grids (dims: int[nsys][3], nx ny nz each) as
@@ -177,8 +186,31 @@ RSV_API rsv_status rsv_mat_set_values(rsv_mat *A, const double *vals, int on_dev
  * x, y: device float64[3*nb]; x and y must not overlap. */
 RSV_API rsv_status rsv_spmv(const rsv_mat *A, double alpha, const double *x, double beta, double *y);
 /* Same in FP32: values rounded once to float at set_values time (the copy
- * used by mixed-precision inner solves); x, y device float32[3*nb]. */
+ * used by mixed-precision inner solves); x, y device float32[3*nb].
+ * RSV_EINVAL on a matrix created with prec RSV_PREC_FP64. */
 RSV_API rsv_status rsv_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y);
+
+/* ---- vectors (Section "Distributed Matrices": the vector type beside the
+ * matrix) ------------------------------------------------------------------
+ * A vector is n values of one precision in device memory: float64 for
+ * RSV_PREC_FP64, float32 for RSV_PREC_MIXED.
+ * rsv_vec_create: owns 3*nx*ny*nz zeroed values (one per unknown of the grid),
+ *   allocated with cudaMalloc and zeroed on `stream` (synchronised).
+ * rsv_vec_wrap: borrows n values at dev_ptr (device or managed memory, for
+ *   example a torch tensor's data_ptr(); aligned to the element size); the
+ *   caller keeps the memory alive while the vector is used and frees it
+ *   itself.  RSV_EINVAL for a host pointer, a misaligned pointer or n < 0.
+ * rsv_vec_set / rsv_vec_get: copy n float64 values in / out (host or device
+ *   pointer, on_device 0/1), converting to / from float32 for an FP32 vector,
+ *   on `stream`; host copies synchronise it, device copies are stream-ordered.
+ * rsv_vec_info: the data pointer, length and precision (any output may be NULL).
+ * rsv_vec_destroy frees owned memory only (after the device's work in flight). */
+RSV_API rsv_status rsv_vec_create(const rsv_grid *g, int prec, void *stream, rsv_vec **out);
+RSV_API rsv_status rsv_vec_wrap(void *dev_ptr, int64_t n, int prec, rsv_vec **out);
+RSV_API rsv_status rsv_vec_set(rsv_vec *v, const double *src, int on_device, void *stream);
+RSV_API rsv_status rsv_vec_get(const rsv_vec *v, double *dst, int on_device, void *stream);
+RSV_API rsv_status rsv_vec_info(const rsv_vec *v, void **dev_ptr, int64_t *n, int *prec);
+RSV_API void rsv_vec_destroy(rsv_vec *v);
 
 /* ---- vector algebra (Section "Algebraic Operations") --------------------
  * Device float64 arrays of length n; the scalar result is returned on the
@@ -199,9 +231,12 @@ RSV_API rsv_status rsv_axpby(void *stream, int64_t n, double alpha, const double
  * held by every GPU that loads the library until the process exits) instead
  * of memory from the allocator; no call to it allocates or frees.
  * Limits: 1 <= k <= 64 (RSV_EINVAL otherwise), ldv >= n.  The first call on
- * a device resolves the array's device address; make that first call before
- * any stream capture.  Every call reuses the same array, so calls whose GPU
- * work overlaps (other streams, other host threads) race: serialise them. */
+ * a device resolves the array's device address and keeps it for the life of
+ * the process; make that first call before any stream capture.  A
+ * cudaDeviceReset in the process invalidates the kept address: do not call
+ * this entry point after resetting a device it has already been called on.
+ * Every call reuses the same array, so calls whose GPU work overlaps (other
+ * streams, other host threads) race: serialise them. */
 RSV_API rsv_status rsv_mdot_noalloc(void *stream, int64_t n, const double *w, const double *V, int64_t ldv, int k,
                                     double *result);
 
@@ -247,10 +282,15 @@ RSV_API rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x);
  * A_ii^{-1}; block ILU(0) and CPR: the ILU factor's U_ii^{-1}) to host
  * float64[nb][3][3]. */
 RSV_API rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host);
-/* Solve A x = b.  b, x: float64[3*nb], host (on_device = 0) or device
- * (on_device = 1); x holds the initial guess on entry and the solution on
- * return (also on ENOCONV).  info may be NULL. */
-RSV_API rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info);
+/* Solve A x = b (the paper's solve call on a SOLVER with a matrix and two
+ * vectors, Section "Solvers").  b, x: FP64 vectors of 3*nb values (RSV_EINVAL
+ * for another length or precision, or b and x sharing memory); x holds the
+ * initial guess on entry and the solution on return (also on ENOCONV).  The
+ * call synchronises the solver's stream; info may be NULL. */
+RSV_API rsv_status rsv_solve(rsv_solver *s, const rsv_vec *b, rsv_vec *x, rsv_solve_info *info);
+/* The same solve on raw float64[3*nb] arrays, host (on_device = 0: copied in
+ * and out inside the call) or device (on_device = 1). */
+RSV_API rsv_status rsv_solve_ptr(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info);
 
 /* Batched solve (the batch extension of the paper's per-process solves; its
  * systems are independent as the paper's subdomain systems are, Section
@@ -259,10 +299,14 @@ RSV_API rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_d
  * preconditioner NONE, BJACOBI or BILU0), with its own scalars, tolerance
  * rtol * ||b_s||, iteration count and status; FP64 or FP32 inner solves
  * under per-system FP64 refinement.  One pass over all systems is captured
- * in a CUDA graph and replayed.  b, x: float64[3*nb] (host or device), x
- * holds the initial guess; infos: rsv_solve_info[nsys] or NULL.  Returns the
- * first non-OK per-system status, else RSV_OK. */
-RSV_API rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *infos);
+ * in a CUDA graph and replayed.  b, x: FP64 vectors of 3*nb values (the
+ * systems' unknowns concatenated), x holds the initial guess; infos:
+ * rsv_solve_info[nsys] or NULL.  Returns the first non-OK per-system status,
+ * else RSV_OK.  rsv_solve_batched_ptr takes raw float64[3*nb] arrays, host
+ * (on_device = 0) or device (on_device = 1). */
+RSV_API rsv_status rsv_solve_batched(rsv_solver *s, const rsv_vec *b, rsv_vec *x, rsv_solve_info *infos);
+RSV_API rsv_status rsv_solve_batched_ptr(rsv_solver *s, const double *b, double *x, int on_device,
+                                         rsv_solve_info *infos);
 
 #ifdef __cplusplus
 }

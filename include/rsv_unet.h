@@ -111,6 +111,19 @@ RSV_API rsv_status rsv_unet_train_step(rsv_unet *u, const double *rp, const doub
 RSV_API rsv_status rsv_unet_train_batch(rsv_unet *u, int n, const double *const *rp, const double *const *lnk,
                                         const double *const *target, float lr, double *losses);
 
+/* Checkpoints of a network in training: its FP32 parameters, both Adam moment
+ * arrays and the Adam step count, so that training resumes exactly where it
+ * stopped.  The file is a magic line "RSVUNET1", one line of JSON (format,
+ * version 1, nx, ny, nz, base, levels, nparam, adam_step, dtype "float32",
+ * endian "little", sections ["params", "adam_m", "adam_v"]), then the three
+ * float32 arrays of nparam values in that order.  rsv_unet_load requires a
+ * network of the same grid, base and levels (RSV_EINVAL otherwise, or for a
+ * malformed or truncated file) and leaves the network unchanged on error.
+ * Both synchronise the network's stream.  The paper has no learned stage; this
+ * is the save/load of its extension's trained state. */
+RSV_API rsv_status rsv_unet_save(const rsv_unet *u, const char *path);
+RSV_API rsv_status rsv_unet_load(rsv_unet *u, const char *path);
+
 /* ------------------------------------------------------------------ use inside the solver
  * rsv_solver_set_learned: the network u (on the solver matrix's grid, one
  * system) becomes the pressure stage of RSV_PC_CPR_LEARNED; lnk is ln k of the

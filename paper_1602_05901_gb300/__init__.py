@@ -70,6 +70,13 @@ _SIGS = {
     "rsv_grid_create": (_I, [_I, _I, _I, _PP]),
     "rsv_grid_destroy": (None, [_P]),
     "rsv_mat_create": (_I, [_P, _P, _PP]),
+    "rsv_mat_create_bsr": (_I, [_P, _I, _I, _P, _PP]),
+    "rsv_vec_create": (_I, [_P, _I, _P, _PP]),
+    "rsv_vec_wrap": (_I, [_P, _I64, _I, _PP]),
+    "rsv_vec_set": (_I, [_P, _P, _I, _P]),
+    "rsv_vec_get": (_I, [_P, _P, _I, _P]),
+    "rsv_vec_info": (_I, [_P, _PP, ctypes.POINTER(_I64), ctypes.POINTER(_I)]),
+    "rsv_vec_destroy": (None, [_P]),
     "rsv_mat_destroy": (None, [_P]),
     "rsv_mat_create_batch": (_I, [_I, _P, _P, _PP]),
     "rsv_mat_get_batch": (_I, [_P, ctypes.POINTER(_I), _P]),
@@ -89,8 +96,10 @@ _SIGS = {
     "rsv_precond_get_dinv": (_I, [_P, _P]),
     "rsv_cpr_info": (_I, [_P, ctypes.POINTER(_I), _P, _P, _P]),
     "rsv_cpr_vcycle": (_I, [_P, _P, _P]),
-    "rsv_solve": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
-    "rsv_solve_batched": (_I, [_P, _P, _P, _I, _P]),
+    "rsv_solve": (_I, [_P, _P, _P, ctypes.POINTER(rsv_solve_info)]),
+    "rsv_solve_ptr": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
+    "rsv_solve_batched": (_I, [_P, _P, _P, _P]),
+    "rsv_solve_batched_ptr": (_I, [_P, _P, _P, _I, _P]),
     "rsv_conv3d_fwd": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P, _I, _P]),
     "rsv_conv3d_dgrad": (_I, [_P, _I, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _I, _P]),
     "rsv_conv3d_wgrad": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P]),
@@ -100,6 +109,8 @@ _SIGS = {
     "rsv_unet_set_params": (_I, [_P, _P, _I]),
     "rsv_unet_get_params": (_I, [_P, _P, _I]),
     "rsv_unet_get_grads": (_I, [_P, _P, _I]),
+    "rsv_unet_save": (_I, [_P, ctypes.c_char_p]),
+    "rsv_unet_load": (_I, [_P, ctypes.c_char_p]),
     "rsv_unet_apply": (_I, [_P, _P, _P, _P]),
     "rsv_unet_train_step": (_I, [_P, _P, _P, _P, _F, ctypes.POINTER(_D)]),
     "rsv_unet_train_batch": (_I, [_P, _I, _P, _P, _P, _F, _P]),
@@ -181,7 +192,8 @@ class Matrix:
     ``Matrix.batch([(nx, ny, nz), ...])`` builds the block-diagonal matrix of a
     batch of independent grids (solve it with ``Solver.solve_batched``)."""
 
-    def __init__(self, nx, ny, nz, stream=None, _batch_dims=None):
+    def __init__(self, nx, ny, nz, stream=None, _batch_dims=None, precision="mixed"):
+        """precision "fp64": FP64 values only (FP64 solvers); "mixed": also the FP32 copy."""
         self.nx, self.ny, self.nz = nx, ny, nz
         self.stream = _stream_ptr(stream)
         h = ctypes.c_void_p()
@@ -189,7 +201,8 @@ class Matrix:
             g = ctypes.c_void_p()
             check(_lib.rsv_grid_create(nx, ny, nz, ctypes.byref(g)), "rsv_grid_create")
             try:
-                check(_lib.rsv_mat_create(g, self.stream, ctypes.byref(h)), "rsv_mat_create")
+                prec = {"fp64": RSV_PREC_FP64, "mixed": RSV_PREC_MIXED}[precision]
+                check(_lib.rsv_mat_create_bsr(g, 3, prec, self.stream, ctypes.byref(h)), "rsv_mat_create_bsr")
             finally:
                 _lib.rsv_grid_destroy(g)
         else:
@@ -237,6 +250,61 @@ class Matrix:
         h = getattr(self, "handle", None)
         if h:
             _lib.rsv_mat_destroy(h)
+            self.handle = None
+
+
+class Vector:
+    """An rsv_vec handle: owned device memory (``Vector.create``) or a borrowed
+    CUDA tensor (``Vector.wrap``; the tensor must outlive the handle)."""
+
+    def __init__(self, handle, keep=None):
+        self.handle = handle
+        self._keep = keep
+        ptr, n, prec = ctypes.c_void_p(), _I64(), ctypes.c_int()
+        check(_lib.rsv_vec_info(handle, ctypes.byref(ptr), ctypes.byref(n), ctypes.byref(prec)), "rsv_vec_info")
+        self.data_ptr, self.n, self.precision = ptr.value, n.value, prec.value
+
+    @classmethod
+    def create(cls, nx, ny, nz, precision="fp64", stream=None):
+        g, h = ctypes.c_void_p(), ctypes.c_void_p()
+        check(_lib.rsv_grid_create(nx, ny, nz, ctypes.byref(g)), "rsv_grid_create")
+        try:
+            prec = {"fp64": RSV_PREC_FP64, "mixed": RSV_PREC_MIXED}[precision]
+            check(_lib.rsv_vec_create(g, prec, _stream_ptr(stream), ctypes.byref(h)), "rsv_vec_create")
+        finally:
+            _lib.rsv_grid_destroy(g)
+        return cls(h)
+
+    @classmethod
+    def wrap(cls, t):
+        """Borrow a contiguous CUDA float64 (FP64) or float32 (FP32) tensor."""
+        assert t.is_cuda and t.is_contiguous()
+        prec = RSV_PREC_FP64 if t.element_size() == 8 else RSV_PREC_MIXED
+        h = ctypes.c_void_p()
+        check(_lib.rsv_vec_wrap(ctypes.c_void_p(t.data_ptr()), t.numel(), prec, ctypes.byref(h)), "rsv_vec_wrap")
+        return cls(h, keep=t)
+
+    @classmethod
+    def of(cls, v):
+        return v if isinstance(v, Vector) else cls.wrap(v)
+
+    def set(self, src, stream=None):
+        on_dev = int(hasattr(src, "is_cuda") and src.is_cuda)
+        if not on_dev:
+            src = np.ascontiguousarray(src, dtype=np.float64)
+        check(_lib.rsv_vec_set(self.handle, _ptr(src), on_dev, _stream_ptr(stream)), "rsv_vec_set")
+
+    def get(self, dst=None, stream=None):
+        if dst is None:
+            dst = np.zeros(self.n)
+        on_dev = int(hasattr(dst, "is_cuda") and dst.is_cuda)
+        check(_lib.rsv_vec_get(self.handle, _ptr(dst), on_dev, _stream_ptr(stream)), "rsv_vec_get")
+        return dst
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.rsv_vec_destroy(h)
             self.handle = None
 
 
@@ -290,10 +358,16 @@ class Solver:
         return x
 
     def solve(self, b, x, raise_on_error=False):
-        """b, x: float64 [3*nb], both host numpy or both CUDA tensors. Returns (status, info dict)."""
-        on_dev = int(hasattr(b, "is_cuda") and b.is_cuda)
+        """b, x: float64 [3*nb], both host numpy, both CUDA tensors, or both :class:`Vector`.
+        Device data goes through rsv_solve on vector handles (tensors are wrapped, not
+        copied); host arrays through rsv_solve_ptr, which copies them in and out.
+        Returns (status, info dict)."""
         info = rsv_solve_info()
-        st = _lib.rsv_solve(self.handle, _ptr(b), _ptr(x), on_dev, ctypes.byref(info))
+        if isinstance(b, Vector) or (hasattr(b, "is_cuda") and b.is_cuda):
+            bv, xv = Vector.of(b), Vector.of(x)
+            st = _lib.rsv_solve(self.handle, bv.handle, xv.handle, ctypes.byref(info))
+        else:
+            st = _lib.rsv_solve_ptr(self.handle, _ptr(b), _ptr(x), 0, ctypes.byref(info))
         if raise_on_error:
             check(st, "rsv_solve")
         return st, info.as_dict()
@@ -322,9 +396,11 @@ class Solver:
 
     def solve_batched(self, b, x):
         """Independent per-grid solves of a batch matrix. Returns (status, [info dict per grid])."""
-        on_dev = int(hasattr(b, "is_cuda") and b.is_cuda)
         infos = (rsv_solve_info * self.A.nsys)()
-        st = _lib.rsv_solve_batched(self.handle, _ptr(b), _ptr(x), on_dev, infos)
+        if isinstance(b, Vector) or (hasattr(b, "is_cuda") and b.is_cuda):
+            st = _lib.rsv_solve_batched(self.handle, Vector.of(b).handle, Vector.of(x).handle, infos)
+        else:
+            st = _lib.rsv_solve_batched_ptr(self.handle, _ptr(b), _ptr(x), 0, infos)
         return st, [i.as_dict() for i in infos]
 
     def __del__(self):
@@ -363,6 +439,13 @@ class Unet:
         out = np.zeros(self.nparam, dtype=np.float32)
         check(_lib.rsv_unet_get_grads(self.handle, _ptr(out), 0), "rsv_unet_get_grads")
         return out
+
+    def save(self, path):
+        """Parameters, Adam moments and step count (rsv_unet_save)."""
+        check(_lib.rsv_unet_save(self.handle, os.fsencode(path)), "rsv_unet_save")
+
+    def load(self, path):
+        check(_lib.rsv_unet_load(self.handle, os.fsencode(path)), "rsv_unet_load")
 
     def apply(self, rp, lnk, corr):
         """corr = s * U(rp / s, lnk); CUDA float64 tensors of nx*ny*nz values."""

@@ -2,6 +2,7 @@
 // matrix handles (Sections "Grid", "Distributed Matrices") and the vector
 // algebra entry points (Section "Algebraic Operations").  The solver handle
 // and the Krylov drivers live in solve.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -17,10 +18,6 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 static std::atomic<uint64_t> g_launches{0};
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-
-namespace {
-
-}  // namespace
 
 rsv_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return RSV_OK;
@@ -109,7 +106,7 @@ namespace rsv {
 
 // Seven-point BSR pattern of one grid or of a block-diagonal batch of grids
 // (each grid's cells contiguous, bottom-up within the grid).
-rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, rsv_mat **out) {
+rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, rsv_mat **out, bool with_f32) {
     const int nsys = (int)dims.size() / 3;
     int64_t total = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -155,7 +152,7 @@ rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, r
     if ((e = cudaMalloc((void **)&A->d_rp, sizeof(int32_t) * (A->nb + 1))) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_ci, sizeof(int32_t) * (A->nnzb + 16))) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_v, vbytes)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&A->d_v32, vbytes / 2)) != cudaSuccess ||
+        (with_f32 && (e = cudaMalloc((void **)&A->d_v32, vbytes / 2)) != cudaSuccess) ||
         (e = cudaMalloc((void **)&A->d_sys, sizeof(SysGrid) * nsys)) != cudaSuccess ||
         (e = cudaMalloc((void **)&A->d_sys_of_cell, sizeof(int32_t) * A->nb)) != cudaSuccess ||
         (e = cudaMemcpyAsync(A->d_rp, A->h_rp.data(), sizeof(int32_t) * (A->nb + 1), cudaMemcpyHostToDevice,
@@ -169,7 +166,7 @@ rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, r
         (e = cudaMemsetAsync(A->d_ci + A->nnzb, 0, sizeof(int32_t) * 16, A->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(A->d_v, 0, vbytes, A->stream)) != cudaSuccess ||
         (e = spmv_init()) != cudaSuccess ||
-        (e = cudaMemsetAsync(A->d_v32, 0, vbytes / 2, A->stream)) != cudaSuccess ||
+        (with_f32 && (e = cudaMemsetAsync(A->d_v32, 0, vbytes / 2, A->stream)) != cudaSuccess) ||
         (e = cudaStreamSynchronize(A->stream)) != cudaSuccess) {
         mat_free(A);
         return cuda_status(e);
@@ -183,13 +180,19 @@ rsv_status mat_create_grids(const std::vector<int> &dims, cudaStream_t stream, r
 extern "C" {
 
 rsv_status rsv_mat_create(const rsv_grid *g, void *stream, rsv_mat **out) {
+    return rsv_mat_create_bsr(g, 3, RSV_PREC_MIXED, stream, out);
+}
+
+rsv_status rsv_mat_create_bsr(const rsv_grid *g, int block, int prec, void *stream, rsv_mat **out) {
     if (!g || !out) return RSV_EINVAL;
-    return mat_create_grids({g->nx, g->ny, g->nz}, (cudaStream_t)stream, out);
+    if (prec != RSV_PREC_FP64 && prec != RSV_PREC_MIXED) return RSV_EINVAL;
+    if (block != 3) return RSV_ENOTSUP;
+    return mat_create_grids({g->nx, g->ny, g->nz}, (cudaStream_t)stream, out, prec == RSV_PREC_MIXED);
 }
 
 rsv_status rsv_mat_create_batch(int nsys, const int *dims, void *stream, rsv_mat **out) {
     if (nsys < 1 || nsys > (1 << 20) || !dims || !out) return RSV_EINVAL;
-    return mat_create_grids(std::vector<int>(dims, dims + 3 * (size_t)nsys), (cudaStream_t)stream, out);
+    return mat_create_grids(std::vector<int>(dims, dims + 3 * (size_t)nsys), (cudaStream_t)stream, out, true);
 }
 
 rsv_status rsv_mat_get_batch(const rsv_mat *A, int *nsys, int64_t *cell_offsets) {
@@ -222,7 +225,7 @@ rsv_status rsv_mat_set_values(rsv_mat *A, const double *vals, int on_device) {
     const size_t bytes = sizeof(double) * 9 * (size_t)A->nnzb;
     RSV_CUDA_TRY(cudaMemcpyAsync(A->d_v, vals, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                  A->stream));
-    RSV_CUDA_TRY(launch_cast_f64_f32(A->stream, 9 * A->nnzb, A->d_v, A->d_v32));
+    if (A->d_v32) RSV_CUDA_TRY(launch_cast_f64_f32(A->stream, 9 * A->nnzb, A->d_v, A->d_v32));
     if (!on_device) RSV_CUDA_TRY(cudaStreamSynchronize(A->stream));
     A->version++;
     return RSV_OK;
@@ -235,8 +238,143 @@ rsv_status rsv_spmv(const rsv_mat *A, double alpha, const double *x, double beta
 }
 
 rsv_status rsv_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y) {
-    if (!A || !x || !y) return RSV_EINVAL;
+    if (!A || !x || !y || !A->d_v32) return RSV_EINVAL;
     RSV_CUDA_TRY(launch_spmv_f32(A, alpha, x, beta, y, nullptr));
+    return RSV_OK;
+}
+
+// ------------------------------------------------------------------ vectors
+
+}  // extern "C"
+
+namespace rsv {
+namespace {
+
+__global__ void cast_f32_f64_kernel(int64_t n, const float *__restrict__ a, double *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+cudaError_t launch_cast_f32_f64(cudaStream_t st, int64_t n, const float *a, double *b) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    cast_f32_f64_kernel<<<(unsigned)std::min<int64_t>(want, 152 * 16), 256, 0, st>>>(n, a, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_bytes(int prec) { return prec == RSV_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+}  // namespace
+}  // namespace rsv
+
+extern "C" {
+
+rsv_status rsv_vec_create(const rsv_grid *g, int prec, void *stream, rsv_vec **out) {
+    if (!g || !out || (prec != RSV_PREC_FP64 && prec != RSV_PREC_MIXED)) return RSV_EINVAL;
+    rsv_vec *v = new (std::nothrow) rsv_vec();
+    if (!v) return RSV_ENOMEM;
+    v->n = 3 * (int64_t)g->nx * g->ny * g->nz;
+    v->prec = prec;
+    v->owned = true;
+    cudaError_t e = cudaMalloc(&v->data, std::max<size_t>(16, v->n * elem_bytes(prec)));
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->data, 0, v->n * elem_bytes(prec), (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        if (v->data) cudaFree(v->data);
+        delete v;
+        return cuda_status(e);
+    }
+    *out = v;
+    return RSV_OK;
+}
+
+rsv_status rsv_vec_wrap(void *dev_ptr, int64_t n, int prec, rsv_vec **out) {
+    if (!out || n < 0 || (prec != RSV_PREC_FP64 && prec != RSV_PREC_MIXED)) return RSV_EINVAL;
+    if (n > 0 && (!dev_ptr || !is_device_pointer(dev_ptr))) return RSV_EINVAL;
+    if ((uintptr_t)dev_ptr % elem_bytes(prec)) return RSV_EINVAL;
+    rsv_vec *v = new (std::nothrow) rsv_vec();
+    if (!v) return RSV_ENOMEM;
+    v->data = dev_ptr;
+    v->n = n;
+    v->prec = prec;
+    v->owned = false;
+    *out = v;
+    return RSV_OK;
+}
+
+void rsv_vec_destroy(rsv_vec *v) {
+    if (!v) return;
+    if (v->owned && v->data) cudaFree(v->data);  // cudaFree waits for the device's work in flight
+    delete v;
+}
+
+rsv_status rsv_vec_info(const rsv_vec *v, void **dev_ptr, int64_t *n, int *prec) {
+    if (!v) return RSV_EINVAL;
+    if (dev_ptr) *dev_ptr = v->data;
+    if (n) *n = v->n;
+    if (prec) *prec = v->prec;
+    return RSV_OK;
+}
+
+rsv_status rsv_vec_set(rsv_vec *v, const double *src, int on_device, void *stream) {
+    if (!v || (v->n > 0 && !src)) return RSV_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (v->n == 0) return RSV_OK;
+    if (v->prec == RSV_PREC_FP64) {
+        RSV_CUDA_TRY(cudaMemcpyAsync(v->data, src, sizeof(double) * v->n,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        if (!on_device) RSV_CUDA_TRY(cudaStreamSynchronize(st));
+        return RSV_OK;
+    }
+    if (on_device) {
+        RSV_CUDA_TRY(launch_cast_f64_f32(st, v->n, src, (float *)v->data));
+        return RSV_OK;
+    }
+    std::vector<float> tmp;
+    try {
+        tmp.resize(v->n);
+    } catch (...) {
+        return RSV_ENOMEM;
+    }
+    for (int64_t i = 0; i < v->n; ++i) tmp[i] = (float)src[i];
+    RSV_CUDA_TRY(cudaMemcpyAsync(v->data, tmp.data(), sizeof(float) * v->n, cudaMemcpyHostToDevice, st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(st));
+    return RSV_OK;
+}
+
+rsv_status rsv_vec_get(const rsv_vec *v, double *dst, int on_device, void *stream) {
+    if (!v || (v->n > 0 && !dst)) return RSV_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (v->n == 0) return RSV_OK;
+    if (v->prec == RSV_PREC_FP64) {
+        RSV_CUDA_TRY(cudaMemcpyAsync(dst, v->data, sizeof(double) * v->n,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        if (!on_device) RSV_CUDA_TRY(cudaStreamSynchronize(st));
+        return RSV_OK;
+    }
+    if (on_device) {
+        RSV_CUDA_TRY(launch_cast_f32_f64(st, v->n, (const float *)v->data, dst));
+        return RSV_OK;
+    }
+    std::vector<float> tmp;
+    try {
+        tmp.resize(v->n);
+    } catch (...) {
+        return RSV_ENOMEM;
+    }
+    RSV_CUDA_TRY(cudaMemcpyAsync(tmp.data(), v->data, sizeof(float) * v->n, cudaMemcpyDeviceToHost, st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < v->n; ++i) dst[i] = (double)tmp[i];
     return RSV_OK;
 }
 

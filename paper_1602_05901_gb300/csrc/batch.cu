@@ -583,8 +583,15 @@ void free_batch(rsv_solver *s) {
 
 using namespace rsv;
 
-extern "C" rsv_status rsv_solve_batched(rsv_solver *s, const double *b, double *x, int on_device,
-                                        rsv_solve_info *infos) {
+extern "C" rsv_status rsv_solve_batched(rsv_solver *s, const rsv_vec *b, rsv_vec *x, rsv_solve_info *infos) {
+    if (!s || !b || !x) return RSV_EINVAL;
+    if (b->prec != RSV_PREC_FP64 || x->prec != RSV_PREC_FP64 || b->n != s->n || x->n != s->n) return RSV_EINVAL;
+    if (b->data == x->data && s->n > 0) return RSV_EINVAL;
+    return rsv_solve_batched_ptr(s, (const double *)b->data, (double *)x->data, 1, infos);
+}
+
+extern "C" rsv_status rsv_solve_batched_ptr(rsv_solver *s, const double *b, double *x, int on_device,
+                                            rsv_solve_info *infos) {
     if (!s || !b || !x) return RSV_EINVAL;
     if (s->pc_type < 0 || s->pc_version != s->A->version) return RSV_EINVAL;
     if (s->p.solver != RSV_BICGSTAB) return RSV_ENOTSUP;

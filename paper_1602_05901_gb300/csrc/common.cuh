@@ -125,8 +125,17 @@ struct rsv_mat {
     std::vector<int32_t> h_rp, h_ci;
     int32_t *d_rp = nullptr, *d_ci = nullptr;
     double *d_v = nullptr;   // nnzb*9 (+ tail pad)
-    float *d_v32 = nullptr;  // FP32 copy of the values
+    float *d_v32 = nullptr;  // FP32 copy of the values (matrices created for mixed precision only)
     uint64_t version = 0;
+};
+
+// A vector of the boundary: n values of one precision in device memory, owned
+// (rsv_vec_create) or borrowed (rsv_vec_wrap).
+struct rsv_vec {
+    void *data = nullptr;
+    int64_t n = 0;
+    int prec = 0;          // RSV_PREC_FP64: double, RSV_PREC_MIXED: float
+    bool owned = false;
 };
 
 namespace rsv {

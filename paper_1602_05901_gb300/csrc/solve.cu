@@ -480,6 +480,7 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
     if (p->precision != RSV_PREC_FP64 && p->precision != RSV_PREC_MIXED) return RSV_EINVAL;
     if (p->precision == RSV_PREC_MIXED && (!(p->inner_rtol > 0.0) || !(p->inner_rtol < 1.0) || p->max_outer < 1))
         return RSV_EINVAL;
+    if (p->precision == RSV_PREC_MIXED && !A->d_v32) return RSV_EINVAL;  // matrix created without an FP32 copy
     rsv_solver *s = new (std::nothrow) rsv_solver();
     if (!s) return RSV_ENOMEM;
     s->A = A;
@@ -635,7 +636,14 @@ rsv_status rsv_precond_get_dinv(rsv_solver *s, double *dinv_host) {
     return RSV_OK;
 }
 
-rsv_status rsv_solve(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info) {
+rsv_status rsv_solve(rsv_solver *s, const rsv_vec *b, rsv_vec *x, rsv_solve_info *info) {
+    if (!s || !b || !x) return RSV_EINVAL;
+    if (b->prec != RSV_PREC_FP64 || x->prec != RSV_PREC_FP64 || b->n != s->n || x->n != s->n) return RSV_EINVAL;
+    if (b->data == x->data && s->n > 0) return RSV_EINVAL;
+    return rsv_solve_ptr(s, (const double *)b->data, (double *)x->data, 1, info);
+}
+
+rsv_status rsv_solve_ptr(rsv_solver *s, const double *b, double *x, int on_device, rsv_solve_info *info) {
     if (!s || !b || !x) return RSV_EINVAL;
     if (s->pc_type < 0 || s->pc_version != s->A->version) return RSV_EINVAL;
     const int64_t n = s->n;

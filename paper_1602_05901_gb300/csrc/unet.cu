@@ -25,6 +25,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/rsv_unet.h"
@@ -712,6 +715,96 @@ extern "C" rsv_status rsv_unet_get_params(const rsv_unet *u, float *params, int 
 
 extern "C" rsv_status rsv_unet_get_grads(const rsv_unet *u, float *grads, int on_device) {
     return u ? copy_out(u, u->g, grads, on_device) : RSV_EINVAL;
+}
+
+// ---- checkpoints: a text header line (JSON) then params, Adam m, Adam v as little-endian float32
+namespace {
+
+constexpr char kCkptMagic[] = "RSVUNET1\n";
+
+bool read_json_int(const std::string &h, const char *key, long long *out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = h.find(k);
+    if (at == std::string::npos) return false;
+    return std::sscanf(h.c_str() + at + k.size(), " %lld", out) == 1;
+}
+
+}  // namespace
+
+extern "C" rsv_status rsv_unet_save(const rsv_unet *u, const char *path) {
+    if (!u || !path) return RSV_EINVAL;
+    std::vector<float> buf;
+    try {
+        buf.resize(3 * (size_t)u->nparam);
+    } catch (...) {
+        return RSV_ENOMEM;
+    }
+    const float *src[3] = {u->p, u->m, u->v};
+    for (int q = 0; q < 3; ++q)
+        RSV_CUDA_TRY(cudaMemcpyAsync(buf.data() + q * (size_t)u->nparam, src[q], sizeof(float) * u->nparam,
+                                     cudaMemcpyDeviceToHost, u->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(u->st));
+    char head[512];
+    const int len = std::snprintf(head, sizeof head,
+                                  "{\"format\":\"rsv_unet\",\"version\":1,\"nx\":%d,\"ny\":%d,\"nz\":%d,"
+                                  "\"base\":%d,\"levels\":%d,\"nparam\":%lld,\"adam_step\":%d,"
+                                  "\"dtype\":\"float32\",\"endian\":\"little\","
+                                  "\"sections\":[\"params\",\"adam_m\",\"adam_v\"]}\n",
+                                  u->nx, u->ny, u->nz, u->base, u->L, (long long)u->nparam, u->adam_t);
+    if (len <= 0 || len >= (int)sizeof head) return RSV_EINVAL;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return RSV_EINVAL;
+    bool ok = std::fwrite(kCkptMagic, 1, sizeof kCkptMagic - 1, f) == sizeof kCkptMagic - 1 &&
+              std::fwrite(head, 1, (size_t)len, f) == (size_t)len &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? RSV_OK : RSV_EINVAL;
+}
+
+extern "C" rsv_status rsv_unet_load(rsv_unet *u, const char *path) {
+    if (!u || !path) return RSV_EINVAL;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return RSV_EINVAL;
+    char magic[sizeof kCkptMagic - 1];
+    char line[512];
+    rsv_status st = RSV_OK;
+    std::vector<float> buf;
+    if (std::fread(magic, 1, sizeof magic, f) != sizeof magic || std::memcmp(magic, kCkptMagic, sizeof magic) ||
+        !std::fgets(line, sizeof line, f))
+        st = RSV_EINVAL;
+    long long nx = 0, ny = 0, nz = 0, base = 0, levels = 0, nparam = 0, step = 0, version = 0;
+    if (st == RSV_OK) {
+        const std::string h(line);
+        if (h.find("\"format\":\"rsv_unet\"") == std::string::npos || !read_json_int(h, "version", &version) ||
+            version != 1 || !read_json_int(h, "nx", &nx) || !read_json_int(h, "ny", &ny) ||
+            !read_json_int(h, "nz", &nz) || !read_json_int(h, "base", &base) || !read_json_int(h, "levels", &levels) ||
+            !read_json_int(h, "nparam", &nparam) || !read_json_int(h, "adam_step", &step))
+            st = RSV_EINVAL;
+        // the network must have the stored architecture (grid, width, depth)
+        else if (nx != u->nx || ny != u->ny || nz != u->nz || base != u->base || levels != u->L ||
+                 nparam != u->nparam || step < 0 || step > (1ll << 30))
+            st = RSV_EINVAL;
+    }
+    if (st == RSV_OK) {
+        try {
+            buf.resize(3 * (size_t)u->nparam);
+        } catch (...) {
+            st = RSV_ENOMEM;
+        }
+    }
+    if (st == RSV_OK && (std::fread(buf.data(), sizeof(float), buf.size(), f) != buf.size() || std::fgetc(f) != EOF))
+        st = RSV_EINVAL;
+    std::fclose(f);
+    if (st != RSV_OK) return st;
+    float *dst[3] = {u->p, u->m, u->v};
+    for (int q = 0; q < 3; ++q)
+        RSV_CUDA_TRY(cudaMemcpyAsync(dst[q], buf.data() + q * (size_t)u->nparam, sizeof(float) * u->nparam,
+                                     cudaMemcpyHostToDevice, u->st));
+    u->adam_t = (int)step;
+    u->acts_valid = false;
+    RSV_TRY(refresh_bf16(u));
+    RSV_CUDA_TRY(cudaStreamSynchronize(u->st));
+    return RSV_OK;
 }
 
 extern "C" rsv_status rsv_unet_apply(rsv_unet *u, const double *rp, const double *lnk, double *corr) {

@@ -58,3 +58,24 @@ def kron_bsr(nx, ny, nz, m_block, acc_block, trans=lambda c, o: 1.0):
             diag = diag + t * np.asarray(m_block)
         vals[dpos] = diag
     return rp, ci, vals
+
+
+def per_entry_ratio(got, ref, floor=1e-3):
+    """Largest per-entry error, each relative to its own reference magnitude:
+    max_i |got_i - ref_i| / (|ref_i| + floor * rms(ref)).
+
+    The floor (a fixed fraction of the RMS entry) keeps entries that are near
+    zero from dominating; a wrong value in a handful of entries still shows at
+    full size instead of being diluted by the vector's length as in a norm."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    rms = np.sqrt(np.mean(ref * ref)) if ref.size else 0.0
+    scale = np.abs(ref) + floor * rms
+    scale[scale == 0] = 1.0
+    return float(np.max(np.abs(got - ref) / scale)) if ref.size else 0.0
+
+
+def report_ratio(name, value, bound):
+    """Print an observed per-entry error beside its bound (pytest -s shows it)."""
+    print(f"PER_ENTRY {name} {value:.3e} bound {bound:.1e}")
+    return value

@@ -22,11 +22,18 @@ def lib():
     return ctypes.CDLL(path), path
 
 
+# The boundary's calls: grid, BSR matrix, vectors, solver, preconditioner setup,
+# solve (single and batched), the learned stage's checkpoints, destroy calls.
+BOUNDARY = ("rsv_grid_create", "rsv_grid_destroy", "rsv_mat_create_bsr", "rsv_mat_get_pattern", "rsv_mat_set_values",
+            "rsv_mat_destroy", "rsv_vec_create", "rsv_vec_wrap", "rsv_vec_set", "rsv_vec_get", "rsv_vec_destroy",
+            "rsv_solver_create", "rsv_solver_destroy", "rsv_precond_setup", "rsv_solve", "rsv_solve_batched",
+            "rsv_unet_load", "rsv_unet_save", "rsv_status_string", "rsv_spmv")
+
+
 def test_header_declares_entry_points():
     names = declared_functions()
-    for must in ("rsv_grid_create", "rsv_mat_create", "rsv_mat_set_values", "rsv_spmv", "rsv_solver_create",
-                 "rsv_precond_setup", "rsv_solve"):
-        assert must in names
+    for must in BOUNDARY + ("rsv_mat_create", "rsv_solve_ptr", "rsv_solve_batched_ptr"):
+        assert must in names, must
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -54,7 +61,25 @@ def test_host_side_argument_checks_without_gpu(lib):
     assert rsv.rsv_mat_create(None, None, ctypes.byref(g)) == rsv.RSV_EINVAL
     assert rsv.rsv_solver_create(None, None, ctypes.byref(g)) == rsv.RSV_EINVAL
     assert rsv.rsv_precond_setup(None, 1, None) == rsv.RSV_EINVAL
-    assert rsv.rsv_solve(None, None, None, 0, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_solve(None, None, None, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_solve_ptr(None, None, None, 0, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_solve_batched(None, None, None, None) == rsv.RSV_EINVAL
+    # the BSR matrix: block size 3 only, FP64 or mixed storage (checked before any device call)
+    assert rsv.rsv_grid_create(3, 2, 1, ctypes.byref(g)) == rsv.RSV_OK
+    m = ctypes.c_void_p()
+    assert rsv.rsv_mat_create_bsr(g, 4, rsv.RSV_PREC_FP64, None, ctypes.byref(m)) == rsv.RSV_ENOTSUP
+    assert rsv.rsv_mat_create_bsr(g, 3, 7, None, ctypes.byref(m)) == rsv.RSV_EINVAL
+    assert rsv.rsv_mat_create_bsr(None, 3, rsv.RSV_PREC_FP64, None, ctypes.byref(m)) == rsv.RSV_EINVAL
+    v = ctypes.c_void_p()
+    assert rsv.rsv_vec_create(g, 7, None, ctypes.byref(v)) == rsv.RSV_EINVAL
+    assert rsv.rsv_vec_create(None, rsv.RSV_PREC_FP64, None, ctypes.byref(v)) == rsv.RSV_EINVAL
+    rsv.rsv_grid_destroy(g)
+    assert rsv.rsv_vec_wrap(None, 10, rsv.RSV_PREC_FP64, ctypes.byref(v)) == rsv.RSV_EINVAL
+    assert rsv.rsv_vec_wrap(None, -1, rsv.RSV_PREC_FP64, ctypes.byref(v)) == rsv.RSV_EINVAL
+    assert rsv.rsv_vec_set(None, None, 0, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_vec_get(None, None, 0, None) == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_save(None, b"/nonexistent") == rsv.RSV_EINVAL
+    assert rsv.rsv_unet_load(None, b"/nonexistent") == rsv.RSV_EINVAL
     assert rsv.status_string(rsv.RSV_ENOCONV) == "not converged within maxit"
     p = rsv.solver_params()
     assert (p.restart, p.rtol, p.maxit, p.btol) == (30, 1e-8, 2000, 1e-30)

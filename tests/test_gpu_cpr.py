@@ -4,6 +4,7 @@ import pytest
 
 import oracle
 import synth
+from tests.helpers import per_entry_ratio, report_ratio
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +69,8 @@ def test_vcycle_matches_oracle(rsv, torch, dims, sweeps, coarse):
     s.vcycle(bd, xd)
     torch.cuda.synchronize()
     e = xd.cpu().numpy()
-    assert np.linalg.norm(e - e_or) <= 1e-10 * np.linalg.norm(e_or)
+    ratio = report_ratio(f"vcycle_{dims}_{sweeps}_{coarse}", per_entry_ratio(e, e_or), 1e-9)
+    assert ratio <= 1e-9
 
 
 @pytest.mark.parametrize("dims", DIMS)
@@ -82,7 +84,8 @@ def test_cpr_apply_matches_oracle(rsv, torch, dims):
     zd = torch.zeros_like(fd)
     s.apply(fd, zd)
     torch.cuda.synchronize()
-    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+    ratio = report_ratio(f"cpr_apply_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-9)
+    assert ratio <= 1e-9
 
 
 @pytest.mark.parametrize("dims", [(20, 20, 10), (33, 17, 9)])
@@ -96,8 +99,8 @@ def test_cpr_apply_fp32_matches_oracle(rsv, torch, dims):
     zd = torch.zeros_like(fd)
     s.apply(fd, zd)
     torch.cuda.synchronize()
-    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
-    assert err <= 1e-4, err
+    ratio = report_ratio(f"cpr_apply_fp32_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 2e-3)
+    assert ratio <= 2e-3
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -114,7 +117,12 @@ def test_cpr_solve_tiny(rsv, torch, precision, solver):
     assert st == rsv.RSV_OK, (st, info)
     relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
     assert relres <= 1e-8
-    if precision == "fp64":
+    if precision == "fp64" and solver != "bicgstab":
+        o = oracle.System.from_problem(p, pc="cpr")
+        ost, _, oinfo = o.gmres(p.b, flexible=(solver == "fgmres"), maxit=4000)
+        assert ost == 0 and abs(info["iters"] - oinfo["iters"]) <= max(2, 0.1 * oinfo["iters"]), (info, oinfo)
+    elif precision == "fp64":
+        # BiCGSTAB's count is a chaotic function of rounding: compare with the oracle's spread
         its = []
         for t in range(6):
             bb = p.b if t == 0 else p.b * (1 + 1e-15 * np.random.default_rng(1000 + t).standard_normal(p.n))
@@ -127,6 +135,9 @@ def test_cpr_solve_tiny(rsv, torch, precision, solver):
 
 
 def test_cpr_mid_full_size(rsv, torch):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solves.json")))
     p = synth.workload("mid_100x100x50")
     for precision in ("fp64", "mixed"):
         A = rsv.Matrix(p.nx, p.ny, p.nz)
@@ -142,6 +153,10 @@ def test_cpr_mid_full_size(rsv, torch):
         relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(
             p.b)
         assert relres <= 1e-8
+        # iteration counts against the oracle's: FP64 GMRES, and the refinement model of the mixed solve
+        g = gold["mid_100x100x50/" + ("gmres" if precision == "fp64" else "refine-gmres") + "/cpr"]
+        print(f"CPR_MID_ITERS {precision} gpu {info['iters']} oracle {g['iters']}")
+        assert abs(info["iters"] - g["iters"]) <= max(2, 0.1 * g["iters"]), (precision, info, g)
 
 
 # ---- the other stage orders of Section "CPR-like preconditioners" (FP, FPF, FFPF)
@@ -170,7 +185,8 @@ def test_cpr_order_apply_matches_oracle(rsv, torch, pc, dims):
     zd = torch.zeros_like(fd)
     s.apply(fd, zd)
     torch.cuda.synchronize()
-    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+    ratio = report_ratio(f"{pc}_apply_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-9)
+    assert ratio <= 1e-9
 
 
 @pytest.mark.parametrize("pc", ORDERS)
@@ -184,8 +200,8 @@ def test_cpr_order_apply_fp32_matches_oracle(rsv, torch, pc):
     zd = torch.zeros_like(fd)
     s.apply(fd, zd)
     torch.cuda.synchronize()
-    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
-    assert err <= 1e-4, err
+    ratio = report_ratio(f"{pc}_apply_fp32", per_entry_ratio(zd.cpu().numpy(), z_or), 2e-3)
+    assert ratio <= 2e-3
 
 
 @pytest.mark.parametrize("pc", ORDERS)
@@ -228,7 +244,8 @@ def test_abf_cpr_apply_matches_oracle(rsv, torch, pc, dims):
     zd = torch.zeros_like(fd)
     s.apply(fd, zd)
     torch.cuda.synchronize()
-    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-9 * np.linalg.norm(z_or)
+    ratio = report_ratio(f"abf_{pc}_apply_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-9)
+    assert ratio <= 1e-9
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

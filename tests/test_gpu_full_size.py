@@ -9,6 +9,8 @@
   solve to rtol 1e-8.
 """
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -20,6 +22,7 @@ from oracle import unet as U
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solves.json")
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +78,10 @@ def test_large_cpr_solve(rsv, torch, large, precision):
     assert st == 0, info
     relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
     assert relres <= 1e-8 and abs(relres - info["true_relres"]) <= 1e-10, (relres, info)
-    print(precision, info)
+    # iteration count within 10% of the oracle's (FP64 GMRES, or its refinement model of the mixed solve)
+    gold = json.load(open(GOLDEN))["large_256x256x128/" + ("gmres" if precision == "fp64" else "refine-gmres") + "/cpr"]
+    print(f"LARGE_CPR_ITERS {precision} gpu {info['iters']} oracle {gold['iters']}", info)
+    assert abs(info["iters"] - gold["iters"]) <= max(2, 0.1 * gold["iters"]), (info, gold)
 
 
 def _bf16(torch, a):

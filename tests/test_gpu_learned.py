@@ -59,6 +59,9 @@ def test_learned_cpr_apply_matches_oracle(rsv, prob):
                               BASE, LEVELS, bf16=True)
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert rel < 5e-3, rel
+    from tests.helpers import per_entry_ratio, report_ratio
+    ratio = report_ratio("learned_cpr_apply", per_entry_ratio(got, ref, floor=1e-2), 0.1)
+    assert ratio <= 0.1
 
 
 def test_learned_solve_converges_and_reports_fallback(rsv, prob):

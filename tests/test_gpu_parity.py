@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import synth
+from tests.helpers import per_entry_ratio, report_ratio
 
 pytestmark = pytest.mark.gpu
 
@@ -114,7 +115,32 @@ def test_preconditioner_factor_and_apply(rsv, torch, dims, pc):
     s.apply(rd, zd)
     torch.cuda.synchronize()
     _, z_or = o.pc_apply(r)
-    assert np.linalg.norm(zd.cpu().numpy() - z_or) <= 1e-11 * np.linalg.norm(z_or)
+    ratio = report_ratio(f"{pc}_apply_fp64_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-10)
+    assert ratio <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ilu_apply_mid_full_size_per_entry(rsv, torch, precision):
+    """Block ILU(0) apply at 100x100x50 (13x13 tiles of 8x4 pencils, the full
+    edge hand-off protocol of the tile sweeps) against the oracle, per entry.
+    FP32 (mixed): the GPU applies the FP32 factor in FP32; the oracle applies the
+    same FP32-rounded factor in FP64."""
+    p = synth.workload("mid_100x100x50")
+    A = _mat(rsv, p)
+    s = rsv.Solver(A, precision=precision)
+    s.setup("bilu0")
+    o = oracle.System.from_problem(p, pc="bilu0", float_round=(precision == "mixed"))
+    r = np.random.default_rng(46).standard_normal(p.n)
+    if precision == "mixed":
+        r = r.astype(np.float32)
+    rd = torch.from_numpy(r).cuda()
+    zd = torch.zeros_like(rd)
+    s.apply(rd, zd)
+    torch.cuda.synchronize()
+    _, z_or = o.pc_apply(r.astype(np.float64))
+    bound = 1e-10 if precision == "fp64" else 2e-3
+    ratio = report_ratio(f"bilu0_apply_{precision}_mid", per_entry_ratio(zd.cpu().numpy(), z_or), bound)
+    assert ratio <= bound
 
 
 SOLVES = [("bicgstab", "bjacobi"), ("gmres", "bilu0"), ("fgmres", "bilu0"), ("bicgstab", "bilu0"),
@@ -161,8 +187,13 @@ def test_solve_tiny_matches_oracle(rsv, torch, solver, pc, dims):
     xh = x.cpu().numpy()
     relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, xh)) / np.linalg.norm(p.b)
     assert relres <= 1e-8 and abs(relres - info["true_relres"]) <= 1e-12
-    lo, hi = _oracle_iter_range(p, solver, pc)
-    assert 0.9 * lo - 2 <= info["iters"] <= 1.1 * hi + 2, (info, lo, hi)
+    if solver == "bicgstab":
+        # BiCGSTAB's count is a chaotic function of rounding: compare with the oracle's spread
+        lo, hi = _oracle_iter_range(p, solver, pc)
+        assert 0.9 * lo - 2 <= info["iters"] <= 1.1 * hi + 2, (info, lo, hi)
+    else:
+        ost, _, oinfo = _oracle_solve(p, solver, pc, maxit=4000)
+        assert ost == 0 and _iters_close(info["iters"], oinfo["iters"]), (info, oinfo)
 
 
 def test_host_buffers_match_device_buffers(rsv, torch):
@@ -256,8 +287,8 @@ def test_mixed_preconditioner_fp32(rsv, torch, dims, pc):
     s.apply(rd, zd)
     torch.cuda.synchronize()
     _, z_or = of.pc_apply(r.astype(np.float64))
-    err = np.linalg.norm(zd.cpu().numpy().astype(np.float64) - z_or) / np.linalg.norm(z_or)
-    assert err <= 1e-4, err
+    ratio = report_ratio(f"{pc}_apply_fp32_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 2e-3)
+    assert ratio <= 2e-3
 
 
 @pytest.mark.parametrize("solver,pc", [("gmres", "bilu0"), ("bicgstab", "bilu0"), ("gmres", "bjacobi"),
@@ -277,10 +308,17 @@ def test_mixed_solve_reaches_fp64_tolerance(rsv, torch, solver, pc):
     assert info["outer_iters"] >= 2
     outer = oracle.System.from_problem(p, pc="none")
     inner = oracle.System.from_problem(p, pc=pc, float_round=True)
-    ost, _, oinfo = oracle.refine(outer, inner, p.b, solver="bicgstab" if solver == "bicgstab" else "gmres",
-                                  maxit=6000)
-    assert ost == 0
-    assert 0.5 * oinfo["iters"] - 5 <= info["iters"] <= 1.5 * oinfo["iters"] + 5, (info, oinfo)
+    its = []
+    # GMRES: the oracle's refinement count itself; BiCGSTAB: its spread under rounding-level
+    # perturbations of b (the count is a chaotic function of rounding)
+    for t in range(1 if solver != "bicgstab" else 6):
+        bb = p.b if t == 0 else p.b * (1 + 1e-15 * np.random.default_rng(2000 + t).standard_normal(p.n))
+        ost, _, oinfo = oracle.refine(outer, inner, bb, solver="bicgstab" if solver == "bicgstab" else "gmres",
+                                      maxit=6000)
+        assert ost == 0
+        its.append(oinfo["iters"])
+    print(f"MIXED_ITERS {solver}/{pc} gpu {info['iters']} oracle {its}")
+    assert 0.9 * min(its) - 2 <= info["iters"] <= 1.1 * max(its) + 2, (info, its)
 
 
 def test_watchdog_timeout_returns_status_and_context_survives(rsv, torch):
@@ -316,6 +354,9 @@ def test_mid_mixed_gmres_bilu0_full_size(rsv, torch):
     assert st == 0, info
     relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
     assert relres <= 1e-8
+    gold = json.load(open(GOLDEN))["mid_100x100x50/refine-gmres/bilu0"]
+    print(f"MIXED_ITERS mid gmres/bilu0 gpu {info['iters']} oracle {gold['iters']}")
+    assert _iters_close(info["iters"], gold["iters"]), (info, gold)
 
 
 def test_mid_gmres_bilu0_full_size(rsv, torch):

@@ -86,8 +86,12 @@ def test_unet_forward_matches_oracle(rsv, case):
     ref = U.apply_stage(params, rp, lnk, base, levels, bf16=True)
     ref64 = U.apply_stage(params, rp, lnk, base, levels, bf16=False)
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    # Same BF16 rounding points on both sides; only FP32 summation order differs.
+    # Same BF16 rounding points on both sides; only FP32 summation order differs,
+    # which can flip a BF16 rounding (2^-8 relative) of an activation here and there.
     assert rel < 5e-3, rel
+    from tests.helpers import per_entry_ratio, report_ratio
+    ratio = report_ratio(f"unet_forward_{case}", per_entry_ratio(got, ref, floor=1e-2), 0.1)
+    assert ratio <= 0.1
     assert np.linalg.norm(ref - ref64) / np.linalg.norm(ref64) < 0.1
     rsv.rsv_unet_destroy(h)
 
