@@ -1,19 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: time to solve A x = b to rtol 1e-8 on one GB300, plus BSR SpMV HBM GB/s.
 
-Workload: the 100x100x50 grid (500,000 cells, 1.5M unknowns) with layered
-permeability (seed 1), solved by GMRES(30) + block ILU(0) in wavefront order
-to a true FP64 relative residual of 1e-8.  One step = preconditioner setup +
-solve from x0 = 0 with the matrix and right-hand side already resident in
-HBM, in the mixed-precision form (FP32 inner solves under FP64 iterative
-refinement); the plain FP64 solve of the same system is timed the same way
-and reported beside it.  The matrix (249 MB of FP64 blocks) is larger than
-the 129 MB L2, so no flush is needed between steps.
+Workload: the 256x256x128 channelised grid (8,388,608 cells, 25.2M unknowns,
+4.2 GB of FP64 blocks; log-normal permeability with sigma 2, five x-aligned
+streaks, 16 seeded wells, seed 2), solved by GMRES(30) + CPR-PF (quasi-IMPES,
+geometric-multigrid V-cycle, block ILU(0)) to a true FP64 relative residual
+of 1e-8.  One step = preconditioner setup + solve from x0 = 0 with the matrix
+and right-hand side already resident in HBM, in the mixed-precision form
+(FP32 inner solves under FP64 iterative refinement); the plain FP64 solve of
+the same system is timed beside it over --fp64-steps solves.  The matrix is
+far larger than the 129 MB L2, so no flush is needed between steps.
+`--workload mid_100x100x50 --pc bilu0` runs the 100x100x50 layered workload
+with block ILU(0) instead.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU FP64 oracle
-instead, on a bounded sample of the same workload scaled to the full solve.
-Multi-GPU (torchrun): independent replicas, one per GPU, timed together; the
-solver has no data-path collective.
+(OpenMP build, every host core) instead, on bounded samples of the same
+workload projected to the full solve.  Multi-GPU (torchrun): independent
+replicas, one per GPU, timed together; the solver has no data-path collective.
 """
 from __future__ import annotations
 
@@ -29,7 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solve time to rtol 1e-8 + SpMV HBM GB/s; mixed/learned vs plain FP64 on 1 GB300"
-WORKLOAD = "mid_100x100x50"
+WORKLOAD = "large_256x256x128"
+PC = "cpr"
+MID = "mid_100x100x50"
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129e6
 
@@ -52,22 +57,9 @@ def spmv_bytes(nb, nnzb, val_bytes=8):
     return nnzb * (9 * val_bytes + 4) + (nb + 1) * 4 + 2 * nb * 3 * val_bytes
 
 
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (CUDA cores) from the pool's nominal table
-
-# DRAM bytes per launch (read + write) measured by one ncu capture of the current kernels on this
-# workload (profiles/ilu_apply_mid_100x100x50.md).  Set an entry to None whenever its kernel changes.
-NCU_TRAFFIC = {
-    "ilu_apply_f32": 206.8e6,   # gather_tiles + forward + backward sweep, FP32
-    "ilu_apply_f64": 462.4e6,
-    "spmv_f32": 148.0e6,
-    "spmv_f64": 284.2e6,
-}
-
-
-def ilu_apply_flops(nb, nnzb):
-    """FP64/FP32 flops of one block ILU(0) apply: a 3x3 block-vector product (9 FMA) per
-    off-diagonal block and two D^{-1} products per cell."""
-    return 2 * 9 * ((nnzb - nb) + 2 * nb)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture, with the
+# kernel sources and their hash at capture time: a figure is reported only while the sources are unchanged.
+NCU_TRAFFIC = {}
 
 
 def spmv_flops(nnzb):
@@ -150,45 +142,111 @@ def max_over_ranks(ms, dist, dev=None):
     return float(t.item())
 
 
-def cpu_baseline(p, gpu_iters, sample_iters, solver="gmres", pc="bilu0"):
-    """Time the oracle (as it stands, one thread) on the first `sample_iters` Krylov
-    iterations of the workload and scale its solve time to `gpu_iters` iterations."""
-    import oracle
-    t0 = time.perf_counter()
-    s = oracle.System.from_problem(p, pc=pc)
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    st, x, info = s.gmres(p.b, m=30, maxit=sample_iters) if solver == "gmres" else s.bicgstab(p.b, maxit=sample_iters)
-    t_solve = time.perf_counter() - t0
-    done = max(info["iters"], 1)
-    est_ms = 1e3 * (t_setup + t_solve * gpu_iters / done)
-    return {"value": round(est_ms, 3), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"oracle setup + first {done} of {gpu_iters} GMRES(30)+BILU0 iterations on {WORKLOAD} "
-                      f"({t_setup + t_solve:.1f} s of CPU work), solve time scaled linearly to {gpu_iters} iterations"}
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def golden_iters(workload, key):
+    """The oracle's own iteration count on a workload (tests/golden/oracle_solves.json, written by
+    tests/golden/make_golden.py from the oracle alone), or None."""
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+    try:
+        return int(json.load(open(gold))[f"{workload}/{key}"]["iters"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class OracleSample:
+    """The oracle (as it stands, its OpenMP build at every host core) on a bounded sample of the
+    workload: one preconditioner setup, then GMRES(30) runs of `sample_iters` iterations from
+    x0 = 0.  The full solve's time is projected as setup + per-iteration time x the oracle's own
+    full iteration count.  The sample's iterations are the first of a restart cycle, whose
+    Gram-Schmidt work is below a cycle's average; the preconditioner dominates each iteration."""
+
+    def __init__(self, p, pc, full_iters, threads=None):
+        import oracle
+        self.threads = oracle.use_threads(threads or os.cpu_count() or 1)
+        self.p, self.full_iters = p, full_iters
+        t0 = time.perf_counter()
+        self.sys = oracle.System.from_problem(p, pc=pc)
+        self.setup_s = time.perf_counter() - t0
+
+    def run(self, sample_iters):
+        t0 = time.perf_counter()
+        _, _, info = self.sys.gmres(self.p.b, m=30, maxit=sample_iters)
+        dt = time.perf_counter() - t0
+        return dt, max(info["iters"], 1)
+
+    def projected_ms(self, per_iter_s):
+        return 1e3 * (self.setup_s + per_iter_s * self.full_iters)
+
+
+def cpu_baseline(p, workload, pc, full_iters, sample_iters):
+    """cpu_baseline entry of the bench line: one OracleSample run."""
+    t_all = time.perf_counter()
+    o = OracleSample(p, pc, full_iters)
+    dt, done = o.run(sample_iters)
+    per_iter = dt / done
+    return {"value": round(o.projected_ms(per_iter), 3), "unit": "ms", "cores": o.threads, "kind": "oracle",
+            "cpu": cpu_model(), "build": "oracle.c with OpenMP (SpMV rows, vector updates, one colour of "
+            "Gauss-Seidel, stencil products in parallel; ILU(0) sweeps sequential)",
+            "sample": f"oracle setup ({o.setup_s:.1f} s) + the first {done} GMRES(30)+{pc.upper()} iterations "
+                      f"on {workload} at {o.threads} threads ({per_iter:.2f} s each; "
+                      f"{time.perf_counter() - t_all:.1f} s of CPU work), projected to the oracle's "
+                      f"{full_iters} iterations of the full FP64 solve"}
 
 
 def run_reference(args, rank, ws):
+    """The reference arm: the CPU oracle on the same workload and config as the GPU arm.  Each
+    timed step is a bounded sample (args.ref_sample_iters GMRES iterations); the line's value
+    projects the per-iteration time of all timed steps to the oracle's full solve."""
     if rank != 0:
         return 0
     import synth
-    p = synth.workload(WORKLOAD)
-    full_iters = 456  # oracle iteration count on this workload (tests/golden/oracle_solves.json)
-    gold = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
-    try:
-        full_iters = json.load(open(gold))[f"{WORKLOAD}/gmres/bilu0"]["iters"]
-    except (OSError, KeyError, ValueError):
-        pass
-    sample = max(5, args.ref_sample_iters)
+    p = synth.workload(args.workload)
+    full_iters = golden_iters(args.workload, f"gmres/{args.pc}")
+    if full_iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no recorded oracle iteration count for "
+                          f"{args.workload} gmres/{args.pc}"}), flush=True)
+        return 0
+    o = OracleSample(p, args.pc, full_iters)
     for _ in range(args.warmup):
-        cpu_baseline(p, full_iters, 5)
-    vals = [cpu_baseline(p, full_iters, sample)["value"] for _ in range(args.steps)]
-    v = statistics.median(vals)
+        o.run(max(1, args.ref_sample_iters // 2))
+    t0 = time.perf_counter()
+    tot_s, tot_it = 0.0, 0
+    for _ in range(args.steps):
+        dt, done = o.run(args.ref_sample_iters)
+        tot_s += dt
+        tot_it += done
+    wall_s = time.perf_counter() - t0
+    per_iter = tot_s / max(tot_it, 1)
+    v = round(o.projected_ms(per_iter), 3)
+    step_ms = round(1e3 * wall_s / max(args.steps, 1), 3)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": "gmres(30)", "pc": "bilu0", "rtol": 1e-8},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} of {full_iters} iterations per step, scaled"},
+            "config": bench_config(p, args.workload, args.pc, ws),
+            "value_is_projection": True,
+            "projection": f"value = oracle setup ({o.setup_s:.1f} s) + mean time per GMRES iteration over the "
+                          f"{args.steps} timed steps ({per_iter:.3f} s) x the oracle's {full_iters} iterations of "
+                          f"the full FP64 solve; ms_per_step is the measured time of one sampled step",
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": o.threads, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"each step: the first {args.ref_sample_iters} GMRES(30)+"
+                                       f"{args.pc.upper()} iterations from x0 = 0 (FP64 oracle, OpenMP build)"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -334,7 +392,7 @@ def run_cpr_orders(args):
     import synth
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    p = synth.workload(WORKLOAD)
+    p = synth.workload(MID)
     stream = torch.cuda.current_stream(dev).cuda_stream
     A = rsv.Matrix(p.nx, p.ny, p.nz, stream=stream)
     A.set_values(torch.from_numpy(p.vals).to(dev))
@@ -365,7 +423,7 @@ def run_cpr_orders(args):
                      "ms": round(e0.elapsed_time(e1) / args.steps, 3),
                      "iters": infos[-1]["iters"], "outer_iters": infos[-1].get("outer_iters", 0),
                      "true_relres": infos[-1]["true_relres"]})
-    print(json.dumps({"mode": "cpr-orders", "workload": WORKLOAD, "solver": "gmres(30)", "rtol": 1e-8,
+    print(json.dumps({"mode": "cpr-orders", "workload": MID, "solver": "gmres(30)", "rtol": 1e-8,
                       "steps": args.steps, "warmup": args.warmup, "results": rows}))
     return 0
 
@@ -486,18 +544,19 @@ def run_profile_conv():
     return 0
 
 
-def run_profile_mode(mode):
+def run_profile_mode(args):
     """Small, self-checking runs of the hot path for ncu (no timing is reported)."""
     import torch
 
     import paper_1602_05901_gb300 as rsv
     import synth
-    p = synth.workload(WORKLOAD)
+    mode = args.mode
+    p = synth.workload(args.workload)
     A = rsv.Matrix(p.nx, p.ny, p.nz)
     A.set_values(p.vals)
     if mode == "profile-solve":
         s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=60, precision="mixed")
-        s.setup("bilu0")
+        s.setup(args.pc)
         b = torch.from_numpy(p.b).cuda()
         x = torch.zeros_like(b)
         st, info = s.solve(b, x)
@@ -522,15 +581,209 @@ def run_profile_mode(mode):
     return 0
 
 
+PC_DESC = {"cpr": "CPR-PF: quasi-IMPES, GMG V-cycle (2 red-black sweeps, <= 6 levels), block ILU(0) "
+                  "(i+j+k wavefront tiles)",
+           "bilu0": "block ILU(0) (i+j+k wavefront tiles)"}
+MOBILITY_READING = ("M_ij: off-diagonal entries U(0.1,1), each diagonal entry U(0.1,1) plus its row's three draws "
+                    "(row-diagonally dominant); nine i.i.d. U(0.1,1) entries make the Jacobian indefinite")
+
+
+def bench_config(p, workload, pc, ws):
+    return {"workload": workload, "grid": [p.nx, p.ny, p.nz], "cells": p.nb, "unknowns": p.n, "nnzb": p.nnzb,
+            "solver": "gmres(30)", "pc": PC_DESC[pc], "rtol": 1e-8, "x0": "zero",
+            "precision": "value: FP32 inner solves (inner rtol 1e-5; the last step only to what the target "
+                         "needs) under FP64 refinement; fp64: plain FP64",
+            "mobility_reading": MOBILITY_READING, "parallelism": f"replicas x{ws}",
+            "l2": f"inputs larger than L2 (FP64 blocks {p.vals.nbytes / 1e6:.0f} MB > 129 MB), no flush"}
+
+
+def source_sha(*names):
+    """Short hash of kernel sources: a recorded ncu traffic figure holds only for the sources it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1602_05901_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch from one ncu capture (read + write), or None when the kernel's sources
+    changed since the capture."""
+    entry = NCU_TRAFFIC.get(key)
+    if not entry:
+        return None
+    traffic, srcs, sha = entry
+    return traffic if source_sha(*srcs) == sha else None
+
+
+def run_bench(args, rank, ws, local, dist):
+    import numpy as np  # noqa: F401
+    import torch
+
+    import paper_1602_05901_gb300 as rsv
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = synth.workload(args.workload)
+    A = rsv.Matrix(p.nx, p.ny, p.nz, stream=stream)
+    vals_d = torch.from_numpy(p.vals).to(dev)
+    A.set_values(vals_d)
+    del vals_d
+    b = torch.from_numpy(p.b).to(dev)
+    x = torch.zeros_like(b)
+    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=6000, precision="mixed")
+    s64 = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=6000, precision="fp64")
+
+    def step(solver):
+        solver.setup(args.pc)
+        x.zero_()
+        st, info = solver.solve(b, x)
+        if st != rsv.RSV_OK:
+            raise RuntimeError(f"solve failed: {rsv.status_string(st)} {info}")
+        return info
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(solver, steps):
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = rsv.rsv_kernel_launches()
+        e0.record(stream)
+        infos = [step(solver) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_ = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
+        return ms_, infos[-1], rsv.rsv_kernel_launches() - l0
+
+    fp64_steps = max(1, min(args.steps, args.fp64_steps))
+    for _ in range(args.warmup):
+        step(s)
+    step(s64)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    ms, info, launches = timed(s, args.steps)
+    ms64, info64, _ = timed(s64, fp64_steps)
+    clocks = sampler.stop()
+
+    # ---- kernel microbenchmarks on the same stream (CUDA events)
+    peak, peak_src = hbm_peak()
+
+    def event_ms(fn, reps):
+        for _ in range(3):
+            fn()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    xs = torch.randn(p.n, dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    xs32, ys32 = xs.float(), torch.empty(p.n, dtype=torch.float32, device=dev)
+    spmv_ms = event_ms(lambda: A.spmv(xs, ys), 30)
+    spmv32_ms = event_ms(lambda: A.spmv(xs32, ys32), 30)
+    sb, sb32 = spmv_bytes(p.nb, p.nnzb), spmv_bytes(p.nb, p.nnzb, 4)
+    spmv_gbs, spmv32_gbs = sb / (spmv_ms * 1e-3) / 1e9, sb32 / (spmv32_ms * 1e-3) / 1e9
+    # the mixed path's preconditioner stages, FP32: block ILU(0) alone and the whole CPR apply
+    s_ilu = rsv.Solver(A, precision="mixed")
+    s_ilu.setup("bilu0")
+    zs32 = torch.empty_like(xs32)
+    ilu32_ms = event_ms(lambda: s_ilu.apply(xs32, zs32), 10)
+    del s_ilu
+    s.setup(args.pc)
+    pc32_ms = event_ms(lambda: s.apply(xs32, zs32), 10)
+    ib32 = ilu_apply_bytes(p.nb, p.nnzb, 4)
+    ilu32_gbs = ib32 / (ilu32_ms * 1e-3) / 1e9
+    # dominant kernel of the timed (mixed) path per inner iteration: the FP32 ILU(0) sweeps (one per
+    # preconditioner application) against the FP32 SpMV (one per iteration, two with CPR)
+    spmv_per_iter = 2 if args.pc == "cpr" else 1
+    if ilu32_ms >= spmv_per_iter * spmv32_ms:
+        dom = {"kernel": "block ILU(0) apply, FP32 (forward + backward tile sweeps)", "ms": ilu32_ms, "bytes": ib32,
+               "gbs": ilu32_gbs, "traffic": recorded_traffic("ilu_apply_f32_" + args.workload)}
+    else:
+        dom = {"kernel": "BSR SpMV FP32", "ms": spmv32_ms, "bytes": sb32, "gbs": spmv32_gbs,
+               "traffic": recorded_traffic("spmv_f32_" + args.workload)}
+    roofline = {"bound": "hbm", "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(dom["gbs"] / peak, 4), "traffic": dom["traffic"], "kernel": dom["kernel"],
+                "algorithmic_bytes_per_launch": dom["bytes"], "avg_launch_ms": round(dom["ms"], 4),
+                "peak_source": peak_src}
+    del xs, ys, xs32, ys32, zs32
+
+    # ---- end to end through the C ABI with host buffers: values, b and x in, x out, every step
+    vals_h = torch.from_numpy(p.vals).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        A.set_values(vals_h.numpy())
+        s.setup(args.pc)
+        x_h.zero_()
+        st, einfo = s.solve(b_h.numpy(), x_h.numpy())
+        assert st == rsv.RSV_OK, rsv.status_string(st)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    wall_e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+    h2d = p.vals.nbytes + p.b.nbytes + p.b.nbytes
+    d2h = p.b.nbytes
+    del vals_h
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        full = golden_iters(args.workload, f"gmres/{args.pc}") or info64["iters"]
+        cpu = cpu_baseline(p, args.workload, args.pc, full, args.cpu_sample_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
+            "config": bench_config(p, args.workload, args.pc, ws),
+            "iters": info["iters"], "outer_iters": info["outer_iters"], "true_relres": info["true_relres"],
+            "ms_setup": round(info["ms_setup"], 3), "ms_solve": round(info["ms_solve"], 3),
+            "fp64": {"ms_per_step": round(ms64, 3), "steps": fp64_steps, "warmup": 1, "iters": info64["iters"],
+                     "true_relres": info64["true_relres"], "ms_setup": round(info64["ms_setup"], 3),
+                     "speedup_mixed_over_fp64": round(ms64 / ms, 3),
+                     "oracle_iters": golden_iters(args.workload, f"gmres/{args.pc}")},
+            "oracle_refinement_iters": golden_iters(args.workload, f"refine-gmres/{args.pc}"),
+            "kernels": {"spmv_f64_ms": round(spmv_ms, 4), "spmv_f64_gbs": round(spmv_gbs, 1),
+                        "spmv_f64_frac": round(spmv_gbs / peak, 4),
+                        "spmv_f64_gflops": round(spmv_flops(p.nnzb) / (spmv_ms * 1e-3) / 1e9, 1),
+                        "spmv_f32_ms": round(spmv32_ms, 4), "spmv_f32_gbs": round(spmv32_gbs, 1),
+                        "spmv_f32_frac": round(spmv32_gbs / peak, 4), "spmv_algorithmic_bytes": [sb, sb32],
+                        "ilu_apply_f32_ms": round(ilu32_ms, 4), "ilu_apply_f32_gbs": round(ilu32_gbs, 1),
+                        "pc_apply_f32_ms": round(pc32_ms, 4)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "steps": args.e2e_steps,
+                    "wall_ms": round(wall_e2e_ms, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "rsv_mat_set_values + rsv_precond_setup + rsv_solve_ptr on pinned host buffers"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsv", choices=["rsv", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["large_256x256x128", "mid_100x100x50"])
+    ap.add_argument("--pc", default=PC, choices=["cpr", "bilu0"])
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 solves (at most --steps)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-iters", type=int, default=60)
-    ap.add_argument("--ref-sample-iters", type=int, default=30)
+    ap.add_argument("--cpu-sample-iters", type=int, default=10)
+    ap.add_argument("--ref-sample-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-train", type=int, default=12, help="learned mode: training systems")
     ap.add_argument("--learned-epochs", type=int, default=20, help="learned mode: epochs")
@@ -556,7 +809,7 @@ def main():
     if args.mode == "learned":
         return run_learned(args)
     if args.mode != "bench":
-        return run_profile_mode(args.mode)
+        return run_profile_mode(args)
     if args.warmup < 3 and args.impl == "rsv":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
@@ -566,152 +819,10 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return rc
-
-    import numpy as np
-    import torch
-
-    import paper_1602_05901_gb300 as rsv
-    import synth
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    p = synth.workload(WORKLOAD)
-    A = rsv.Matrix(p.nx, p.ny, p.nz, stream=stream)
-    vals_d = torch.from_numpy(p.vals).to(dev)
-    A.set_values(vals_d)
-    b = torch.from_numpy(p.b).to(dev)
-    x = torch.zeros_like(b)
-    s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision="mixed")
-    s64 = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=4000, precision="fp64")
-
-    def step(solver):
-        solver.setup("bilu0")
-        x.zero_()
-        st, info = solver.solve(b, x)
-        if st != rsv.RSV_OK:
-            raise RuntimeError(f"solve failed: {rsv.status_string(st)} {info}")
-        return info
-
-    def timed(solver, steps):
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        l0 = rsv.rsv_kernel_launches()
-        e0.record(stream)
-        infos = [step(solver) for _ in range(steps)]
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_ = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
-        return ms_, infos[-1], rsv.rsv_kernel_launches() - l0
-
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
-        step(s)
-        step(s64)
-    torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local)
-    ms, info, launches = timed(s, args.steps)
-    ms64, info64, _ = timed(s64, max(1, args.steps))
-    clocks = sampler.stop()
-
-    # ---- kernel microbenchmarks on the same stream (CUDA events)
-    peak, peak_src = hbm_peak()
-
-    def event_ms(fn, reps):
-        for _ in range(3):
-            fn()
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / reps
-
-    xs = torch.randn(p.n, dtype=torch.float64, device=dev)
-    ys = torch.empty_like(xs)
-    xs32, ys32 = xs.float(), torch.empty(p.n, dtype=torch.float32, device=dev)
-    spmv_ms = event_ms(lambda: A.spmv(xs, ys), 50)
-    spmv32_ms = event_ms(lambda: A.spmv(xs32, ys32), 50)
-    sb, sb32 = spmv_bytes(p.nb, p.nnzb), spmv_bytes(p.nb, p.nnzb, 4)
-    spmv_gbs, spmv32_gbs = sb / (spmv_ms * 1e-3) / 1e9, sb32 / (spmv32_ms * 1e-3) / 1e9
-    s.setup("bilu0")
-    s64.setup("bilu0")
-    zs32 = torch.empty_like(xs32)
-    ilu32_ms = event_ms(lambda: s.apply(xs32, zs32), 20)
-    zs = torch.empty_like(xs)
-    ilu_ms = event_ms(lambda: s64.apply(xs, zs), 10)
-    ib32 = ilu_apply_bytes(p.nb, p.nnzb, 4)
-    ilu32_gbs = ib32 / (ilu32_ms * 1e-3) / 1e9
-    ilu_gflops = ilu_apply_flops(p.nb, p.nnzb) / (ilu_ms * 1e-3) / 1e9
-    # dominant kernel of the timed (mixed) path per inner iteration: FP32 ILU apply vs FP32 SpMV
-    if ilu32_ms >= spmv32_ms:
-        dom = {"kernel": "block ILU(0) apply, FP32 (forward+backward tile sweeps)", "ms": ilu32_ms, "bytes": ib32,
-               "gbs": ilu32_gbs, "traffic": NCU_TRAFFIC["ilu_apply_f32"]}
-    else:
-        dom = {"kernel": "BSR SpMV FP32", "ms": spmv32_ms, "bytes": sb32, "gbs": spmv32_gbs,
-               "traffic": NCU_TRAFFIC["spmv_f32"]}
-    roofline = {"bound": "hbm", "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(dom["gbs"] / peak, 4), "traffic": dom["traffic"], "kernel": dom["kernel"],
-                "algorithmic_bytes_per_launch": dom["bytes"], "avg_launch_ms": round(dom["ms"], 4),
-                "peak_source": peak_src}
-
-    # ---- end to end through the C ABI with host buffers
-    vals_h = torch.from_numpy(p.vals).pin_memory()
-    b_h = torch.from_numpy(p.b).pin_memory()
-    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
-        A.set_values(vals_h.numpy())
-        s.setup("bilu0")
-        x_h.zero_()
-        st, einfo = s.solve(b_h.numpy(), x_h.numpy())
-        assert st == rsv.RSV_OK, rsv.status_string(st)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    wall_e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
-    h2d = p.vals.nbytes + p.b.nbytes + p.b.nbytes
-    d2h = p.b.nbytes
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, info64["iters"], args.cpu_sample_iters)
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [p.nx, p.ny, p.nz], "cells": p.nb, "unknowns": p.n,
-                       "nnzb": p.nnzb, "solver": "gmres(30)", "pc": "bilu0 (i+j+k wavefront tiles)",
-                       "precision": "mixed: FP32 inner (inner rtol 1e-5) + FP64 refinement",
-                       "rtol": 1e-8, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (FP64 blocks 249 MB > 129 MB), no flush"},
-            "iters": info["iters"], "outer_iters": info["outer_iters"], "true_relres": info["true_relres"],
-            "ms_setup": round(info["ms_setup"], 3), "ms_solve": round(info["ms_solve"], 3),
-            "fp64": {"ms_per_step": round(ms64, 3), "iters": info64["iters"], "true_relres": info64["true_relres"],
-                     "speedup_mixed_over_fp64": round(ms64 / ms, 3),
-                     "ilu_apply_ms": round(ilu_ms, 4), "ilu_apply_gflops": round(ilu_gflops, 1),
-                     "ilu_frac_of_fp64_peak": round(ilu_gflops / (FP64_PEAK_TFLOPS * 1e3), 4)},
-            "spmv": {"gbs": round(spmv_gbs, 1), "frac_of_peak": round(spmv_gbs / peak, 4), "avg_launch_ms":
-                     round(spmv_ms, 4), "algorithmic_bytes": sb,
-                     "gflops_fp64": round(spmv_flops(p.nnzb) / (spmv_ms * 1e-3) / 1e9, 1),
-                     "fp32_gbs": round(spmv32_gbs, 1), "fp32_frac_of_peak": round(spmv32_gbs / peak, 4),
-                     "fp32_avg_launch_ms": round(spmv32_ms, 4)},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "wall_ms": round(wall_e2e_ms, 3),
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-        }
-        print(json.dumps(line), flush=True)
+    rc = run_bench(args, rank, ws, local, dist)
     if dist is not None:
         dist.destroy_process_group()
-    return 0
+    return rc
 
 
 if __name__ == "__main__":

@@ -112,13 +112,18 @@ typedef struct {
  * (Section "Numerical experiments" names quasi-IMPES and ABF):
  *   0  quasi-IMPES: w_c = (1, -D01/D11, -D02/D22), D = A_cc (default);
  *   1  ABF: w_c = first row of D^{-1} (each block row premultiplied by D^{-1});
- *      RSV_ESINGULAR at setup when |det D| <= 1e-300.
- * The pressure operator is A_pp(c, l) = w_c . A_cl[:, 0] either way. */
+ *      RSV_ESINGULAR at setup when |det D| <= 1e-300;
+ *   2  true-IMPES: w_c = first row of C_c^{-1}, C_c the cell's accumulation
+ *      block (the time-derivative part of A_cc, given by
+ *      rsv_precond_set_accumulation; RSV_EINVAL at setup without it), so that
+ *      w_c C_c = (1, 0, 0): the secondary unknowns leave the accumulation terms.
+ *      RSV_ESINGULAR at setup when |det C_c| <= 1e-300.
+ * The pressure operator is A_pp(c, l) = w_c . A_cl[:, 0] in every case. */
 typedef struct {
     int gmg_max_levels;    /* <= 8 */
     int gmg_max_coarse;    /* stop coarsening at or below this many cells */
     int gmg_sweeps;        /* red-black Gauss-Seidel sweeps before and after */
-    int decoupling;        /* 0 quasi-IMPES, 1 ABF */
+    int decoupling;        /* 0 quasi-IMPES, 1 ABF, 2 true-IMPES */
 } rsv_pc_params;
 
 /* Filled by rsv_solve. */
@@ -260,6 +265,12 @@ RSV_API void rsv_solver_destroy(rsv_solver *s);
  *         RSV_ENOTSUP for a batch matrix (more than one grid).
  * params may be NULL (defaults); RSV_EINVAL for a parameter out of range. */
 RSV_API rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *params);
+/* The accumulation blocks C_c of the Jacobian (its time-derivative part; the
+ * flux terms excluded), float64[nb][3][3] row-major in cell order, host
+ * (on_device = 0) or device (on_device = 1); copied into the solver for the
+ * true-IMPES decoupling (rsv_pc_params.decoupling = 2) of later setups.
+ * acc = NULL drops them.  Synchronises the solver's stream. */
+RSV_API rsv_status rsv_precond_set_accumulation(rsv_solver *s, const double *acc, int on_device);
 /* z = M^{-1} r with the current preconditioner of an FP64 solver; device
  * float64[3*nb]; r and z must not overlap.  Returns before the GPU work ends
  * (stream-ordered); a device-side failure surfaces at the next rsv_solve. */

@@ -31,7 +31,7 @@ OK, EINVAL, ENOMEM, ESINGULAR, EBREAKDOWN, ENOCONV, ENAN = 0, 1, 2, 5, 6, 7, 9
 # "cpr" is CPR-PF (pressure stage, then full stage); the other orders follow the
 # paper's CPR-FP, CPR-FPF and CPR-FFPF algorithms
 PC = {"none": 0, "bjacobi": 1, "bilu0": 2, "cpr": 3, "cpr_fp": 5, "cpr_fpf": 6, "cpr_ffpf": 7}
-DECOUPLING = {"qi": 0, "abf": 1}
+DECOUPLING = {"qi": 0, "abf": 1, "timpes": 2}
 
 
 def build(force: bool = False) -> str:
@@ -83,7 +83,7 @@ def lib():
             "or_gs_colour": (None, [I, I, I, P, P, P, I]),
             "or_gmg_vcycle": (I, [I, I, I, P, I, I, I, P, P, P]),
             "or_create": (P, [I, I, I, P, P, P, I]), "or_destroy": (None, [P]),
-            "or_setup": (I, [P, I, I, I, I, I, I]), "or_decouple_setup": (I, [I, I, I, P, P, P, I, P, P]), "or_pc_apply": (I, [P, P, P]),
+            "or_setup": (I, [P, I, I, I, I, I, I]), "or_decouple_setup": (I, [I, I, I, P, P, P, I, P, P, P]), "or_set_accumulation": (None, [P, P]), "or_pc_apply": (I, [P, P, P]),
             "or_get_factors": (None, [P, P, P, P]), "or_gmg_levels": (I, [P]),
             "or_gmres": (I, [P, P, P, I, D, I, I, P]),
             "or_bicgstab": (I, [P, P, P, D, D, I, P]),
@@ -186,13 +186,16 @@ def qi_setup(nx, ny, nz, row_ptr, col_idx, vals):
     return st, w, a7
 
 
-def decouple_setup(nx, ny, nz, row_ptr, col_idx, vals, decoupling="qi"):
-    """Weights w [nb,3] and pressure stencil [nb,7] for decoupling "qi" (quasi-IMPES) or "abf"."""
+def decouple_setup(nx, ny, nz, row_ptr, col_idx, vals, decoupling="qi", acc=None):
+    """Weights w [nb,3] and pressure stencil [nb,7] for decoupling "qi" (quasi-IMPES), "abf" or
+    "timpes" (true-IMPES: needs the accumulation blocks acc [nb,3,3])."""
     rp, ci, v = _i32(row_ptr), _i32(col_idx), _f64(vals)
     nb = nx * ny * nz
     w = np.zeros((nb, 3))
     a7 = np.zeros((nb, 7))
-    st = lib().or_decouple_setup(nx, ny, nz, _p(rp), _p(ci), _p(v), DECOUPLING[decoupling], _p(w), _p(a7))
+    keep = _f64(acc) if acc is not None else None   # alive across the call
+    accp = _p(keep) if keep is not None else None
+    st = lib().or_decouple_setup(nx, ny, nz, _p(rp), _p(ci), _p(v), DECOUPLING[decoupling], accp, _p(w), _p(a7))
     return st, w, a7
 
 
@@ -247,7 +250,7 @@ class System:
     """A BSR system plus one preconditioner, driven through the C oracle."""
 
     def __init__(self, nx, ny, nz, row_ptr, col_idx, vals, pc="none", float_round=False,
-                 gmg_levels=6, gmg_coarse=512, gmg_sweeps=2, decoupling="qi"):
+                 gmg_levels=6, gmg_coarse=512, gmg_sweeps=2, decoupling="qi", acc=None):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.nb = nx * ny * nz
         self._rp, self._ci = _i32(row_ptr), _i32(col_idx)
@@ -255,6 +258,8 @@ class System:
         self._h = lib().or_create(nx, ny, nz, _p(self._rp), _p(self._ci), _p(self._v), int(float_round))
         if not self._h:
             raise MemoryError("oracle system allocation failed")
+        if acc is not None:
+            lib().or_set_accumulation(self._h, _p(_f64(acc)))
         self.setup_status = lib().or_setup(self._h, PC[pc], gmg_levels, gmg_coarse, gmg_sweeps,
                                            int(float_round), DECOUPLING[decoupling])
         self.pc = pc

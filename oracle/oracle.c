@@ -277,17 +277,23 @@ static int stencil_slot(int di, int dj, int dk) {
  * quasi-IMPES reading w_c = (1, -D01/D11, -D02/D22); 1: ABF (alternate block
  * factorization, Section "Numerical experiments" names it beside quasi-IMPES),
  * which premultiplies each block row by D^{-1}, so w_c is the first row of
- * D^{-1} = adj(D) / det(D) (D = A_cc).  Either way A_pp(c, l) = w_c . A_cl[:, 0]. */
+ * D^{-1} = adj(D) / det(D) (D = A_cc); 2: true-IMPES (named beside them), the
+ * same with D = C_c, the cell's accumulation block (the time-derivative part
+ * of the Jacobian, passed in as acc[nb][3][3]): w_c C_c = (1, 0, 0) removes
+ * the secondary unknowns from the accumulation terms.  Every time
+ * A_pp(c, l) = w_c . A_cl[:, 0]. */
 int or_decouple_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v, int decoupling,
-                      double *w, double *a7) {
+                      const double *acc, double *w, double *a7) {
     int nb = nx * ny * nz;
+    if (decoupling == 2 && !acc) return OR_EINVAL;
     memset(a7, 0, sizeof(double) * 7 * (size_t)nb);
     for (int c = 0; c < nb; ++c) {
         int32_t pd = find_block(rp, ci, c, c);
         if (pd < 0) return OR_EINVAL;
-        const double *d = v + 9 * (int64_t)pd;
+        /* ABF inverts the diagonal block of A; true-IMPES the cell's accumulation block */
+        const double *d = (decoupling == 2) ? acc + 9 * (int64_t)c : v + 9 * (int64_t)pd;
         double *wc = w + 3 * (int64_t)c;
-        if (decoupling == 1) {
+        if (decoupling == 1 || decoupling == 2) {
             /* first row of the adjugate: cofactors of the first column */
             const double c0 = d[4] * d[8] - d[5] * d[7];
             const double c1 = d[5] * d[6] - d[3] * d[8];
@@ -317,7 +323,7 @@ int or_decouple_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *
 }
 
 int or_qi_setup(int nx, int ny, int nz, const int32_t *rp, const int32_t *ci, const double *v, double *w, double *a7) {
-    return or_decouple_setup(nx, ny, nz, rp, ci, v, 0, w, a7);
+    return or_decouple_setup(nx, ny, nz, rp, ci, v, 0, NULL, w, a7);
 }
 
 /* Pi_r with the decoupling folded in: p_i = w_i . r_i. */
@@ -520,7 +526,8 @@ typedef struct {
     int pc;
     double *dinv;     /* block Jacobi */
     double *lu, *udinv; /* block ILU(0) */
-    double *w, *a7;   /* quasi-IMPES weights, pressure stencil */
+    double *w, *a7;   /* decoupling weights, pressure stencil */
+    double *acc;      /* accumulation blocks [nb][3][3] (true-IMPES), or NULL */
     or_gmg gmg;
     double *tmp_p, *tmp_x, *tmp_r;
     int64_t pc_applies;
@@ -544,7 +551,7 @@ or_system *or_create(int nx, int ny, int nz, const int32_t *rp, const int32_t *c
 
 void or_destroy(or_system *s) {
     if (!s) return;
-    free(s->v); free(s->dinv); free(s->lu); free(s->udinv); free(s->w); free(s->a7);
+    free(s->v); free(s->dinv); free(s->lu); free(s->udinv); free(s->w); free(s->a7); free(s->acc);
     free(s->tmp_p); free(s->tmp_x); free(s->tmp_r);
     if (s->gmg.nlev) gmg_free(&s->gmg);
     free(s);
@@ -555,6 +562,15 @@ void or_destroy(or_system *s) {
  * 5 CPR-FP, 6 CPR-FPF, 7 CPR-FFPF (the same two stages in the other orders).
  * float_round != 0 rounds the stored factors to float after setup; decoupling:
  * 0 quasi-IMPES, 1 ABF (CPR only). */
+/* Accumulation blocks for true-IMPES decoupling (nb blocks of 3x3, copied). */
+void or_set_accumulation(or_system *s, const double *acc) {
+    free(s->acc);
+    s->acc = NULL;
+    if (!acc) return;
+    s->acc = (double *)malloc(sizeof(double) * 9 * (size_t)s->nb);
+    memcpy(s->acc, acc, sizeof(double) * 9 * (size_t)s->nb);
+}
+
 int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweeps, int float_round, int decoupling) {
     int nb = s->nb;
     s->pc = pc;
@@ -579,7 +595,7 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
     if (is_cpr(pc)) {
         s->w = (double *)malloc(sizeof(double) * 3 * (size_t)nb);
         s->a7 = (double *)malloc(sizeof(double) * 7 * (size_t)nb);
-        st = or_decouple_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, decoupling, s->w, s->a7);
+        st = or_decouple_setup(s->nx, s->ny, s->nz, s->rp, s->ci, s->v, decoupling, s->acc, s->w, s->a7);
         if (st) return st;
         if (float_round) {
             for (size_t q = 0; q < 3 * (size_t)nb; ++q) s->w[q] = round_f32(s->w[q]);

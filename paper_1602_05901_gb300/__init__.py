@@ -91,6 +91,7 @@ _SIGS = {
     "rsv_solver_create": (_I, [_P, ctypes.POINTER(rsv_solver_params), _PP]),
     "rsv_solver_destroy": (None, [_P]),
     "rsv_precond_setup": (_I, [_P, _I, ctypes.POINTER(rsv_pc_params)]),
+    "rsv_precond_set_accumulation": (_I, [_P, _P, _I]),
     "rsv_precond_apply": (_I, [_P, _P, _P]),
     "rsv_precond_apply_f32": (_I, [_P, _P, _P]),
     "rsv_precond_get_dinv": (_I, [_P, _P]),
@@ -175,7 +176,7 @@ def solver_params(solver="gmres", restart=30, rtol=1e-8, atol=0.0, btol=1e-30, m
     return p
 
 
-DECOUPLING = {"qi": 0, "abf": 1}
+DECOUPLING = {"qi": 0, "abf": 1, "timpes": 2}
 
 
 def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2, decoupling="qi"):
@@ -323,6 +324,16 @@ class Solver:
                                     ctypes.byref(pc_params(**pcp)))
         check(st, "rsv_precond_setup")
 
+    def set_accumulation(self, acc):
+        """Accumulation blocks [nb,3,3] (host numpy or CUDA tensor) for decoupling="timpes"; None drops them."""
+        if acc is None:
+            check(_lib.rsv_precond_set_accumulation(self.handle, None, 0), "rsv_precond_set_accumulation")
+            return
+        on_dev = int(hasattr(acc, "is_cuda") and acc.is_cuda)
+        if not on_dev:
+            acc = np.ascontiguousarray(acc, dtype=np.float64)
+        check(_lib.rsv_precond_set_accumulation(self.handle, _ptr(acc), on_dev), "rsv_precond_set_accumulation")
+
     def apply(self, r, z):
         if r.dtype.itemsize == 4:
             check(_lib.rsv_precond_apply_f32(self.handle, _ptr(r), _ptr(z)), "rsv_precond_apply_f32")
@@ -398,7 +409,8 @@ class Solver:
         """Independent per-grid solves of a batch matrix. Returns (status, [info dict per grid])."""
         infos = (rsv_solve_info * self.A.nsys)()
         if isinstance(b, Vector) or (hasattr(b, "is_cuda") and b.is_cuda):
-            st = _lib.rsv_solve_batched(self.handle, Vector.of(b).handle, Vector.of(x).handle, infos)
+            bv, xv = Vector.of(b), Vector.of(x)  # keep the handles alive across the call
+            st = _lib.rsv_solve_batched(self.handle, bv.handle, xv.handle, infos)
         else:
             st = _lib.rsv_solve_batched_ptr(self.handle, _ptr(b), _ptr(x), 0, infos)
         return st, [i.as_dict() for i in infos]

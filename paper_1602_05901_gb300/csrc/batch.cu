@@ -625,14 +625,14 @@ extern "C" rsv_status rsv_solve_batched_ptr(rsv_solver *s, const double *b, doub
         // FP64: BiCGSTAB on A x = b from the given x (solve for the correction of b - A x0)
         double *r0 = s->r64;
         RSV_CUDA_TRY(cudaMemcpyAsync(r0, db, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
-        RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, r0, nullptr));
+        RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, r0, nullptr, &s->ds->status, (unsigned long long)s->p.watchdog * 1000ull));
         RSV_TRY(bicg_inner<double>(s, B, r0, (double *)B->xin, s->p.rtol, 0));
         RSV_CUDA_TRY(launch_axpby<double>(s->st, n, 1.0, (const double *)B->xin, 1.0, dx, dx));
     } else {
         double *rn = d.red + 7 * nsys;  // outer residual norms
         for (int outer = 0; outer <= s->p.max_outer; ++outer) {
             RSV_CUDA_TRY(cudaMemcpyAsync(s->r64, db, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
-            RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, s->r64, nullptr));
+            RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, s->r64, nullptr, &s->ds->status, (unsigned long long)s->p.watchdog * 1000ull));
             RSV_CUDA_TRY(seg_dot<double>(s, B, s->r64, s->r64, (const double *)nullptr, rn, nullptr, 1, 0, nullptr));
             count_launches(1);
             b_outer_check<<<sgrid(nsys), 128, 0, s->st>>>(d, nsys, s->p.rtol, rn, s->p.max_outer, s->p.maxit);
@@ -656,7 +656,7 @@ extern "C" rsv_status rsv_solve_batched_ptr(rsv_solver *s, const double *b, doub
     // FP64 true residual per system
     double *rn = d.red + 7 * nsys;
     RSV_CUDA_TRY(cudaMemcpyAsync(s->r64, db, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->st));
-    RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, s->r64, nullptr));
+    RSV_CUDA_TRY(launch_spmv_f64(A, -1.0, dx, 1.0, s->r64, nullptr, &s->ds->status, (unsigned long long)s->p.watchdog * 1000ull));
     RSV_CUDA_TRY(seg_dot<double>(s, B, s->r64, s->r64, (const double *)nullptr, rn, nullptr, 1, 0, nullptr));
     std::vector<double> h_rn(nsys), h_bn(nsys), h_outer(nsys);
     std::vector<int> h_iters(nsys), h_status(nsys);

@@ -183,6 +183,76 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot_kernel(int64_t n, const T
     }
 }
 
+// Two multi-vector dot products in one read of the basis: ow[i] = <w, V_i> and
+// ou[i] = <u, V_i> for i < k (u is typically a column of V itself).  Groups of
+// eight basis vectors per pass over w and u, so a group's sixteen sums go
+// through the same butterfly reduction as the one-vector multi-dot.  Partial
+// slots: 2 g0 + i (w) and 2 g0 + 8 + i (u) for the group starting at g0.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kRedThreads, 2) mdot2_kernel(int64_t n, const T *__restrict__ w,
+                                                            const T *__restrict__ u, const T *__restrict__ V,
+                                                            int64_t ldv, int k, double *partial, double *ow,
+                                                            double *ou, unsigned *counter, const int *done) {
+    if (is_done(done)) return;
+    using VT = Vec<T>;
+    constexpr int G2 = kGroup / 2;
+    __shared__ double smg[kGroup][kRedThreads / 32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int g0 = 0; g0 < k; g0 += G2) {
+        Acc<T> aw[G2], au[G2];
+        const int kg = min(G2, k - g0);
+        int64_t tail = 0;
+        if (VEC) {
+            const int64_t nv = n / VT::N;
+            for (int64_t r = tid; r < nv; r += stride) {
+                const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
+                const typename VT::V ur = reinterpret_cast<const typename VT::V *>(u)[r];
+                typename VT::V vr[G2];
+#pragma unroll
+                for (int i = 0; i < G2; ++i)
+                    if (i < kg) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)(g0 + i) * ldv)[r];
+#pragma unroll
+                for (int i = 0; i < G2; ++i)
+                    if (i < kg) {
+#pragma unroll
+                        for (int q = 0; q < VT::N; ++q) {
+                            aw[i].add(VT::get(wr, q), VT::get(vr[i], q));
+                            au[i].add(VT::get(ur, q), VT::get(vr[i], q));
+                        }
+                    }
+            }
+            tail = nv * VT::N;
+        }
+        for (int64_t r = tail + tid; r < n; r += stride) {
+            const T wr = w[r], ur = u[r];
+#pragma unroll
+            for (int i = 0; i < G2; ++i)
+                if (i < kg) {
+                    const T vv = V[(int64_t)(g0 + i) * ldv + r];
+                    aw[i].add(wr, vv);
+                    au[i].add(ur, vv);
+                }
+        }
+        Part<T> vals[kGroup];
+#pragma unroll
+        for (int i = 0; i < G2; ++i) {
+            vals[i] = i < kg ? Part<T>::of(aw[i]) : Part<T>::zero();
+            vals[G2 + i] = i < kg ? Part<T>::of(au[i]) : Part<T>::zero();
+        }
+        block_partial_group<T>(vals, kGroup, smg, partial, 2 * g0);
+    }
+    if (last_cta(counter)) {
+        for (int i = threadIdx.x >> 5; i < 2 * k; i += kRedThreads / 32) {
+            const int vec = i / k, q = i - vec * k;  // output vec (0: w, 1: u), basis index q
+            const int slot = 2 * (q / G2) * G2 + vec * G2 + q % G2;
+            const double sum = final_sum(partial, slot);
+            if ((threadIdx.x & 31) == 0) (vec ? ou : ow)[q] = sum;
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 // out = base + sgn * sum_i c_i V_i, in the vector precision; ||out|| summed like the dot products.
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) maxpy_kernel(int64_t n, const T *base, const T *__restrict__ V,
@@ -445,6 +515,19 @@ cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int6
 }
 
 template <typename T>
+cudaError_t launch_mdot2(cudaStream_t st, int64_t n, const T *w, const T *u, const T *V, int64_t ldv, int k,
+                         double *partial, double *ow, double *ou, unsigned *counter, const int *done) {
+    if (k < 1 || k > kMaxRestart + 1) return cudaErrorInvalidValue;
+    rsv::count_launches(1);
+    if (vec_ok<T>(ldv, {w, u, V}))
+        mdot2_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, u, V, ldv, k, partial, ow, ou, counter, done);
+    else
+        mdot2_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, u, V, ldv, k, partial, ow, ou, counter,
+                                                                   done);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
                          double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done,
                          const int *skip) {
@@ -520,6 +603,8 @@ cudaError_t launch_add_f32_scaled(cudaStream_t st, int64_t n, const float *df, c
 #define RSV_BLAS_INST(T)                                                                                            \
     template cudaError_t launch_mdot<T>(cudaStream_t, int64_t, const T *, const T *, int64_t, int, double *,       \
                                         double *, unsigned *, const int *, double *, const int *);                 \
+    template cudaError_t launch_mdot2<T>(cudaStream_t, int64_t, const T *, const T *, const T *, int64_t, int,      \
+                                         double *, double *, double *, unsigned *, const int *);                   \
     template cudaError_t launch_maxpy<T>(cudaStream_t, int64_t, const T *, const T *, int64_t, int, const double *, \
                                          double, T *, double *, double *, unsigned *, const int *, const int *);    \
     template cudaError_t launch_maxpy_mdot<T>(cudaStream_t, int64_t, T *, const T *, int64_t, int, const double *,  \

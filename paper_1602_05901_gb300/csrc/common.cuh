@@ -43,6 +43,8 @@ struct DevState {
     double y[kMaxRestart];
     double h1[kMaxRestart + 1], h2[kMaxRestart + 1];  // CGS2 projection coefficients
     double red[kMaxRestart + 1];                       // generic reduction outputs
+    double G[(kMaxRestart + 1) * (kMaxRestart + 1)];   // Gram matrix of the current Arnoldi basis, row-major
+    double gcol[kMaxRestart + 1];                      // <v_j, v_i>, i <= j: column j of G
     double beta, hn, wnorm, tol;
     double rho, rho1, alpha, omega;
     double bnorm;
@@ -85,12 +87,14 @@ struct Cpr {  // CPR pressure stage: quasi-IMPES weights and the GMG hierarchy (
     int dims[kMaxLevels][3] = {};
     double *a7[kMaxLevels] = {};  // FP64 seven-point stencils, slot-major [7][n]
     void *a7f[kMaxLevels] = {};   // FP32 copies (mixed precision)
+    void *a7s[kMaxLevels] = {};   // colour-split copies in T for the smoother (every level but the coarsest)
     void *x[kMaxLevels] = {}, *b[kMaxLevels] = {};  // per-level solution and right-hand side (T)
     double *w64 = nullptr;        // quasi-IMPES weights [nb][3], FP64
     void *w = nullptr;            // weights in T
     double *dense = nullptr, *minv = nullptr, *work = nullptr;  // coarsest LU / inverse / scratch
     int *piv = nullptr;
     void *r = nullptr, *z = nullptr, *xp = nullptr;  // full-stage residual and ILU correction (T)
+    void *apc = nullptr;          // pressure column of every block [nnzb][3] (T): CPR-PF's stage-two residual
 };
 
 struct Schedule {  // i+j+k wavefront hyperplanes
@@ -143,11 +147,17 @@ namespace rsv {
 // ---- launchers implemented in spmv.cu
 // One-time kernel attributes (large dynamic shared memory); called at matrix creation.
 cudaError_t spmv_init();
+// status (optional): receives RSV_ETIMEOUT when a CTA's staged copies do not arrive within
+// timeout_ns; the rows that CTA still owed are then written as NaN.
 cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
-                            const int *done);
+                            const int *done, int *status = nullptr, unsigned long long timeout_ns = 2000000000ull);
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
-                            const int *done);
+                            const int *done, int *status = nullptr, unsigned long long timeout_ns = 2000000000ull);
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b);
+// r = f - A (p_c, 0, 0)_c from the blocks' pressure columns apc [nnzb][3] (T = double or float).
+template <typename T>
+cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p, const T *f, T *r, const int *done,
+                                     int *status, unsigned long long timeout_ns);
 
 // ---- launchers implemented in blas.cu (T = double or float; reductions in FP64)
 // out[i] = <w, V_i> for i < k; V_i = V + i*ldv.  Deterministic two-level reduction.
@@ -157,6 +167,11 @@ template <typename T>
 cudaError_t launch_mdot(cudaStream_t st, int64_t n, const T *w, const T *V, int64_t ldv, int k, double *partial,
                         double *out, unsigned *counter, const int *done, double *self_nrm = nullptr,
                         const int *skip = nullptr);
+// ow[i] = <w, V_i> and ou[i] = <u, V_i> for i < k (k <= kMaxRestart + 1), one read of the basis;
+// partial needs 2 * 8 * ceil(k / 8) slots of kRedBlocks doubles.
+template <typename T>
+cudaError_t launch_mdot2(cudaStream_t st, int64_t n, const T *w, const T *u, const T *V, int64_t ldv, int k,
+                         double *partial, double *ow, double *ou, unsigned *counter, const int *done);
 // out = base + sgn * sum_i c[i] V_i (base may be null); if nrm != nullptr, *nrm = ||out||_2.
 template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
@@ -194,9 +209,9 @@ cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const T *dinv, const T 
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status);
 
 // ---- implemented in cpr.cu
-// decoupling: 0 quasi-IMPES, 1 ABF (rsv_pc_params)
-cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling, Cpr *P,
-                      int *status);
+// decoupling: 0 quasi-IMPES, 1 ABF, 2 true-IMPES from the accumulation blocks acc [nb][9] (rsv_pc_params)
+cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling,
+                      const double *acc, Cpr *P, int *status);
 void free_cpr(Cpr *P);
 template <typename T>
 cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,

@@ -52,7 +52,8 @@ __device__ __forceinline__ int slot_of(int di, int dj, int dk) {
 // Quasi-IMPES weights and the pressure stencil of the block row of cell c.
 template <typename Tv>
 __global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *__restrict__ v, int decoupling,
-                                double *__restrict__ w, double *__restrict__ a7, int *status) {
+                                const double *__restrict__ acc, double *__restrict__ w, double *__restrict__ a7,
+                                int *status) {
     const int64_t n = g.n();
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -63,10 +64,13 @@ __global__ void qi_setup_kernel(G3 g, const int32_t *__restrict__ rp, const Tv *
     for (int s = 0; s < 7; ++s) slot_pos[s] = has[s] ? q++ : -1;
     const Tv *dv = v + 9 * ((int64_t)rp[c] + slot_pos[3]);
     double d[9];
-    for (int q = 0; q < 9; ++q) d[q] = (double)dv[q];
+    if (decoupling == 2)  // true-IMPES: the cell's accumulation block instead of A's diagonal block
+        for (int q = 0; q < 9; ++q) d[q] = acc[9 * c + q];
+    else
+        for (int q = 0; q < 9; ++q) d[q] = (double)dv[q];
     double w0, w1, w2;
-    if (decoupling == 1) {
-        // ABF: the first row of D^{-1} = adj(D) / det(D), from the cofactors of D's first column
+    if (decoupling == 1 || decoupling == 2) {
+        // ABF / true-IMPES: the first row of D^{-1} = adj(D) / det(D), from the cofactors of D's first column
         const double c0 = d[4] * d[8] - d[5] * d[7];
         const double det = d[0] * c0 + d[1] * (d[5] * d[6] - d[3] * d[8]) + d[2] * (d[3] * d[7] - d[4] * d[6]);
         if (!(fabs(det) > 1e-300)) {
@@ -240,26 +244,76 @@ __global__ void coarse_apply_kernel(int n, const double *__restrict__ Minv, cons
     if (lane == 0) x[row] = (T)s;
 }
 
-// One red-black Gauss-Seidel half sweep: cells of colour (i+j+k) mod 2.
+// Colour-split position of the cell (2 h + parity, j, k) of colour `colour` in grid row
+// row = j + ny k: the row's red cells first (i ascending), then its black cells.  A row
+// starting with a red cell ((j + k) even) holds ceil(nx / 2) red cells, else floor(nx / 2).
+__device__ __forceinline__ int64_t split_pos(G3 g, int64_t row, int j, int k, int h, int colour) {
+    const int nred = (g.nx + 1 - ((j + k) & 1)) >> 1;
+    return row * g.nx + (colour == 0 ? h : nred + h);
+}
+
+// a7s[s][split_pos(c)] = a7[s][c] (converted to T).
 template <typename T>
-__global__ void rbgs_kernel(G3 g, const T *__restrict__ a7, const T *__restrict__ b, T *__restrict__ x, int colour,
-                            const int *done) {
-    if (gated(done)) return;
+__global__ void split_stencil_kernel(G3 g, const double *__restrict__ a7, T *__restrict__ a7s) {
     const int64_t n = g.n();
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n) return;
     int i, j, k;
     ijk(c, g, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    const int64_t ps = split_pos(g, c / g.nx, j, k, i >> 1, (i + j + k) & 1);
+    for (int s = 0; s < 7; ++s) a7s[(int64_t)s * n + ps] = (T)a7[(int64_t)s * n + c];
+}
+
+// One red-black Gauss-Seidel half sweep over the cells of colour (i+j+k) mod 2;
+// one thread per cell of that colour (a row of nx cells holds ceil(nx/2) or
+// floor(nx/2) of them).  Cells of one colour couple only to the other colour,
+// so the update x_c = (b_c - sum_n a_cn x_n) / a_cc reads only cells this
+// launch does not write.  MODE selects what the neighbours hold:
+//   0  x as stored;
+//   1  zero (the first half sweep of a V-cycle level from a zero guess:
+//      x_c = b_c / a_cc, and x need not be cleared first);
+//   2  x + P xc (the first half sweep after the coarse correction: the
+//      prolongation x += P xc is applied to the neighbours on the fly; this
+//      colour's own cells are overwritten, so the correction need not be
+//      stored for them, and the other colour's cells are overwritten by the
+//      next half sweep, which reads only this colour).
+// Each variant rounds exactly as the separate zeroing / prolongation kernels
+// followed by the plain half sweep.
+//
+// The coefficients come from a colour-split copy a7s (see split_pos): the cells
+// of one colour in a grid row are contiguous there, so a half sweep reads
+// only its own colour's coefficients, coalesced.
+template <typename T, int MODE>
+__global__ void rbgs_kernel(G3 g, const T *__restrict__ a7s, const T *__restrict__ b, T *__restrict__ x, int colour,
+                            const T *__restrict__ xc, G3 cg, const int *done) {
+    if (gated(done)) return;
+    const int64_t n = g.n();
+    const int half = (g.nx + 1) >> 1;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = q / half;  // row = j + ny k
+    if (row >= (int64_t)g.ny * g.nz) return;
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const int h = (int)(q - row * half);
+    const int i = 2 * h + ((colour + j + k) & 1);
+    if (i >= g.nx) return;
+    const int64_t c = row * g.nx + i;
+    const T *a7 = a7s + split_pos(g, row, j, k, h, colour);  // slot s at a7[s * n]
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
     T s = b[c];
-    if (k > 0) s -= a7[0 * n + c] * x[c - sz];
-    if (j > 0) s -= a7[1 * n + c] * x[c - sy];
-    if (i > 0) s -= a7[2 * n + c] * x[c - 1];
-    if (i < g.nx - 1) s -= a7[4 * n + c] * x[c + 1];
-    if (j < g.ny - 1) s -= a7[5 * n + c] * x[c + sy];
-    if (k < g.nz - 1) s -= a7[6 * n + c] * x[c + sz];
-    x[c] = s / a7[3 * n + c];
+    if (MODE != 1) {
+        auto nbr = [&](int64_t o, int ii, int jj, int kk) -> T {
+            T v = x[o];
+            if (MODE == 2) v += xc[(int64_t)(kk >> 1) * cg.nx * cg.ny + (int64_t)(jj >> 1) * cg.nx + (ii >> 1)];
+            return v;
+        };
+        if (k > 0) s -= a7[0 * n] * nbr(c - sz, i, j, k - 1);
+        if (j > 0) s -= a7[1 * n] * nbr(c - sy, i, j - 1, k);
+        if (i > 0) s -= a7[2 * n] * nbr(c - 1, i - 1, j, k);
+        if (i < g.nx - 1) s -= a7[4 * n] * nbr(c + 1, i + 1, j, k);
+        if (j < g.ny - 1) s -= a7[5 * n] * nbr(c + sy, i, j + 1, k);
+        if (k < g.nz - 1) s -= a7[6 * n] * nbr(c + sz, i, j, k + 1);
+    }
+    x[c] = s / a7[3 * n];
 }
 
 // b_coarse[C] = sum over the children f of C of (b_f - (A x)_f): residual and
@@ -337,6 +391,16 @@ __global__ void prolong_pressure_kernel(int64_t nb, const T *__restrict__ p, con
     r[3 * c + 2] = f[3 * c + 2];
 }
 
+// The pressure column of every block, apc[3 q + e] = A_q[e][0] (in the solver's precision).
+template <typename Tv, typename T>
+__global__ void pressure_columns_kernel(int64_t nnzb, const Tv *__restrict__ v, T *__restrict__ apc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnzb; q += (int64_t)gridDim.x * blockDim.x) {
+        apc[3 * q] = (T)v[9 * q];
+        apc[3 * q + 1] = (T)v[9 * q + 3];
+        apc[3 * q + 2] = (T)v[9 * q + 6];
+    }
+}
+
 // x_c += (p_c, 0, 0): a pressure-stage correction added to the iterate
 template <typename T>
 __global__ void prolong_add_pressure_kernel(int64_t nb, const T *__restrict__ p, T *__restrict__ x, const int *done) {
@@ -359,39 +423,46 @@ unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, 
 
 void free_cpr(Cpr *P) {
     for (int l = 0; l < kMaxLevels; ++l)
-        for (void *p : {(void *)P->a7[l], P->a7f[l], P->x[l], P->b[l]})
+        for (void *p : {(void *)P->a7[l], P->a7f[l], P->a7s[l], P->x[l], P->b[l]})
             if (p) cudaFree(p);
     for (void *p : {(void *)P->w64, P->w, (void *)P->minv, (void *)P->dense, (void *)P->piv, (void *)P->work,
-                    P->r, P->z, P->xp})
+                    P->r, P->z, P->xp, P->apc})
         if (p) cudaFree(p);
     *P = Cpr();
 }
 
 cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling,
-                      Cpr *P, int *status) {
-    free_cpr(P);
+                      const double *acc, Cpr *P, int *status) {
     cudaStream_t st = A->stream;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
-    P->mixed = mixed;
-    P->sweeps = sweeps;
     // level sizes: halve (ceil) each dimension while the level has more than max_coarse cells
+    int dims[kMaxLevels][3];
     G3 g{A->nx, A->ny, A->nz};
     int nl = 0;
-    P->dims[nl][0] = g.nx, P->dims[nl][1] = g.ny, P->dims[nl][2] = g.nz;
+    dims[nl][0] = g.nx, dims[nl][1] = g.ny, dims[nl][2] = g.nz;
     ++nl;
     max_levels = std::min(std::max(max_levels, 1), kMaxLevels);
     while (nl < max_levels && g.n() > max_coarse) {
         g = G3{(g.nx + 1) / 2, (g.ny + 1) / 2, (g.nz + 1) / 2};
-        P->dims[nl][0] = g.nx, P->dims[nl][1] = g.ny, P->dims[nl][2] = g.nz;
+        dims[nl][0] = g.nx, dims[nl][1] = g.ny, dims[nl][2] = g.nz;
         ++nl;
     }
+    // a new setup of the same hierarchy (the usual case: new values, same grid) reuses the buffers
+    bool same = P->w64 && P->mixed == mixed && P->nlev == nl;
+    for (int l = 0; same && l < nl; ++l)
+        for (int d = 0; d < 3; ++d) same = same && P->dims[l][d] == dims[l][d];
+    if (!same) free_cpr(P);
+    P->mixed = mixed;
+    P->sweeps = sweeps;
+    for (int l = 0; l < nl; ++l)
+        for (int d = 0; d < 3; ++d) P->dims[l][d] = dims[l][d];
     P->nlev = nl;
     const int64_t nb = A->nb;
     const int nc = (int)g.n();
     P->ncoarse = nc;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && !same) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
     };
     alloc((void **)&P->w64, sizeof(double) * 3 * nb);
     alloc(&P->w, es * 3 * nb);
@@ -399,6 +470,7 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
         const int64_t n = (int64_t)P->dims[l][0] * P->dims[l][1] * P->dims[l][2];
         alloc((void **)&P->a7[l], sizeof(double) * 7 * n);
         if (mixed) alloc(&P->a7f[l], sizeof(float) * 7 * n);
+        if (l + 1 < nl) alloc(&P->a7s[l], es * 7 * n);
         alloc(&P->x[l], es * n);
         alloc(&P->b[l], es * n);
     }
@@ -409,14 +481,15 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
     alloc(&P->r, es * 3 * nb);
     alloc(&P->z, es * 3 * nb);
     alloc(&P->xp, es * 3 * nb);
+    alloc(&P->apc, es * 3 * (size_t)A->nnzb);
     if (e != cudaSuccess) return e;
     G3 g0{A->nx, A->ny, A->nz};
     count_launches(1);
     if (mixed)
-        qi_setup_kernel<float><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v32, decoupling, P->w64, P->a7[0],
+        qi_setup_kernel<float><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v32, decoupling, acc, P->w64, P->a7[0],
                                                            status);
     else
-        qi_setup_kernel<double><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v, decoupling, P->w64, P->a7[0],
+        qi_setup_kernel<double><<<blocks(nb), 256, 0, st>>>(g0, A->d_rp, A->d_v, decoupling, acc, P->w64, P->a7[0],
                                                             status);
     for (int l = 0; l + 1 < nl; ++l) {
         G3 f{P->dims[l][0], P->dims[l][1], P->dims[l][2]}, c{P->dims[l + 1][0], P->dims[l + 1][1], P->dims[l + 1][2]};
@@ -428,6 +501,20 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
     coarse_dense_kernel<<<blocks(nc), 256, 0, st>>>(gc, P->a7[nl - 1], P->dense);
     coarse_lu_kernel<<<1, 1024, 0, st>>>(nc, P->dense, P->piv, status);
     coarse_inverse_kernel<<<nc, 128, 0, st>>>(nc, P->dense, P->piv, P->minv, P->work);
+    const unsigned pcb = (unsigned)std::min<int64_t>(blocks(A->nnzb), 152 * 32);
+    count_launches(1);
+    if (mixed)
+        pressure_columns_kernel<float, float><<<pcb, 256, 0, st>>>(A->nnzb, A->d_v32, (float *)P->apc);
+    else
+        pressure_columns_kernel<double, double><<<pcb, 256, 0, st>>>(A->nnzb, A->d_v, (double *)P->apc);
+    for (int l = 0; l + 1 < nl; ++l) {  // the smoothed levels' colour-split coefficients
+        G3 g{P->dims[l][0], P->dims[l][1], P->dims[l][2]};
+        count_launches(1);
+        if (mixed)
+            split_stencil_kernel<float><<<blocks(g.n()), 256, 0, st>>>(g, P->a7[l], (float *)P->a7s[l]);
+        else
+            split_stencil_kernel<double><<<blocks(g.n()), 256, 0, st>>>(g, P->a7[l], (double *)P->a7s[l]);
+    }
     if (mixed) {
         count_launches(1 + nl);
         cast_stencil<<<blocks(3 * nb), 256, 0, st>>>(3 * nb, P->w64, (float *)P->w);
@@ -446,6 +533,7 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
 template <typename T>
 static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done) {
     const T *a7 = P.mixed ? (const T *)P.a7f[l] : (const T *)P.a7[l];
+    const T *a7s = (const T *)P.a7s[l];  // colour-split copy for the smoother
     T *x = (T *)P.x[l], *b = (T *)P.b[l];
     G3 g{P.dims[l][0], P.dims[l][1], P.dims[l][2]};
     const int64_t n = g.n();
@@ -454,22 +542,33 @@ static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done)
         coarse_apply_kernel<T><<<blocks(n * 32), 256, 0, st>>>((int)n, P.minv, b, x, done);
         return cudaGetLastError();
     }
-    count_launches(1 + 2 * P.sweeps);
-    zero_kernel<T><<<blocks(n), 256, 0, st>>>(n, x, done);
-    for (int s = 0; s < P.sweeps; ++s) {
-        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 0, done);
-        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 1, done);
-    }
     G3 c{P.dims[l + 1][0], P.dims[l + 1][1], P.dims[l + 1][2]};
+    const T *xc = (const T *)P.x[l + 1];
+    const unsigned hb = blocks((int64_t)((g.nx + 1) / 2) * g.ny * g.nz);  // one thread per cell of a colour
+    // pre-smoothing from x = 0: red, black, `sweeps` times (the first red half sweep reads no neighbour)
+    count_launches(P.sweeps > 0 ? 2 * P.sweeps : 1);
+    if (P.sweeps == 0) zero_kernel<T><<<blocks(n), 256, 0, st>>>(n, x, done);
+    for (int s = 0; s < P.sweeps; ++s) {
+        if (s == 0)
+            rbgs_kernel<T, 1><<<hb, 256, 0, st>>>(g, a7s, b, x, 0, xc, c, done);
+        else
+            rbgs_kernel<T, 0><<<hb, 256, 0, st>>>(g, a7s, b, x, 0, xc, c, done);
+        rbgs_kernel<T, 0><<<hb, 256, 0, st>>>(g, a7s, b, x, 1, xc, c, done);
+    }
     count_launches(1);
     residual_restrict_kernel<T><<<blocks(c.n()), 256, 0, st>>>(g, a7, b, x, c, (T *)P.b[l + 1], done);
     cudaError_t e = vcycle<T>(P, l + 1, st, done);
     if (e != cudaSuccess) return e;
-    count_launches(1 + 2 * P.sweeps);
-    prolong_add_kernel<T><<<blocks(n), 256, 0, st>>>(g, (const T *)P.x[l + 1], c, x, done);
+    // coarse correction x += P xc and post-smoothing black, red, `sweeps` times (the first black half
+    // sweep applies the correction to the red values it reads)
+    count_launches(P.sweeps > 0 ? 2 * P.sweeps : 1);
+    if (P.sweeps == 0) prolong_add_kernel<T><<<blocks(n), 256, 0, st>>>(g, xc, c, x, done);
     for (int s = 0; s < P.sweeps; ++s) {
-        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 1, done);
-        rbgs_kernel<T><<<blocks(n), 256, 0, st>>>(g, a7, b, x, 0, done);
+        if (s == 0)
+            rbgs_kernel<T, 2><<<hb, 256, 0, st>>>(g, a7s, b, x, 1, xc, c, done);
+        else
+            rbgs_kernel<T, 0><<<hb, 256, 0, st>>>(g, a7s, b, x, 1, xc, c, done);
+        rbgs_kernel<T, 0><<<hb, 256, 0, st>>>(g, a7s, b, x, 0, xc, c, done);
     }
     return cudaGetLastError();
 }
@@ -488,22 +587,22 @@ cudaError_t cpr_pressure_vcycle(const rsv_mat *A, const Cpr &P, const int *gate)
     return vcycle<T>(P, 0, A->stream, gate);
 }
 
-// Stage one's prolongation x = Pi_p P.x[0], then stage two: x += ILU0^{-1}(f - A x).
+// Stage one's prolongation x = Pi_p P.x[0], then stage two: x += ILU0^{-1}(f - A x).  Fused:
+// r = f - A Pi_p p from the pressure columns alone, x = ILU0^{-1} r, then x += Pi_p p (the same
+// sums, in the same order, as forming x = Pi_p p, r = f - A x and x += ILU0^{-1} r).
 template <typename T>
 cudaError_t cpr_finish(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
                        int *status, unsigned long long timeout_ns) {
     cudaStream_t st = A->stream;
     const int64_t nb = A->nb;
-    T *r = (T *)P.r, *z = (T *)P.z;
-    count_launches(1);
-    prolong_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, (const T *)P.x[0], f, x, r, done);
-    cudaError_t e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
-                                     : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
+    T *r = (T *)P.r;
+    const T *p = (const T *)P.x[0];
+    cudaError_t e = launch_pressure_residual<T>(A, (const T *)P.apc, p, f, r, done, status, timeout_ns);
     if (e != cudaSuccess) return e;
-    e = launch_ilu_apply_tiles<T>(A, tiles, r, z, done, status, timeout_ns);
+    e = launch_ilu_apply_tiles<T>(A, tiles, r, x, done, status, timeout_ns);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    add_kernel<T><<<blocks(3 * nb), 256, 0, st>>>(3 * nb, z, x, done);
+    prolong_add_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, p, x, done);
     return cudaGetLastError();
 }
 
@@ -532,8 +631,9 @@ cudaError_t cpr_apply_order(const rsv_mat *A, const Cpr &P, const IluTiles &tile
         if (q > 0) {
             e = cudaMemcpyAsync(r, f, sizeof(T) * 3 * nb, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess)
-                e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done)
-                                     : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done);
+                e = (sizeof(T) == 8) ? launch_spmv_f64(A, -1.0, (const double *)x, 1.0, (double *)r, done, status, timeout_ns)
+                                     : launch_spmv_f32(A, -1.0f, (const float *)x, 1.0f, (float *)r, done, status,
+                                                       timeout_ns);
             src = r;
         }
         if (e != cudaSuccess) break;

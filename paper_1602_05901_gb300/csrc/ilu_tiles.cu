@@ -76,7 +76,7 @@ template <> struct Bits<float> {
     using U = unsigned int;
     static constexpr U SENT = 0x7FA5C0DEu;
     static constexpr int NQP = 36;
-    static constexpr int NG = 3;
+    static constexpr int NG = 2;
 };
 
 // Data stage of one step: factor [32][NQP] and vector [32][4]; a data group holds

@@ -8,11 +8,13 @@
 // Kernels of a step that follows convergence see the device `done` flag and
 // return at once.
 //
-// Arnoldi orthogonalisation is classical Gram-Schmidt ("all projections, then
-// one multi-vector update"), repeated once when the first pass cancelled more
-// than 1 - 1/sqrt(2) of the vector's norm (Kahan's "twice is enough" test);
-// the Hessenberg columns, Givens rotations and the residual estimate are FP64
-// scalars kept in device memory.
+// Arnoldi orthogonalisation is classical Gram-Schmidt with one reorthogonalisation
+// ("all projections, then one multi-vector update", twice).  FP64 bases take the
+// second pass's projections from the Gram matrix of the basis (see
+// gmres_gram_step), so a step reads the basis twice; FP32 bases run the second
+// pass explicitly when the first one cancelled more than 1 - 1/sqrt(2) of the
+// norm.  The Hessenberg columns, Givens rotations and the residual estimate are
+// FP64 scalars kept in device memory.
 //
 // Mixed precision (precision = RSV_PREC_MIXED): an FP64 iterative-refinement
 // loop r = b - A x (FP64 SpMV, FP64 norm), inner solve A d = r / ||r|| with
@@ -88,14 +90,41 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
     for (int i = t; i < j; i += blockDim.x) H[i * m + j] = col[i];
 }
 
-// After the first Gram-Schmidt pass: keep its result when ||w'|| >= ||w|| / sqrt(2),
-// otherwise run the second pass (its coefficients add to the first pass's).
+// Classical Gram-Schmidt with its second pass taken from the Gram matrix G = V^T V
+// of the basis.  With h1 = V^T w, the second pass's projections of w' = w - V h1
+// are V^T w' = h1 - G h1, so the two passes together subtract V h with
+// h = h1 + (h1 - G h1); G's new column <v_j, V> comes from the same read of the
+// basis as h1.  Column j of G (i <= j) is stored, G kept symmetric, h written to
+// h1 and h2 cleared (the Hessenberg column is h1 + h2).  One block of kMaxRestart
+// + 1 threads.  Used for FP64 bases.
+// After the first Gram-Schmidt pass of an FP32 basis: keep its result when
+// ||w'|| >= ||w|| / sqrt(2), otherwise run the second pass (its coefficients add
+// to the first pass's).
 __global__ void gmres_reorth_check(DevState *ds, int k) {
     if (ds->done) return;
     const bool keep = ds->hn >= 0.70710678118654752 * ds->wnorm;
     if (threadIdx.x == 0) ds->skip2 = keep ? 1 : 0;
     if (keep)
         for (int i = threadIdx.x; i < k; i += blockDim.x) ds->h2[i] = 0.0;
+}
+
+__global__ void gmres_gram_step(DevState *ds, int j) {
+    if (ds->done) return;
+    constexpr int L = kMaxRestart + 1;
+    __shared__ double h1[L];
+    const int t = threadIdx.x;
+    if (t <= j) {
+        ds->G[t * L + j] = ds->gcol[t];
+        ds->G[j * L + t] = ds->gcol[t];
+        h1[t] = ds->h1[t];
+    }
+    __syncthreads();
+    if (t <= j) {
+        double gh = 0.0;
+        for (int l = 0; l <= j; ++l) gh += ds->G[t * L + l] * h1[l];
+        ds->h1[t] = h1[t] + (h1[t] - gh);
+        ds->h2[t] = 0.0;
+    }
 }
 
 __global__ void gmres_backsolve(DevState *ds, int m) {
@@ -285,26 +314,41 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
             T *z = flex ? Z + (size_t)j * ldv : t;
             RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
-            // classical Gram-Schmidt; a second pass only when the first one cancelled
-            // more than 1 - 1/sqrt(2) of the norm ("twice is enough")
-            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0], &ds->done,
-                                        &ds->wnorm));
-            if (j + 1 <= kFuseMax<T>) {
-                // the first pass's update also forms the second pass's projections
-                RSV_CUDA_TRY(launch_maxpy_mdot<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, s->partial, ds->h2, &ds->hn,
-                                                  &ds->counter[1], &ds->done));
+            if (sizeof(T) == 8) {
+                // FP64: projections onto V and the Gram matrix's new column in one read of the
+                // basis, the second pass's projections from the Gram matrix, then one update
+                // w -= V h that also forms ||w||.  The update's own rounding (~1e-16) is far
+                // below what the second pass removes, so this is CGS2 with two reads of V.
+                RSV_CUDA_TRY(launch_mdot2<T>(s->st, n, wj, vj, V, ldv, j + 1, s->partial, ds->h1, ds->gcol,
+                                             &ds->counter[0], &ds->done));
                 rsv::count_launches(1);
-                gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
-            } else {
+                gmres_gram_step<<<1, kMaxRestart + 1, 0, s->st>>>(ds, j);
                 RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, &ds->hn,
                                              &ds->counter[1], &ds->done));
-                rsv::count_launches(1);
-                gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
-                RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0],
-                                            &ds->done, nullptr, &ds->skip2));
+            } else {
+                // FP32: the second pass recomputes the projections of the updated vector, which
+                // also removes the first update's FP32 rounding (the Gram-matrix form leaves it,
+                // and the inner solves then take about 10% more iterations); it runs when the
+                // first pass cancelled more than 1 - 1/sqrt(2) of the norm ("twice is enough")
+                RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h1, &ds->counter[0],
+                                            &ds->done, &ds->wnorm));
+                if (j + 1 <= kFuseMax<T>) {
+                    // the first pass's update also forms the second pass's projections
+                    RSV_CUDA_TRY(launch_maxpy_mdot<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, s->partial, ds->h2,
+                                                      &ds->hn, &ds->counter[1], &ds->done));
+                    rsv::count_launches(1);
+                    gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
+                } else {
+                    RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h1, -1.0, wj, s->partial, &ds->hn,
+                                                 &ds->counter[1], &ds->done));
+                    rsv::count_launches(1);
+                    gmres_reorth_check<<<1, 32, 0, s->st>>>(ds, j + 1);
+                    RSV_CUDA_TRY(launch_mdot<T>(s->st, n, wj, V, ldv, j + 1, s->partial, ds->h2, &ds->counter[0],
+                                                &ds->done, nullptr, &ds->skip2));
+                }
+                RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
+                                             &ds->counter[1], &ds->done, &ds->skip2));
             }
-            RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, wj, V, ldv, j + 1, ds->h2, -1.0, wj, s->partial, &ds->hn,
-                                         &ds->counter[1], &ds->done, &ds->skip2));
             rsv::count_launches(1);
             gmres_givens<<<1, kMaxRestart, 0, s->st>>>(ds, j, m);
             if (s->pc_type == RSV_PC_CPR_LEARNED) RSV_CUDA_TRY(learned_watch(s, j));
@@ -346,8 +390,11 @@ rsv_status bicgstab_run(rsv_solver *s, const T *b, T *x, double tol) {
     rsv::count_launches(1);
     bicg_init<<<1, 1, 0, s->st>>>(ds);
     double rn0 = 0.0;
+    int status0 = 0;
     RSV_CUDA_TRY(cudaMemcpyAsync(&rn0, &ds->red[9], sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    RSV_CUDA_TRY(cudaMemcpyAsync(&status0, &ds->status, sizeof(int), cudaMemcpyDeviceToHost, s->st));
     RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+    if (status0 != RSV_OK) return (rsv_status)status0;  // a device-side failure (e.g. a timed-out wait) first
     if (!std::isfinite(rn0)) return RSV_ENAN;
     if (rn0 <= tol) return RSV_OK;
     const int g = egrid(n);
@@ -449,7 +496,7 @@ void solver_free(rsv_solver *s) {
     cudaStreamSynchronize(s->st);
     for (void *p : {(void *)s->ds, (void *)s->partial, s->kw.V, s->kw.Z, s->kw.w, s->kw.t, (void *)s->r64,
                     (void *)s->d_b, (void *)s->d_x, (void *)s->rf, (void *)s->df, (void *)s->dinv,
-                    (void *)s->dinv32})
+                    (void *)s->dinv32, (void *)s->acc})
         if (p) cudaFree(p);
     free_schedule(&s->sch);
     free_tiles(&s->tiles);
@@ -497,7 +544,7 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
         if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
     };
     alloc((void **)&s->ds, sizeof(DevState));
-    alloc((void **)&s->partial, sizeof(double) * (kMaxRestart + 1) * kRedBlocks);
+    alloc((void **)&s->partial, sizeof(double) * 2 * (kMaxRestart + 16) * kRedBlocks);
     if (p->solver == RSV_BICGSTAB) {
         alloc(&s->kw.V, 8 * n * es);
     } else {
@@ -537,8 +584,9 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     if (params) pcp = *params;
     if (pcp.gmg_max_levels < 1 || pcp.gmg_max_levels > kMaxLevels || pcp.gmg_max_coarse < 1 ||
         pcp.gmg_max_coarse > 1024 || pcp.gmg_sweeps < 0 || pcp.gmg_sweeps > 16 || pcp.decoupling < 0 ||
-        pcp.decoupling > 1)
+        pcp.decoupling > 2)
         return RSV_EINVAL;
+    if (cpr && pcp.decoupling == 2 && !s->acc) return RSV_EINVAL;  // true-IMPES needs the accumulation blocks
     rsv_mat *A = s->A;
     s->pc_type = -1;
     RSV_CUDA_TRY(cudaEventRecord(s->e0, s->st));
@@ -561,7 +609,7 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     if (cpr && A->nsys > 1) return RSV_ENOTSUP;
     if (cpr)
         RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, pcp.decoupling,
-                               &s->cpr, &s->ds->status));
+                               s->acc, &s->cpr, &s->ds->status));
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
     RSV_TRY(read_status(s, &status));
@@ -578,6 +626,24 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
 static rsv_status pc_check(rsv_solver *s, const void *r, const void *z) {
     if (!s || !r || !z || r == z) return RSV_EINVAL;
     if (s->pc_type < 0 || s->pc_version != s->A->version) return RSV_EINVAL;
+    return RSV_OK;
+}
+
+rsv_status rsv_precond_set_accumulation(rsv_solver *s, const double *acc, int on_device) {
+    if (!s) return RSV_EINVAL;
+    if (!acc) {
+        if (s->acc) {
+            RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
+            cudaFree(s->acc);
+            s->acc = nullptr;
+        }
+        return RSV_OK;
+    }
+    const size_t bytes = sizeof(double) * 9 * (size_t)std::max<int64_t>(s->A->nb, 1);
+    if (!s->acc) RSV_CUDA_TRY(cudaMalloc((void **)&s->acc, bytes));
+    RSV_CUDA_TRY(cudaMemcpyAsync(s->acc, acc, sizeof(double) * 9 * (size_t)s->A->nb,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
     return RSV_OK;
 }
 

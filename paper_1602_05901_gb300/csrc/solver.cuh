@@ -46,6 +46,7 @@ struct rsv_solver {
     double *rec_buf = nullptr;
     int rec_max = 0;
     int *rec_count = nullptr;
+    double *acc = nullptr;       // accumulation blocks [nb][9] for true-IMPES decoupling, device
     double ms_setup = 0.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -64,11 +65,11 @@ template <typename T>
 cudaError_t spmv(rsv_solver *s, T alpha, const T *x, T beta, T *y, const int *done);
 template <>
 inline cudaError_t spmv<double>(rsv_solver *s, double alpha, const double *x, double beta, double *y, const int *done) {
-    return launch_spmv_f64(s->A, alpha, x, beta, y, done);
+    return launch_spmv_f64(s->A, alpha, x, beta, y, done, &s->ds->status, (unsigned long long)s->p.watchdog * 1000ull);
 }
 template <>
 inline cudaError_t spmv<float>(rsv_solver *s, float alpha, const float *x, float beta, float *y, const int *done) {
-    return launch_spmv_f32(s->A, alpha, x, beta, y, done);
+    return launch_spmv_f32(s->A, alpha, x, beta, y, done, &s->ds->status, (unsigned long long)s->p.watchdog * 1000ull);
 }
 
 // z = M^{-1} r on the solver stream in precision T; `done` gates the kernels.

@@ -31,7 +31,7 @@ template <typename T, int R>
 __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__restrict__ rp,
                                                        const int32_t *__restrict__ ci, const T *__restrict__ v,
                                                        T alpha, const T *__restrict__ x, T beta, T *__restrict__ y,
-                                                       const int *done) {
+                                                       const int *done, int *status, unsigned long long timeout_ns) {
     if (done && *(volatile const int *)done) return;
     using L = SpmvSmem<T, R>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
     __syncthreads();
     {
         unsigned ok = 0, spins = 0;
-        uint64_t deadline = 0;
+        const uint64_t deadline = global_timer() + timeout_ns;
+        bool late = false;
         for (;;) {
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
@@ -76,11 +77,29 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
                 : "memory");
             if (ok) break;
             // the copy is plain memory traffic; the limit only guards against a stuck wait
-            if ((++spins & 1023u) == 0) {
-                const uint64_t now = global_timer();
-                if (deadline == 0) deadline = now + 2000000000ull;
-                else if (now > deadline) return;
+            if ((++spins & 7u) == 0 && global_timer() > deadline) {
+                late = true;
+                break;
             }
+        }
+        if (__syncthreads_or(late)) {
+            // The staged copies did not arrive in time: record it and write NaN to this CTA's rows, so
+            // the output cannot pass for a result; thread 0 then waits (bounded) for the copies still in
+            // flight before the CTA releases its shared memory.
+            if (threadIdx.x == 0 && status) atomicCAS(status, 0, (int)RSV_ETIMEOUT);
+            if (threadIdx.x < 3 * nr) y[3 * (int64_t)r0 + threadIdx.x] = T(__int_as_float(0x7fc00000));
+            if (threadIdx.x == 0) {
+                const uint64_t drain = global_timer() + 10000000ull;
+                do {
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, "
+                        "0, p;\n}"
+                        : "=r"(ok)
+                        : "r"(smem_u32(bar))
+                        : "memory");
+                } while (!ok && global_timer() < drain);
+            }
+            return;
         }
     }
     const int voff = (int)((vb0 - va0) / sizeof(T));
@@ -100,6 +119,94 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
     y[row] = (beta == T(0)) ? alpha * acc : alpha * acc + beta * y[row];
 }
 
+// r = f - A (p_c, 0, 0)_c from the pressure columns apc[3 q + e] = A_q[e][0]: the BSR SpMV
+// above with one column per block and x = p (CPR-PF's stage-two residual).  Same staging; the
+// sum over a row's blocks, and r = -1 * sum + f, round as the full SpMV of (p_c, 0, 0) does.
+template <typename T, int R>
+__global__ void __launch_bounds__(3 * R) pcol_residual_tma(int nb, const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci, const T *__restrict__ apc,
+                                                           const T *__restrict__ p, const T *__restrict__ f,
+                                                           T *__restrict__ r, const int *done, int *status,
+                                                           unsigned long long timeout_ns) {
+    if (done && *(volatile const int *)done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int VALS = R * 7 * 3 + 32 / sizeof(T);
+    constexpr int CI = R * 7 + 8;
+    T *sv = reinterpret_cast<T *>(smem);
+    int32_t *sci = reinterpret_cast<int32_t *>(smem + (size_t)VALS * sizeof(T));
+    int32_t *srp = sci + CI;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(srp + R + 4);
+    const int r0 = blockIdx.x * R;
+    const int nr = min(R, nb - r0);
+    const int p0 = rp[r0], p1 = rp[r0 + nr];
+    const uintptr_t vb0 = (uintptr_t)(apc + (int64_t)p0 * 3), vb1 = (uintptr_t)(apc + (int64_t)p1 * 3);
+    const uintptr_t va0 = vb0 & ~(uintptr_t)15, va1 = (vb1 + 15) & ~(uintptr_t)15;
+    const uintptr_t cb0 = (uintptr_t)(ci + p0), cb1 = (uintptr_t)(ci + p1);
+    const uintptr_t ca0 = cb0 & ~(uintptr_t)15, ca1 = (cb1 + 15) & ~(uintptr_t)15;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned bytes = (unsigned)((va1 - va0) + (ca1 - ca0));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sv)),
+            "l"(va0), "r"((unsigned)(va1 - va0)), "r"(smem_u32(bar))
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sci)),
+            "l"(ca0), "r"((unsigned)(ca1 - ca0)), "r"(smem_u32(bar))
+            : "memory");
+    }
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t] - p0;
+    const int t = threadIdx.x;
+    const int64_t row = 3 * (int64_t)r0 + t;
+    const T fr = t < nr * 3 ? f[row] : T(0);  // issued before the wait
+    __syncthreads();
+    {
+        unsigned ok = 0, spins = 0;
+        const uint64_t deadline = global_timer() + timeout_ns;
+        bool late = false;
+        for (;;) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(smem_u32(bar))
+                : "memory");
+            if (ok) break;
+            if ((++spins & 7u) == 0 && global_timer() > deadline) {
+                late = true;
+                break;
+            }
+        }
+        if (__syncthreads_or(late)) {
+            if (t == 0 && status) atomicCAS(status, 0, (int)RSV_ETIMEOUT);
+            if (t < 3 * nr) r[row] = T(__int_as_float(0x7fc00000));
+            if (t == 0) {
+                const uint64_t drain = global_timer() + 10000000ull;
+                do {
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, "
+                        "0, p;\n}"
+                        : "=r"(ok)
+                        : "r"(smem_u32(bar))
+                        : "memory");
+                } while (!ok && global_timer() < drain);
+            }
+            return;
+        }
+    }
+    if (t >= nr * 3) return;
+    const int voff = (int)((vb0 - va0) / sizeof(T));
+    const int coff = (int)((cb0 - ca0) / 4);
+    const int rl = t / 3, e = t - 3 * (t / 3);
+    T acc = T(0);
+    for (int q = srp[rl]; q < srp[rl + 1]; ++q) acc = fma(sv[voff + 3 * q + e], p[sci[coff + q]], acc);
+    r[row] = T(-1) * acc + fr;
+}
+
 __global__ void cast_f64_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
@@ -114,24 +221,46 @@ cudaError_t spmv_attr() {
 }
 
 template <typename T, int R>
-cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done) {
+cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done,
+                        int *status, unsigned long long timeout_ns) {
     const int grid = (int)((A->nb + R - 1) / R);
     rsv::count_launches(1);
     spmv_bsr3_tma<T, R><<<grid, 3 * R, SpmvSmem<T, R>::BYTES, A->stream>>>((int)A->nb, A->d_rp, A->d_ci, v, alpha,
-                                                                           x, beta, y, done);
+                                                                           x, beta, y, done, status, timeout_ns);
     return cudaGetLastError();
 }
 
 // Block rows per CTA: 128 by default; batches pick 32, 64 or 128 by timing.
 template <typename T>
-cudaError_t spmv_dispatch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done) {
+cudaError_t spmv_dispatch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done,
+                          int *status, unsigned long long timeout_ns) {
     if (A->nb == 0) return cudaSuccess;
     switch (A->spmv_rows) {
-    case 32: return spmv_launch<T, 32>(A, v, alpha, x, beta, y, done);
-    case 64: return spmv_launch<T, 64>(A, v, alpha, x, beta, y, done);
-    default: return spmv_launch<T, kRows>(A, v, alpha, x, beta, y, done);
+    case 32: return spmv_launch<T, 32>(A, v, alpha, x, beta, y, done, status, timeout_ns);
+    case 64: return spmv_launch<T, 64>(A, v, alpha, x, beta, y, done, status, timeout_ns);
+    default: return spmv_launch<T, kRows>(A, v, alpha, x, beta, y, done, status, timeout_ns);
     }
 }
+
+template <typename T, int R> constexpr size_t pcol_smem() {
+    return (size_t)(R * 7 * 3 + 32 / sizeof(T)) * sizeof(T) + (R * 7 + 8) * 4 + (R + 4) * 4 + 16;
+}
+
+template <typename T>
+cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p, const T *f, T *r, const int *done,
+                                     int *status, unsigned long long timeout_ns) {
+    if (A->nb == 0) return cudaSuccess;
+    constexpr int R = 128;
+    const int grid = (int)((A->nb + R - 1) / R);
+    rsv::count_launches(1);
+    pcol_residual_tma<T, R><<<grid, 3 * R, pcol_smem<T, R>(), A->stream>>>((int)A->nb, A->d_rp, A->d_ci, apc, p, f, r,
+                                                                          done, status, timeout_ns);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pressure_residual<double>(const rsv_mat *, const double *, const double *, const double *,
+                                                      double *, const int *, int *, unsigned long long);
+template cudaError_t launch_pressure_residual<float>(const rsv_mat *, const float *, const float *, const float *,
+                                                     float *, const int *, int *, unsigned long long);
 
 cudaError_t spmv_init() {
     cudaError_t e;
@@ -139,17 +268,24 @@ cudaError_t spmv_init() {
         (e = spmv_attr<double, kRows>()) != cudaSuccess || (e = spmv_attr<float, 32>()) != cudaSuccess ||
         (e = spmv_attr<float, 64>()) != cudaSuccess || (e = spmv_attr<float, kRows>()) != cudaSuccess)
         return e;
+    if ((e = cudaFuncSetAttribute((const void *)pcol_residual_tma<double, 128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcol_smem<double, 128>())) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute((const void *)pcol_residual_tma<float, 128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcol_smem<float, 128>())) !=
+            cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
 cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, double beta, double *y,
-                            const int *done) {
-    return spmv_dispatch<double>(A, A->d_v, alpha, x, beta, y, done);
+                            const int *done, int *status, unsigned long long timeout_ns) {
+    return spmv_dispatch<double>(A, A->d_v, alpha, x, beta, y, done, status, timeout_ns);
 }
 
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
-                            const int *done) {
-    return spmv_dispatch<float>(A, A->d_v32, alpha, x, beta, y, done);
+                            const int *done, int *status, unsigned long long timeout_ns) {
+    return spmv_dispatch<float>(A, A->d_v32, alpha, x, beta, y, done, status, timeout_ns);
 }
 
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b) {

@@ -7,6 +7,6 @@ nor the CPU oracle; both of those consume what it generates.
 """
 from .reservoir import (  # noqa: F401
     Problem, make_problem, perm_lognormal, perm_layered, perm_channelized,
-    assemble_jacobian, seven_point_pattern, nnzb_of, uniform01, std_normal,
+    assemble_jacobian, accumulation_blocks, seven_point_pattern, nnzb_of, uniform01, std_normal,
     WORKLOADS, workload, batch_sizes, unet_init,
 )

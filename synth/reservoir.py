@@ -40,7 +40,7 @@ import numpy as np
 
 __all__ = [
     "Problem", "make_problem", "perm_lognormal", "perm_layered", "perm_channelized",
-    "assemble_jacobian", "seven_point_pattern", "nnzb_of", "uniform01", "std_normal",
+    "assemble_jacobian", "accumulation_blocks", "seven_point_pattern", "nnzb_of", "uniform01", "std_normal",
     "WORKLOADS", "workload", "batch_sizes",
 ]
 
@@ -148,6 +148,15 @@ def perm_channelized(nx, ny, nz, seed, sigma=2.0, nchannels=5, width=8, height=4
 
 # ---------------------------------------------------------------------- Jacobian
 
+def accumulation_blocks(nb, seed, pv_over_dt=PV_OVER_DT):
+    """The accumulation (time-derivative) part of every cell's diagonal block,
+    diag(a_c) * PV/dt with a_c[e] ~ uniform(1, 5): float64 [nb, 3, 3]."""
+    a = 1.0 + 4.0 * uniform01(seed, S_ACC, np.arange(3 * nb)).reshape(nb, 3)
+    acc = np.zeros((nb, 3, 3), dtype=np.float64)
+    acc[:, [0, 1, 2], [0, 1, 2]] = a * pv_over_dt
+    return acc
+
+
 def assemble_jacobian(nx, ny, nz, lnk, seed, pv_over_dt=PV_OVER_DT):
     """Assemble the 3x3-block Jacobian in BSR form (values float64 [nnzb, 3, 3], row-major blocks).
 
@@ -163,9 +172,7 @@ def assemble_jacobian(nx, ny, nz, lnk, seed, pv_over_dt=PV_OVER_DT):
     i = c % nx
     j = (c // nx) % ny
     k = c // (nx * ny)
-    a = 1.0 + 4.0 * uniform01(seed, S_ACC, np.arange(3 * nb)).reshape(nb, 3)
-    diag = np.zeros((nb, 3, 3), dtype=np.float64)
-    diag[:, [0, 1, 2], [0, 1, 2]] = a * pv_over_dt
+    diag = accumulation_blocks(nb, seed, pv_over_dt)
     dirs = [(-nx * ny, k > 0), (-nx, j > 0), (-1, i > 0), (1, i < nx - 1), (nx, j < ny - 1),
             (nx * ny, k < nz - 1)]
     # position of each neighbour in the row: columns are ascending, so count present
@@ -205,6 +212,12 @@ class Problem:
     vals: np.ndarray      # float64 [nnzb, 3, 3]
     b: np.ndarray         # float64 [3*nb]
     lnk: np.ndarray       # float64 [nb]
+    seed: int = 0
+    pv_over_dt: float = PV_OVER_DT
+
+    def accumulation(self):
+        """Accumulation blocks [nb, 3, 3] of the assembled Jacobian (the input of true-IMPES)."""
+        return accumulation_blocks(self.nb, self.seed, self.pv_over_dt)
 
     @property
     def nb(self):
@@ -255,7 +268,7 @@ def make_problem(nx, ny, nz, seed, perm="lognormal", sigma=1.0, wells="corner",
         raise ValueError(f"unknown permeability recipe {perm!r}")
     row_ptr, col_idx, vals = assemble_jacobian(nx, ny, nz, lnk, seed, pv_over_dt)
     w = corner_wells(nx, ny, nz) if wells == "corner" else seeded_wells(nx, ny, nz, seed)
-    return Problem(nx, ny, nz, row_ptr, col_idx, vals, _rhs(nx * ny * nz, seed, w), lnk)
+    return Problem(nx, ny, nz, row_ptr, col_idx, vals, _rhs(nx * ny * nz, seed, w), lnk, seed, pv_over_dt)
 
 
 # Named workloads (grid, permeability recipe, seed, wells).

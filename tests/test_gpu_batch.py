@@ -122,3 +122,36 @@ def test_batch_64_uneven_systems_mixed(rsv):
         rel = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, xs)) / np.linalg.norm(p.b)
         assert rel <= 1e-8
         off += p.nb
+
+
+def test_batch_64_uneven_systems_full_size(rsv):
+    """The 64-system ensemble at its full sizes (grids from 16^3 to 96x96x48, 6.17M cells,
+    18.5M unknowns): BiCGSTAB + block ILU(0), FP32 inner solves under FP64 refinement, one
+    batched call; every system's true residual, recomputed by the oracle's SpMV of that
+    system alone, meets rtol 1e-8, and no system runs away toward maxit (every count stays
+    below 1,000)."""
+    import torch
+    dims = synth.batch_sizes()
+    probs = _batch_problems(dims)
+    vals, b = _concat(probs)
+    A = rsv.Matrix.batch(dims)
+    assert A.nb == sum(p.nb for p in probs) == 6171613
+    A.set_values(torch.from_numpy(vals).cuda())
+    del vals
+    s = rsv.Solver(A, solver="bicgstab", precision="mixed", rtol=1e-8, maxit=4000)
+    s.setup("bilu0")
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    st, infos = s.solve_batched(torch.from_numpy(b).cuda(), x)
+    assert st == 0, [i for i in infos if i["status"]]
+    xh = x.cpu().numpy()
+    off = 0
+    its = []
+    for p, info in zip(probs, infos):
+        xs = xh[3 * off:3 * (off + p.nb)]
+        rel = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, xs)) / np.linalg.norm(p.b)
+        assert rel <= 1e-8 and abs(rel - info["true_relres"]) <= 1e-12 * max(1.0, rel / 1e-8), (rel, info)
+        assert info["status"] == 0 and info["outer_iters"] >= 1
+        its.append(info["iters"])
+        off += p.nb
+    assert max(its) < 1000, its
+    print(f"BATCH64_FULL iters min/median/max {min(its)}/{int(np.median(its))}/{max(its)}")

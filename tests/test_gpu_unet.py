@@ -90,7 +90,9 @@ def test_unet_forward_matches_oracle(rsv, case):
     # which can flip a BF16 rounding (2^-8 relative) of an activation here and there.
     assert rel < 5e-3, rel
     from tests.helpers import per_entry_ratio, report_ratio
-    ratio = report_ratio(f"unet_forward_{case}", per_entry_ratio(got, ref, floor=1e-2), 0.1)
+    # per entry, against the RMS entry: flipped BF16 roundings spread errors of ~1% of the RMS
+    # everywhere; a wrong value in a few voxels stands far above that
+    ratio = report_ratio(f"unet_forward_{case}", per_entry_ratio(got, ref, floor=1.0), 0.1)
     assert ratio <= 0.1
     assert np.linalg.norm(ref - ref64) / np.linalg.norm(ref64) < 0.1
     rsv.rsv_unet_destroy(h)

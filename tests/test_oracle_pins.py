@@ -345,6 +345,52 @@ def test_abf_pressure_stage_exact_on_component_decoupled_system():
     assert np.allclose(x[0::3], np.linalg.solve(A[0::3, 0::3], f[0::3]), rtol=1e-10)
 
 
+@pytest.mark.parametrize("dims", [(4, 3, 2), (7, 5, 3)])
+def test_true_impes_weights_remove_secondary_unknowns_from_accumulation(dims):
+    """True-IMPES takes the weights from each cell's accumulation block C_c:
+    w_c = first row of C_c^{-1} (numpy's inverse), so w_c C_c = (1, 0, 0), and A_pp
+    is the weighted product W A P.  With C_c = D_c (the diagonal block of A) it is
+    ABF exactly; with the generator's diagonal accumulation blocks the weights are
+    (1/C_00, 0, 0) and A_pp is the pressure-pressure block scaled per row."""
+    p = _prob(dims, seed=24)
+    nx, ny, nz = dims
+    rng = np.random.default_rng(25)
+    C = rng.standard_normal((p.nb, 3, 3)) + 3 * np.eye(3)
+    st, w, a7 = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "timpes", acc=C)
+    assert st == 0
+    for c in range(p.nb):
+        assert np.allclose(w[c], np.linalg.inv(C[c])[0], rtol=1e-12, atol=1e-14 * np.abs(w[c]).max())
+        assert np.allclose(w[c] @ C[c], [1.0, 0.0, 0.0], atol=1e-12)
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    W = np.zeros((p.nb, p.n))
+    for c in range(p.nb):
+        W[c, 3 * c:3 * c + 3] = w[c]
+    assert np.allclose(stencil_to_dense(nx, ny, nz, a7), W @ A[:, 0::3], rtol=1e-12, atol=1e-12)
+    # C = D: the ABF weights
+    D = np.stack([p.vals[next(q for q in range(p.row_ptr[c], p.row_ptr[c + 1]) if p.col_idx[q] == c)]
+                  for c in range(p.nb)])
+    _, w_d, a7_d = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "timpes", acc=D)
+    _, w_abf, a7_abf = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "abf")
+    assert np.array_equal(w_d, w_abf) and np.array_equal(a7_d, a7_abf)
+    # the generator's accumulation blocks are diagonal
+    acc = p.accumulation()
+    _, w_g, a7_g = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "timpes", acc=acc)
+    assert np.allclose(w_g[:, 0], 1.0 / acc[:, 0, 0], rtol=1e-15) and np.all(w_g[:, 1:] == 0.0)
+    assert np.allclose(stencil_to_dense(nx, ny, nz, a7_g), A[0::3, 0::3] / acc[:, 0, 0][:, None], rtol=1e-13)
+    # without accumulation blocks true-IMPES is refused
+    st, _, _ = oracle.decouple_setup(nx, ny, nz, p.row_ptr, p.col_idx, p.vals, "timpes")
+    assert st == oracle.EINVAL
+
+
+def test_true_impes_cpr_solves_to_the_dense_solution():
+    p = _prob((6, 5, 4), seed=26)
+    s = oracle.System.from_problem(p, pc="cpr", decoupling="timpes", acc=p.accumulation())
+    assert s.setup_status == 0
+    st, x, info = s.gmres(p.b, rtol=1e-10, maxit=500)
+    A = bsr_to_dense(p.row_ptr, p.col_idx, p.vals)
+    assert st == 0 and np.allclose(x, np.linalg.solve(A, p.b), rtol=1e-7, atol=1e-9)
+
+
 CPR_ORDERS = [("cpr", "PF"), ("cpr_fp", "FP"), ("cpr_fpf", "FPF"), ("cpr_ffpf", "FFPF")]
 
 
