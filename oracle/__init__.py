@@ -89,6 +89,10 @@ def lib():
             "or_bicgstab": (I, [P, P, P, D, D, I, P]),
             "or_refine": (I, [P, P, P, P, I, I, D, D, I, I, P]),
             "or_set_threads": (I, [I]),
+            "or_set_coarsening": (None, [P, I]),
+            "or_amg_hierarchy": (I, [I, I, I, P, I, I, P]),
+            "or_amg_vcycle": (I, [I, I, I, P, I, I, I, P, P, P]),
+            "or_amg_level": (I, [I, I, I, P, I, I, I, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -244,13 +248,54 @@ def gmg_vcycle(nx, ny, nz, a7, rhs, max_levels=6, max_coarse=512, sweeps=2):
     return st, e, nl.value
 
 
+COARSENING = {"gmg": 0, "amg": 1}
+
+
+def amg_hierarchy(nx, ny, nz, a7, max_levels=8, max_coarse=512):
+    """[(points, nonzeros)] per level of the algebraic (PMIS) hierarchy, finest first."""
+    a7 = _f64(a7)
+    sizes = np.zeros(32, dtype=np.int32)
+    nl = lib().or_amg_hierarchy(nx, ny, nz, _p(a7), max_levels, max_coarse, _p(sizes))
+    if nl < 0:
+        raise ValueError(f"AMG setup failed: status {-nl}")
+    return [(int(sizes[2 * l]), int(sizes[2 * l + 1])) for l in range(nl)]
+
+
+def amg_vcycle(nx, ny, nz, a7, rhs, max_levels=8, max_coarse=512, sweeps=2):
+    a7, rhs = _f64(a7), _f64(rhs)
+    e = np.zeros_like(rhs)
+    nl = ctypes.c_int(0)
+    st = lib().or_amg_vcycle(nx, ny, nz, _p(a7), max_levels, max_coarse, sweeps, _p(rhs), _p(e), ctypes.byref(nl))
+    return st, e, nl.value
+
+
+def amg_level(nx, ny, nz, a7, level, max_levels=8, max_coarse=512):
+    """Level `level` of the AMG hierarchy: (cf [n], P as dense-free CSR (rp, ci, v), A_coarse CSR (rp, ci, v))."""
+    levels = amg_hierarchy(nx, ny, nz, a7, max_levels, max_coarse)
+    n, _ = levels[level]
+    nc, nnzc = levels[level + 1]
+    a7 = _f64(a7)
+    cf = np.zeros(n, dtype=np.int32)
+    prp = np.zeros(n + 1, dtype=np.int32)
+    cap = 8 * n + 1
+    pci = np.zeros(cap, dtype=np.int32)
+    pv = np.zeros(cap)
+    arp = np.zeros(nc + 1, dtype=np.int32)
+    aci = np.zeros(nnzc, dtype=np.int32)
+    av = np.zeros(nnzc)
+    nnzp = lib().or_amg_level(nx, ny, nz, _p(a7), max_levels, max_coarse, level, _p(cf), _p(prp), _p(pci), _p(pv),
+                              _p(arp), _p(aci), _p(av))
+    assert 0 <= nnzp <= cap
+    return cf, (prp, pci[:nnzp].copy(), pv[:nnzp].copy()), (arp, aci, av)
+
+
 # ------------------------------------------------------------------ system
 
 class System:
     """A BSR system plus one preconditioner, driven through the C oracle."""
 
     def __init__(self, nx, ny, nz, row_ptr, col_idx, vals, pc="none", float_round=False,
-                 gmg_levels=6, gmg_coarse=512, gmg_sweeps=2, decoupling="qi", acc=None):
+                 gmg_levels=6, gmg_coarse=512, gmg_sweeps=2, decoupling="qi", acc=None, coarsening="gmg"):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.nb = nx * ny * nz
         self._rp, self._ci = _i32(row_ptr), _i32(col_idx)
@@ -260,6 +305,7 @@ class System:
             raise MemoryError("oracle system allocation failed")
         if acc is not None:
             lib().or_set_accumulation(self._h, _p(_f64(acc)))
+        lib().or_set_coarsening(self._h, COARSENING[coarsening])
         self.setup_status = lib().or_setup(self._h, PC[pc], gmg_levels, gmg_coarse, gmg_sweeps,
                                            int(float_round), DECOUPLING[decoupling])
         self.pc = pc

@@ -514,6 +514,385 @@ int or_gmg_vcycle(int nx, int ny, int nz, const double *a7, int max_levels, int 
     return st;
 }
 
+
+/* ---------------------------------------------------- algebraic multigrid */
+
+/* Algebraic coarsening for the pressure stage (Section "Algebraic Multigrid
+ * Methods", AMG setup algorithm: strength matrix, coarse set as a subset of
+ * the fine points, prolongation, R = P^T, Galerkin product, smoothers; and
+ * the same V-cycle algorithm as the geometric hierarchy).  The readings:
+ *   - strength: j != i strongly influences i when -a_ij >= theta max_{k != i}
+ *     (-a_ik), theta = 0.5 (the strength threshold of the default-parameter
+ *     figure); no strong connections when that maximum is <= 0;
+ *   - coarse set: PMIS (one of the parallel coarsenings the section names).
+ *     Measure lambda_i = |{k : i in S_k}| + u_i with u_i a counter-based
+ *     uniform in [0, 1) (splitmix64 of the point index).  Points that no
+ *     point depends on (lambda_i < 1) start as F.  Then, in rounds from the
+ *     previous round's state: an undecided point whose measure exceeds every
+ *     undecided strong neighbour's (S_i and S_i^T) becomes C; afterwards each
+ *     undecided point that strongly depends on a C point becomes F;
+ *   - prolongation: identity on C points; direct interpolation on F points,
+ *     w_ij = -alpha_i a_ij / a_ii for j in C_i = S_i n C, with
+ *     alpha_i = sum_{k != i} a_ik / sum_{k in C_i} a_ik (a zero row when C_i
+ *     is empty or that sum vanishes);
+ *   - smoother: l1-Jacobi, x += D^{-1} (b - A x) with D_ii = sum_j |a_ij|,
+ *     `sweeps` times before and after the coarse correction (the hybrid
+ *     Gauss-Seidel of the defaults is Jacobi between blocks; with one row per
+ *     block it is Jacobi, and the l1 diagonal keeps it convergent without a
+ *     damping parameter);
+ *   - levels: coarsen while a level has more than max_coarse points, up to
+ *     max_levels levels, and stop when a round keeps more than 90% of the
+ *     points; the coarsest level is solved exactly (dense LU). */
+typedef struct { int n; int *rp, *ci; double *v; } or_csr;
+
+static void csr_free(or_csr *a) { free(a->rp); free(a->ci); free(a->v); memset(a, 0, sizeof *a); }
+
+static double amg_uniform(int64_t i) {
+    uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Strength pattern: s_rp/s_ci list, per row, the columns j in S_i (ascending). */
+static void amg_strength(const or_csr *A, double theta, int **s_rp, int **s_ci) {
+    int n = A->n;
+    int *rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    int *ci = (int *)malloc(sizeof(int) * (size_t)(A->rp[n] > 0 ? A->rp[n] : 1));
+    for (int i = 0; i < n; ++i) {
+        double mx = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; ++p)
+            if (A->ci[p] != i && -A->v[p] > mx) mx = -A->v[p];
+        rp[i + 1] = rp[i];
+        if (!(mx > 0.0)) continue;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; ++p)
+            if (A->ci[p] != i && -A->v[p] >= theta * mx) ci[rp[i + 1]++] = A->ci[p];
+    }
+    *s_rp = rp;
+    *s_ci = ci;
+}
+
+/* PMIS: cf[i] = 1 (C) or -1 (F). */
+static void amg_pmis(int n, const int *s_rp, const int *s_ci, int *cf) {
+    int *cnt = (int *)calloc((size_t)n, sizeof(int));
+    for (int i = 0; i < n; ++i)
+        for (int p = s_rp[i]; p < s_rp[i + 1]; ++p) cnt[s_ci[p]]++;
+    /* transpose of S: t_ci lists the points k with i in S_k */
+    int *t_rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; ++i) t_rp[i + 1] = t_rp[i] + cnt[i];
+    int *t_ci = (int *)malloc(sizeof(int) * (size_t)(t_rp[n] > 0 ? t_rp[n] : 1));
+    int *fill = (int *)calloc((size_t)n, sizeof(int));
+    for (int k = 0; k < n; ++k)
+        for (int p = s_rp[k]; p < s_rp[k + 1]; ++p) {
+            int i = s_ci[p];
+            t_ci[t_rp[i] + fill[i]++] = k;
+        }
+    double *lam = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        lam[i] = cnt[i] + amg_uniform(i);
+        cf[i] = lam[i] < 1.0 ? -1 : 0;
+    }
+    int *newc = (int *)calloc((size_t)n, sizeof(int));
+    for (;;) {
+        int undecided = 0;
+        for (int i = 0; i < n; ++i) undecided += cf[i] == 0;
+        if (!undecided) break;
+        for (int i = 0; i < n; ++i) {
+            newc[i] = 0;
+            if (cf[i] != 0) continue;
+            int best = 1;
+            for (int p = s_rp[i]; p < s_rp[i + 1] && best; ++p)
+                if (cf[s_ci[p]] == 0 && lam[s_ci[p]] >= lam[i]) best = 0;
+            for (int p = t_rp[i]; p < t_rp[i + 1] && best; ++p)
+                if (cf[t_ci[p]] == 0 && lam[t_ci[p]] >= lam[i]) best = 0;
+            newc[i] = best;
+        }
+        for (int i = 0; i < n; ++i)
+            if (newc[i]) cf[i] = 1;
+        for (int i = 0; i < n; ++i) {
+            if (cf[i] != 0) continue;
+            for (int p = s_rp[i]; p < s_rp[i + 1]; ++p)
+                if (cf[s_ci[p]] == 1) { cf[i] = -1; break; }
+        }
+    }
+    free(cnt); free(t_rp); free(t_ci); free(fill); free(lam); free(newc);
+}
+
+/* Direct interpolation P (n x nc, CSR, columns ascending); cidx[i] = coarse index of C point i. */
+static void amg_interp(const or_csr *A, const int *s_rp, const int *s_ci, const int *cf, const int *cidx,
+                       or_csr *P) {
+    int n = A->n;
+    P->n = n;
+    P->rp = (int *)calloc((size_t)n + 1, sizeof(int));
+    P->ci = (int *)malloc(sizeof(int) * (size_t)(s_rp[n] + n + 1));
+    P->v = (double *)malloc(sizeof(double) * (size_t)(s_rp[n] + n + 1));
+    int q = 0;
+    for (int i = 0; i < n; ++i) {
+        if (cf[i] == 1) {
+            P->ci[q] = cidx[i];
+            P->v[q++] = 1.0;
+        } else {
+            double aii = 0.0, sum_n = 0.0, sum_c = 0.0;
+            for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+                if (A->ci[p] == i) { aii = A->v[p]; continue; }
+                sum_n += A->v[p];
+            }
+            /* strong C neighbours, with their coefficients a_ij */
+            for (int p = s_rp[i]; p < s_rp[i + 1]; ++p) {
+                int j = s_ci[p];
+                if (cf[j] != 1) continue;
+                for (int r = A->rp[i]; r < A->rp[i + 1]; ++r)
+                    if (A->ci[r] == j) sum_c += A->v[r];
+            }
+            if (sum_c != 0.0 && aii != 0.0) {
+                double alpha = sum_n / sum_c;
+                for (int p = s_rp[i]; p < s_rp[i + 1]; ++p) {
+                    int j = s_ci[p];
+                    if (cf[j] != 1) continue;
+                    for (int r = A->rp[i]; r < A->rp[i + 1]; ++r)
+                        if (A->ci[r] == j) {
+                            P->ci[q] = cidx[j];
+                            P->v[q++] = -alpha * A->v[r] / aii;
+                        }
+                }
+            }
+        }
+        P->rp[i + 1] = q;
+    }
+}
+
+/* Galerkin product Ac = P^T A P (nc x nc, CSR, columns ascending).  Entry
+ * (I, J) sums P_fI a_fk P_kJ over fine rows f (ascending), their entries k
+ * (row order) and P's entries in row k (row order). */
+static void amg_rap(const or_csr *A, const or_csr *P, int nc, or_csr *Ac) {
+    int n = A->n;
+    double *acc = (double *)calloc((size_t)nc, sizeof(double));
+    int *mark = (int *)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    for (int J = 0; J < nc; ++J) mark[J] = -1;
+    /* P^T as lists of (f, P_fI) per coarse row I, f ascending */
+    int *t_rp = (int *)calloc((size_t)nc + 1, sizeof(int));
+    for (int f = 0; f < n; ++f)
+        for (int p = P->rp[f]; p < P->rp[f + 1]; ++p) t_rp[P->ci[p] + 1]++;
+    for (int I = 0; I < nc; ++I) t_rp[I + 1] += t_rp[I];
+    int *t_f = (int *)malloc(sizeof(int) * (size_t)(t_rp[nc] > 0 ? t_rp[nc] : 1));
+    double *t_v = (double *)malloc(sizeof(double) * (size_t)(t_rp[nc] > 0 ? t_rp[nc] : 1));
+    int *fill = (int *)calloc((size_t)nc, sizeof(int));
+    for (int f = 0; f < n; ++f)
+        for (int p = P->rp[f]; p < P->rp[f + 1]; ++p) {
+            int I = P->ci[p];
+            t_f[t_rp[I] + fill[I]] = f;
+            t_v[t_rp[I] + fill[I]++] = P->v[p];
+        }
+    int cap = 16 * (nc > 0 ? nc : 1);
+    Ac->n = nc;
+    Ac->rp = (int *)calloc((size_t)nc + 1, sizeof(int));
+    Ac->ci = (int *)malloc(sizeof(int) * (size_t)cap);
+    Ac->v = (double *)malloc(sizeof(double) * (size_t)cap);
+    int *cols = (int *)malloc(sizeof(int) * (size_t)(nc > 0 ? nc : 1));
+    int q = 0;
+    for (int I = 0; I < nc; ++I) {
+        int nnz = 0;
+        for (int t = t_rp[I]; t < t_rp[I + 1]; ++t) {
+            int f = t_f[t];
+            double pf = t_v[t];
+            for (int a = A->rp[f]; a < A->rp[f + 1]; ++a) {
+                int k = A->ci[a];
+                for (int b = P->rp[k]; b < P->rp[k + 1]; ++b) {
+                    int J = P->ci[b];
+                    if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; cols[nnz++] = J; }
+                    acc[J] += pf * A->v[a] * P->v[b];
+                }
+            }
+        }
+        /* ascending columns */
+        for (int x = 1; x < nnz; ++x) {
+            int c = cols[x], y = x - 1;
+            while (y >= 0 && cols[y] > c) { cols[y + 1] = cols[y]; --y; }
+            cols[y + 1] = c;
+        }
+        if (q + nnz > cap) {
+            while (q + nnz > cap) cap *= 2;
+            Ac->ci = (int *)realloc(Ac->ci, sizeof(int) * (size_t)cap);
+            Ac->v = (double *)realloc(Ac->v, sizeof(double) * (size_t)cap);
+        }
+        for (int x = 0; x < nnz; ++x) {
+            Ac->ci[q] = cols[x];
+            Ac->v[q++] = acc[cols[x]];
+        }
+        Ac->rp[I + 1] = q;
+    }
+    free(acc); free(mark); free(t_rp); free(t_f); free(t_v); free(fill); free(cols);
+}
+
+#define OR_AMG_MAX 8
+typedef struct {
+    int nlev, sweeps;
+    or_csr A[OR_AMG_MAX], P[OR_AMG_MAX];  /* P[l]: level l -> l+1 */
+    int *cf[OR_AMG_MAX];                  /* C/F splitting of level l (1 C, -1 F) */
+    double *dl1[OR_AMG_MAX];              /* l1 row norms */
+    double *x[OR_AMG_MAX], *b[OR_AMG_MAX], *r[OR_AMG_MAX];
+    double *coarse_dense;
+} or_amg;
+
+static void amg_free(or_amg *g) {
+    for (int l = 0; l < g->nlev; ++l) {
+        csr_free(&g->A[l]);
+        csr_free(&g->P[l]);
+        free(g->cf[l]);
+        free(g->dl1[l]); free(g->x[l]); free(g->b[l]); free(g->r[l]);
+    }
+    free(g->coarse_dense);
+    memset(g, 0, sizeof *g);
+}
+
+/* Build the hierarchy from the seven-point pressure stencil a7 (slots -z,-y,-x,centre,+x,+y,+z). */
+static int amg_build(or_amg *g, int nx, int ny, int nz, const double *a7, int max_levels, int max_coarse,
+                     int sweeps) {
+    memset(g, 0, sizeof *g);
+    if (max_levels > OR_AMG_MAX) max_levels = OR_AMG_MAX;
+    g->sweeps = sweeps;
+    int n0 = nx * ny * nz;
+    or_csr *A = &g->A[0];
+    A->n = n0;
+    A->rp = (int *)calloc((size_t)n0 + 1, sizeof(int));
+    A->ci = (int *)malloc(sizeof(int) * 7 * (size_t)n0);
+    A->v = (double *)malloc(sizeof(double) * 7 * (size_t)n0);
+    int q = 0;
+    for (int c = 0; c < n0; ++c) {
+        int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        for (int s = 0; s < 7; ++s) {  /* slot order is ascending column order */
+            int ii = i + SX[s], jj = j + SY[s], kk = k + SZ[s];
+            if (ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz) continue;
+            A->ci[q] = nx * ny * kk + nx * jj + ii;
+            A->v[q++] = a7[7 * (size_t)c + s];
+        }
+        A->rp[c + 1] = q;
+    }
+    int l = 0;
+    while (l + 1 < max_levels && g->A[l].n > max_coarse) {
+        int *s_rp, *s_ci;
+        amg_strength(&g->A[l], 0.5, &s_rp, &s_ci);
+        int n = g->A[l].n;
+        int *cf = (int *)malloc(sizeof(int) * (size_t)n), *cidx = (int *)malloc(sizeof(int) * (size_t)n);
+        amg_pmis(n, s_rp, s_ci, cf);
+        int nc = 0;
+        for (int i = 0; i < n; ++i) cidx[i] = cf[i] == 1 ? nc++ : -1;
+        if (nc == 0 || nc > 0.9 * n) { free(s_rp); free(s_ci); free(cf); free(cidx); break; }
+        amg_interp(&g->A[l], s_rp, s_ci, cf, cidx, &g->P[l]);
+        amg_rap(&g->A[l], &g->P[l], nc, &g->A[l + 1]);
+        g->cf[l] = cf;
+        free(s_rp); free(s_ci); free(cidx);
+        ++l;
+    }
+    g->nlev = l + 1;
+    for (int q2 = 0; q2 < g->nlev; ++q2) {
+        int n = g->A[q2].n;
+        g->dl1[q2] = (double *)calloc((size_t)n, sizeof(double));
+        for (int i = 0; i < n; ++i)
+            for (int p = g->A[q2].rp[i]; p < g->A[q2].rp[i + 1]; ++p) g->dl1[q2][i] += fabs(g->A[q2].v[p]);
+        g->x[q2] = (double *)calloc((size_t)n, sizeof(double));
+        g->b[q2] = (double *)calloc((size_t)n, sizeof(double));
+        g->r[q2] = (double *)calloc((size_t)n, sizeof(double));
+    }
+    int L = g->nlev - 1, nc = g->A[L].n;
+    if (nc > 4096) return OR_EINVAL;
+    g->coarse_dense = (double *)calloc((size_t)nc * nc, sizeof(double));
+    for (int i = 0; i < nc; ++i)
+        for (int p = g->A[L].rp[i]; p < g->A[L].rp[i + 1]; ++p) g->coarse_dense[(size_t)i * nc + g->A[L].ci[p]] += g->A[L].v[p];
+    return OR_OK;
+}
+
+static void csr_residual(const or_csr *A, const double *b, const double *x, double *r) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < A->n; ++i) {
+        double s = 0.0;
+        for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) s += A->v[p] * x[A->ci[p]];
+        r[i] = b[i] - s;
+    }
+}
+
+static int amg_vcycle(or_amg *g, int l) {
+    const or_csr *A = &g->A[l];
+    int n = A->n;
+    if (l == g->nlev - 1) return or_dense_solve(n, g->coarse_dense, g->b[l], g->x[l]);
+    memset(g->x[l], 0, sizeof(double) * (size_t)n);
+    for (int s = 0; s < g->sweeps; ++s) {
+        csr_residual(A, g->b[l], g->x[l], g->r[l]);
+        for (int i = 0; i < n; ++i) g->x[l][i] += g->r[l][i] / g->dl1[l][i];
+    }
+    csr_residual(A, g->b[l], g->x[l], g->r[l]);
+    const or_csr *P = &g->P[l];
+    int nc = g->A[l + 1].n;
+    memset(g->b[l + 1], 0, sizeof(double) * (size_t)nc);
+    for (int f = 0; f < n; ++f)  /* b_{l+1} = P^T r */
+        for (int p = P->rp[f]; p < P->rp[f + 1]; ++p) g->b[l + 1][P->ci[p]] += P->v[p] * g->r[l][f];
+    int st = amg_vcycle(g, l + 1);
+    if (st) return st;
+    for (int f = 0; f < n; ++f) {  /* x += P x_{l+1} */
+        double s = 0.0;
+        for (int p = P->rp[f]; p < P->rp[f + 1]; ++p) s += P->v[p] * g->x[l + 1][P->ci[p]];
+        g->x[l][f] += s;
+    }
+    for (int s = 0; s < g->sweeps; ++s) {
+        csr_residual(A, g->b[l], g->x[l], g->r[l]);
+        for (int i = 0; i < n; ++i) g->x[l][i] += g->r[l][i] / g->dl1[l][i];
+    }
+    return OR_OK;
+}
+
+/* Stand-alone AMG pieces for tests.  or_amg_hierarchy: level count, and per
+ * level its size and nonzeros (int[2 * OR_AMG_MAX]).  or_amg_vcycle: one
+ * V-cycle e = V(rhs) from a zero guess. */
+int or_amg_hierarchy(int nx, int ny, int nz, const double *a7, int max_levels, int max_coarse, int *sizes) {
+    or_amg g;
+    int st = amg_build(&g, nx, ny, nz, a7, max_levels, max_coarse, 2);
+    int nl = g.nlev;
+    for (int l = 0; l < nl; ++l) { sizes[2 * l] = g.A[l].n; sizes[2 * l + 1] = g.A[l].rp[g.A[l].n]; }
+    amg_free(&g);
+    return st ? -st : nl;
+}
+
+int or_amg_vcycle(int nx, int ny, int nz, const double *a7, int max_levels, int max_coarse, int sweeps,
+                  const double *rhs, double *e, int *nlev_out) {
+    or_amg g;
+    int st = amg_build(&g, nx, ny, nz, a7, max_levels, max_coarse, sweeps);
+    if (!st) {
+        memcpy(g.b[0], rhs, sizeof(double) * (size_t)nx * ny * nz);
+        st = amg_vcycle(&g, 0);
+        memcpy(e, g.x[0], sizeof(double) * (size_t)nx * ny * nz);
+    }
+    if (nlev_out) *nlev_out = g.nlev;
+    amg_free(&g);
+    return st;
+}
+
+/* Level l's strength pattern, C/F splitting, prolongation and coarse operator
+ * for tests: copies into caller arrays sized by or_amg_hierarchy's counts.
+ * cf[n_l]; P as (rp[n_l+1], ci, v) with at most nnzP entries (returned);
+ * Ac as (rp[nc+1], ci, v). */
+int or_amg_level(int nx, int ny, int nz, const double *a7, int max_levels, int max_coarse, int level, int *cf,
+                 int *p_rp, int *p_ci, double *p_v, int *a_rp, int *a_ci, double *a_v) {
+    or_amg g;
+    int st = amg_build(&g, nx, ny, nz, a7, max_levels, max_coarse, 2);
+    int nnzp = -1;
+    if (!st && level + 1 < g.nlev) {
+        const or_csr *P = &g.P[level], *Ac = &g.A[level + 1];
+        int n = g.A[level].n;
+        for (int i = 0; i < n; ++i) {
+            cf[i] = g.cf[level][i];
+            p_rp[i] = P->rp[i];
+        }
+        p_rp[n] = P->rp[n];
+        for (int p = 0; p < P->rp[n]; ++p) { p_ci[p] = P->ci[p]; p_v[p] = P->v[p]; }
+        for (int I = 0; I <= Ac->n; ++I) a_rp[I] = Ac->rp[I];
+        for (int p = 0; p < Ac->rp[Ac->n]; ++p) { a_ci[p] = Ac->ci[p]; a_v[p] = Ac->v[p]; }
+        nnzp = P->rp[n];
+    }
+    amg_free(&g);
+    return st ? -st : nnzp;
+}
+
 /* ------------------------------------------------------------ system + PCs */
 
 enum { PC_NONE = 0, PC_BJACOBI = 1, PC_BILU0 = 2, PC_CPR = 3, PC_CPR_FP = 5, PC_CPR_FPF = 6, PC_CPR_FFPF = 7 };
@@ -528,6 +907,8 @@ typedef struct {
     double *lu, *udinv; /* block ILU(0) */
     double *w, *a7;   /* decoupling weights, pressure stencil */
     double *acc;      /* accumulation blocks [nb][3][3] (true-IMPES), or NULL */
+    int coarsening;   /* pressure hierarchy: 0 geometric (GMG), 1 algebraic (AMG) */
+    or_amg amg;
     or_gmg gmg;
     double *tmp_p, *tmp_x, *tmp_r;
     int64_t pc_applies;
@@ -554,6 +935,7 @@ void or_destroy(or_system *s) {
     free(s->v); free(s->dinv); free(s->lu); free(s->udinv); free(s->w); free(s->a7); free(s->acc);
     free(s->tmp_p); free(s->tmp_x); free(s->tmp_r);
     if (s->gmg.nlev) gmg_free(&s->gmg);
+    if (s->amg.nlev) amg_free(&s->amg);
     free(s);
 }
 
@@ -601,8 +983,21 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
             for (size_t q = 0; q < 3 * (size_t)nb; ++q) s->w[q] = round_f32(s->w[q]);
             for (size_t q = 0; q < 7 * (size_t)nb; ++q) s->a7[q] = round_f32(s->a7[q]);
         }
-        gmg_build(&s->gmg, s->nx, s->ny, s->nz, s->a7, gmg_levels, gmg_coarse, gmg_sweeps);
-        if (float_round)
+        if (s->coarsening == 1) {
+            st = amg_build(&s->amg, s->nx, s->ny, s->nz, s->a7, gmg_levels, gmg_coarse, gmg_sweeps);
+            if (st) return st;
+            if (float_round)
+                for (int l = 0; l < s->amg.nlev; ++l) {
+                    or_csr *A = &s->amg.A[l], *P = &s->amg.P[l];
+                    for (int p = 0; p < A->rp[A->n]; ++p) A->v[p] = round_f32(A->v[p]);
+                    if (P->rp)
+                        for (int p = 0; p < P->rp[P->n]; ++p) P->v[p] = round_f32(P->v[p]);
+                    for (int i = 0; i < A->n; ++i) s->amg.dl1[l][i] = round_f32(s->amg.dl1[l][i]);
+                }
+        } else {
+            gmg_build(&s->gmg, s->nx, s->ny, s->nz, s->a7, gmg_levels, gmg_coarse, gmg_sweeps);
+        }
+        if (float_round && s->coarsening != 1)
             for (int l = 1; l < s->gmg.nlev; ++l)
                 for (size_t q = 0; q < 7 * (size_t)s->gmg.nx[l] * s->gmg.ny[l] * s->gmg.nz[l]; ++q)
                     s->gmg.a7[l][q] = round_f32(s->gmg.a7[l][q]);
@@ -616,12 +1011,19 @@ int or_setup(or_system *s, int pc, int gmg_levels, int gmg_coarse, int gmg_sweep
 /* CPR-PF in its two-stage multiplicative form (the printed listing overwrites
  * x and reuses f; the reading here is the standard one):
  *   x = Pi_p M_g^{-1} Pi_r f;  r = f - A x;  x = x + ILU0^{-1} r. */
+/* The pressure stage's solve on its right-hand side / solution buffers. */
+static double *pstage_b(or_system *s) { return s->coarsening == 1 ? s->amg.b[0] : s->gmg.b[0]; }
+static double *pstage_x(or_system *s) { return s->coarsening == 1 ? s->amg.x[0] : s->gmg.x[0]; }
+static int pstage_vcycle(or_system *s) { return s->coarsening == 1 ? amg_vcycle(&s->amg, 0) : gmg_vcycle(&s->gmg, 0); }
+
+void or_set_coarsening(or_system *s, int mode) { s->coarsening = mode; }
+
 static int cpr_apply(or_system *s, const double *f, double *x) {
     int nb = s->nb;
-    or_restrict_pressure(nb, s->w, f, s->gmg.b[0]);
-    int st = gmg_vcycle(&s->gmg, 0);
+    or_restrict_pressure(nb, s->w, f, pstage_b(s));
+    int st = pstage_vcycle(s);
     if (st) return st;
-    or_prolong_pressure(nb, s->gmg.x[0], x);
+    or_prolong_pressure(nb, pstage_x(s), x);
     memcpy(s->tmp_r, f, sizeof(double) * 3 * (size_t)nb);
     or_spmv(nb, s->rp, s->ci, s->v, -1.0, x, 1.0, s->tmp_r);
     or_bilu0_apply(nb, s->rp, s->ci, s->lu, s->udinv, s->tmp_r, s->tmp_x);
@@ -644,10 +1046,10 @@ static void stage_full(or_system *s, const double *r, double *y) {
     or_bilu0_apply(s->nb, s->rp, s->ci, s->lu, s->udinv, r, y);
 }
 static int stage_pressure(or_system *s, const double *r, double *y) {
-    or_restrict_pressure(s->nb, s->w, r, s->gmg.b[0]);
-    int st = gmg_vcycle(&s->gmg, 0);
+    or_restrict_pressure(s->nb, s->w, r, pstage_b(s));
+    int st = pstage_vcycle(s);
     if (st) return st;
-    or_prolong_pressure(s->nb, s->gmg.x[0], y);
+    or_prolong_pressure(s->nb, pstage_x(s), y);
     return OR_OK;
 }
 static int cpr_apply_order(or_system *s, const char *stages, const double *f, double *x) {
@@ -694,7 +1096,7 @@ void or_get_factors(const or_system *s, double *udinv, double *w, double *a7) {
     if (a7 && s->a7) memcpy(a7, s->a7, sizeof(double) * 7 * (size_t)s->nb);
 }
 
-int or_gmg_levels(const or_system *s) { return s->gmg.nlev; }
+int or_gmg_levels(const or_system *s) { return s->coarsening == 1 ? s->amg.nlev : s->gmg.nlev; }
 
 /* ------------------------------------------------------------------ GMRES */
 
