@@ -177,12 +177,13 @@ class OracleSample:
     full iteration count.  The sample's iterations are the first of a restart cycle, whose
     Gram-Schmidt work is below a cycle's average; the preconditioner dominates each iteration."""
 
-    def __init__(self, p, pc, full_iters, threads=None):
+    def __init__(self, p, pc, full_iters, threads=None, coarsening="gmg"):
         import oracle
         self.threads = oracle.use_threads(threads or os.cpu_count() or 1)
         self.p, self.full_iters = p, full_iters
         t0 = time.perf_counter()
-        self.sys = oracle.System.from_problem(p, pc=pc)
+        kw = {"coarsening": "amg", "gmg_levels": 8} if coarsening == "amg" else {}
+        self.sys = oracle.System.from_problem(p, pc=pc, **kw)
         self.setup_s = time.perf_counter() - t0
 
     def run(self, sample_iters):
@@ -195,10 +196,10 @@ class OracleSample:
         return 1e3 * (self.setup_s + per_iter_s * self.full_iters)
 
 
-def cpu_baseline(p, workload, pc, full_iters, sample_iters):
+def cpu_baseline(p, workload, pc, full_iters, sample_iters, coarsening="gmg"):
     """cpu_baseline entry of the bench line: one OracleSample run."""
     t_all = time.perf_counter()
-    o = OracleSample(p, pc, full_iters)
+    o = OracleSample(p, pc, full_iters, coarsening=coarsening)
     dt, done = o.run(sample_iters)
     per_iter = dt / done
     return {"value": round(o.projected_ms(per_iter), 3), "unit": "ms", "cores": o.threads, "kind": "oracle",
@@ -218,12 +219,12 @@ def run_reference(args, rank, ws):
         return 0
     import synth
     p = synth.workload(args.workload)
-    full_iters = golden_iters(args.workload, f"gmres/{args.pc}")
+    full_iters = golden_iters(args.workload, f"gmres/{pc_key(args)}")
     if full_iters is None:
         print(json.dumps({"impl": "reference", "unavailable": f"no recorded oracle iteration count for "
-                          f"{args.workload} gmres/{args.pc}"}), flush=True)
+                          f"{args.workload} gmres/{pc_key(args)}"}), flush=True)
         return 0
-    o = OracleSample(p, args.pc, full_iters)
+    o = OracleSample(p, args.pc, full_iters, coarsening=args.coarsening)
     for _ in range(args.warmup):
         o.run(max(1, args.ref_sample_iters // 2))
     t0 = time.perf_counter()
@@ -239,7 +240,7 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(p, args.workload, args.pc, ws),
+            "config": bench_config(p, args.workload, pc_key(args), ws),
             "value_is_projection": True,
             "projection": f"value = oracle setup ({o.setup_s:.1f} s) + mean time per GMRES iteration over the "
                           f"{args.steps} timed steps ({per_iter:.3f} s) x the oracle's {full_iters} iterations of "
@@ -556,7 +557,7 @@ def run_profile_mode(args):
     A.set_values(p.vals)
     if mode == "profile-solve":
         s = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=60, precision="mixed")
-        s.setup(args.pc)
+        s.setup(args.pc, **pc_kwargs(args))
         b = torch.from_numpy(p.b).cuda()
         x = torch.zeros_like(b)
         st, info = s.solve(b, x)
@@ -583,7 +584,20 @@ def run_profile_mode(args):
 
 PC_DESC = {"cpr": "CPR-PF: quasi-IMPES, GMG V-cycle (2 red-black sweeps, <= 6 levels), block ILU(0) "
                   "(i+j+k wavefront tiles)",
+           "cpr-amg": "CPR-PF: quasi-IMPES, AMG V-cycle (PMIS, direct interpolation, 2 l1-Jacobi sweeps, <= 8 "
+                      "levels), block ILU(0) (i+j+k wavefront tiles)",
            "bilu0": "block ILU(0) (i+j+k wavefront tiles)"}
+
+
+def pc_kwargs(args):
+    """Preconditioner parameters of the run: the pressure stage's coarsening for CPR."""
+    if args.pc == "cpr" and args.coarsening == "amg":
+        return {"coarsening": "amg", "gmg_max_levels": 8}
+    return {}
+
+
+def pc_key(args):
+    return "cpr-amg" if args.pc == "cpr" and args.coarsening == "amg" else args.pc
 MOBILITY_READING = ("M_ij: off-diagonal entries U(0.1,1), each diagonal entry U(0.1,1) plus its row's three draws "
                     "(row-diagonally dominant); nine i.i.d. U(0.1,1) entries make the Jacobian indefinite")
 
@@ -638,7 +652,7 @@ def run_bench(args, rank, ws, local, dist):
     s64 = rsv.Solver(A, solver="gmres", restart=30, rtol=1e-8, maxit=6000, precision="fp64")
 
     def step(solver):
-        solver.setup(args.pc)
+        solver.setup(args.pc, **pc_kwargs(args))
         x.zero_()
         st, info = solver.solve(b, x)
         if st != rsv.RSV_OK:
@@ -695,7 +709,7 @@ def run_bench(args, rank, ws, local, dist):
     zs32 = torch.empty_like(xs32)
     ilu32_ms = event_ms(lambda: s_ilu.apply(xs32, zs32), 10)
     del s_ilu
-    s.setup(args.pc)
+    s.setup(args.pc, **pc_kwargs(args))
     pc32_ms = event_ms(lambda: s.apply(xs32, zs32), 10)
     ib32 = ilu_apply_bytes(p.nb, p.nnzb, 4)
     ilu32_gbs = ib32 / (ilu32_ms * 1e-3) / 1e9
@@ -723,7 +737,7 @@ def run_bench(args, rank, ws, local, dist):
     e0.record(stream)
     for _ in range(args.e2e_steps):
         A.set_values(vals_h.numpy())
-        s.setup(args.pc)
+        s.setup(args.pc, **pc_kwargs(args))
         x_h.zero_()
         st, einfo = s.solve(b_h.numpy(), x_h.numpy())
         assert st == rsv.RSV_OK, rsv.status_string(st)
@@ -737,22 +751,22 @@ def run_bench(args, rank, ws, local, dist):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        full = golden_iters(args.workload, f"gmres/{args.pc}") or info64["iters"]
-        cpu = cpu_baseline(p, args.workload, args.pc, full, args.cpu_sample_iters)
+        full = golden_iters(args.workload, f"gmres/{pc_key(args)}") or info64["iters"]
+        cpu = cpu_baseline(p, args.workload, args.pc, full, args.cpu_sample_iters, args.coarsening)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner / f64 refinement", "data": "synthetic",
-            "config": bench_config(p, args.workload, args.pc, ws),
+            "config": bench_config(p, args.workload, pc_key(args), ws),
             "iters": info["iters"], "outer_iters": info["outer_iters"], "true_relres": info["true_relres"],
             "ms_setup": round(info["ms_setup"], 3), "ms_solve": round(info["ms_solve"], 3),
             "fp64": {"ms_per_step": round(ms64, 3), "steps": fp64_steps, "warmup": 1, "iters": info64["iters"],
                      "true_relres": info64["true_relres"], "ms_setup": round(info64["ms_setup"], 3),
                      "speedup_mixed_over_fp64": round(ms64 / ms, 3),
-                     "oracle_iters": golden_iters(args.workload, f"gmres/{args.pc}")},
-            "oracle_refinement_iters": golden_iters(args.workload, f"refine-gmres/{args.pc}"),
+                     "oracle_iters": golden_iters(args.workload, f"gmres/{pc_key(args)}")},
+            "oracle_refinement_iters": golden_iters(args.workload, f"refine-gmres/{pc_key(args)}"),
             "kernels": {"spmv_f64_ms": round(spmv_ms, 4), "spmv_f64_gbs": round(spmv_gbs, 1),
                         "spmv_f64_frac": round(spmv_gbs / peak, 4),
                         "spmv_f64_gflops": round(spmv_flops(p.nnzb) / (spmv_ms * 1e-3) / 1e9, 1),
@@ -780,6 +794,8 @@ def main():
     ap.add_argument("--impl", default="rsv", choices=["rsv", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["large_256x256x128", "mid_100x100x50"])
     ap.add_argument("--pc", default=PC, choices=["cpr", "bilu0"])
+    ap.add_argument("--coarsening", default="gmg", choices=["gmg", "amg"],
+                    help="CPR's pressure hierarchy: geometric (default) or algebraic")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 solves (at most --steps)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-iters", type=int, default=10)

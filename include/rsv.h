@@ -118,12 +118,26 @@ typedef struct {
  *      rsv_precond_set_accumulation; RSV_EINVAL at setup without it), so that
  *      w_c C_c = (1, 0, 0): the secondary unknowns leave the accumulation terms.
  *      RSV_ESINGULAR at setup when |det C_c| <= 1e-300.
- * The pressure operator is A_pp(c, l) = w_c . A_cl[:, 0] in every case. */
+ * The pressure operator is A_pp(c, l) = w_c . A_cl[:, 0] in every case.
+ * coarsening selects the pressure stage's hierarchy (Section "Algebraic
+ * Multigrid Methods", AMG setup algorithm and V-cycle):
+ *   0  geometric: 2x2x2 boxes, Galerkin seven-point levels, red-black
+ *      Gauss-Seidel (gmg_sweeps before and after);
+ *   1  algebraic: strength threshold 0.5, PMIS coarse points, direct
+ *      interpolation, Galerkin products R A P with R = P^T, l1-Jacobi smoothing
+ *      (gmg_sweeps before and after), the coarsest level solved exactly.  The
+ *      hierarchy is built on the host at rsv_precond_setup from the pressure
+ *      operator computed on the device; the V-cycle runs on the device.  Levels:
+ *      coarsen while a level has more than gmg_max_coarse points, at most
+ *      gmg_max_levels (8 reaches small grids; the paper's default 6 may not),
+ *      stopping when a level keeps more than 90% of its points.  RSV_ENOTSUP
+ *      when the coarsest level would exceed 1024 points. */
 typedef struct {
     int gmg_max_levels;    /* <= 8 */
     int gmg_max_coarse;    /* stop coarsening at or below this many cells */
     int gmg_sweeps;        /* red-black Gauss-Seidel sweeps before and after */
     int decoupling;        /* 0 quasi-IMPES, 1 ABF, 2 true-IMPES */
+    int coarsening;        /* pressure hierarchy: 0 geometric (default), 1 algebraic (see below) */
 } rsv_pc_params;
 
 /* Filled by rsv_solve. */
@@ -143,7 +157,7 @@ typedef struct {
 /* Defaults: GMRES, m = 30, rtol 1e-8, atol 0, btol 1e-30, maxit 2000, FP64,
  * inner_rtol 1e-5, max_outer 10, watchdog 2,000,000 us. */
 RSV_API void rsv_solver_params_default(rsv_solver_params *p);
-/* Defaults: 6 levels, 512 coarse cells, 2 sweeps. */
+/* Defaults: 6 levels, 512 coarse cells, 2 sweeps, quasi-IMPES, geometric coarsening. */
 RSV_API void rsv_pc_params_default(rsv_pc_params *p);
 RSV_API const char *rsv_status_string(rsv_status s);
 /* Text of the last CUDA runtime error seen by a call on this thread that
@@ -285,6 +299,11 @@ RSV_API rsv_status rsv_precond_apply_f32(rsv_solver *s, const float *r, float *z
  * concatenated (host float64[sum_l cells_l][7], slots -z, -y, -x, centre, +x,
  * +y, +z).  Any output may be NULL.  Synchronises the stream. */
 RSV_API rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, double *a7_host);
+/* The algebraic pressure hierarchy of a CPR preconditioner set up with
+ * coarsening = 1: its level count and, per level, its points and nonzeros
+ * (int64[2 * nlev], finest first; either output may be NULL).  RSV_EINVAL for
+ * any other preconditioner. */
+RSV_API rsv_status rsv_amg_info(rsv_solver *s, int *nlev, int64_t *sizes);
 /* One multigrid V-cycle on the finest pressure system from a zero guess
  * (Section "Algebraic Multigrid Methods", V-cycle algorithm): x = V(b);
  * device float64[nb] (FP64 solver with a CPR preconditioner only). */

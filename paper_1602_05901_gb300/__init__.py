@@ -47,7 +47,7 @@ class rsv_solver_params(ctypes.Structure):
 
 class rsv_pc_params(ctypes.Structure):
     _fields_ = [("gmg_max_levels", ctypes.c_int), ("gmg_max_coarse", ctypes.c_int), ("gmg_sweeps", ctypes.c_int),
-                ("decoupling", ctypes.c_int)]
+                ("decoupling", ctypes.c_int), ("coarsening", ctypes.c_int)]
 
 
 class rsv_solve_info(ctypes.Structure):
@@ -97,6 +97,7 @@ _SIGS = {
     "rsv_precond_get_dinv": (_I, [_P, _P]),
     "rsv_cpr_info": (_I, [_P, ctypes.POINTER(_I), _P, _P, _P]),
     "rsv_cpr_vcycle": (_I, [_P, _P, _P]),
+    "rsv_amg_info": (_I, [_P, ctypes.POINTER(_I), _P]),
     "rsv_solve": (_I, [_P, _P, _P, ctypes.POINTER(rsv_solve_info)]),
     "rsv_solve_ptr": (_I, [_P, _P, _P, _I, ctypes.POINTER(rsv_solve_info)]),
     "rsv_solve_batched": (_I, [_P, _P, _P, _P]),
@@ -179,11 +180,15 @@ def solver_params(solver="gmres", restart=30, rtol=1e-8, atol=0.0, btol=1e-30, m
 DECOUPLING = {"qi": 0, "abf": 1, "timpes": 2}
 
 
-def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2, decoupling="qi"):
+COARSENING = {"gmg": 0, "amg": 1}
+
+
+def pc_params(gmg_max_levels=6, gmg_max_coarse=512, gmg_sweeps=2, decoupling="qi", coarsening="gmg"):
     p = rsv_pc_params()
     _lib.rsv_pc_params_default(ctypes.byref(p))
     p.gmg_max_levels, p.gmg_max_coarse, p.gmg_sweeps = gmg_max_levels, gmg_max_coarse, gmg_sweeps
     p.decoupling = DECOUPLING[decoupling] if isinstance(decoupling, str) else decoupling
+    p.coarsening = COARSENING[coarsening] if isinstance(coarsening, str) else coarsening
     return p
 
 
@@ -363,6 +368,13 @@ class Solver:
             out.append(a7[off:off + a * b_ * c])
             off += a * b_ * c
         return levels, w, out
+
+    def amg_info(self):
+        """[(points, nonzeros)] per level of the algebraic pressure hierarchy, finest first."""
+        nl = ctypes.c_int()
+        sizes = np.zeros(32, dtype=np.int64)
+        check(_lib.rsv_amg_info(self.handle, ctypes.byref(nl), _ptr(sizes)), "rsv_amg_info")
+        return [(int(sizes[2 * l]), int(sizes[2 * l + 1])) for l in range(nl.value)]
 
     def vcycle(self, b, x):
         check(_lib.rsv_cpr_vcycle(self.handle, _ptr(b), _ptr(x)), "rsv_cpr_vcycle")

@@ -51,6 +51,7 @@ void rsv_pc_params_default(rsv_pc_params *p) {
     p->gmg_max_coarse = 512;
     p->gmg_sweeps = 2;
     p->decoupling = 0;
+    p->coarsening = 0;
 }
 
 const char *rsv_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
@@ -226,6 +227,7 @@ rsv_status rsv_mat_set_values(rsv_mat *A, const double *vals, int on_device) {
     RSV_CUDA_TRY(cudaMemcpyAsync(A->d_v, vals, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                  A->stream));
     if (A->d_v32) RSV_CUDA_TRY(launch_cast_f64_f32(A->stream, 9 * A->nnzb, A->d_v, A->d_v32));
+    RSV_CUDA_TRY(spmv_autotune(A));  // first values only: time the SpMV tile candidates on this pattern
     if (!on_device) RSV_CUDA_TRY(cudaStreamSynchronize(A->stream));
     A->version++;
     return RSV_OK;

@@ -531,39 +531,6 @@ rsv_status batch_init(rsv_solver *s, BatchState **out) {
     return RSV_OK;
 }
 
-// Pick the SpMV tile (block rows per CTA) by timing each candidate.
-rsv_status autotune_spmv(rsv_solver *s) {
-    rsv_mat *A = s->A;
-    const int cands[3] = {32, 64, 128};
-    double *x = nullptr, *y = nullptr;
-    RSV_CUDA_TRY(cudaMallocAsync((void **)&x, sizeof(double) * 3 * A->nb, s->st));
-    cudaError_t e = cudaMallocAsync((void **)&y, sizeof(double) * 3 * A->nb, s->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * 3 * A->nb, s->st);
-    float best = 1e30f;
-    int pick = A->spmv_rows;
-    for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
-        A->spmv_rows = cands[q];
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_spmv_f64(A, 1.0, x, 0.0, y, nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(s->e0, s->st);
-        for (int w = 0; w < 5 && e == cudaSuccess; ++w)
-            e = s->mixed ? launch_spmv_f32(A, 1.0f, (const float *)x, 0.0f, (float *)y, nullptr)
-                         : launch_spmv_f64(A, 1.0, x, 0.0, y, nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(s->e1, s->st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(s->e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->e0, s->e1);
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            pick = cands[q];
-        }
-    }
-    A->spmv_rows = pick;
-    cudaFreeAsync(x, s->st);
-    cudaFreeAsync(y, s->st);
-    if (e != cudaSuccess) return cuda_status(e);
-    return RSV_OK;
-}
-
 }  // namespace
 
 void free_batch(rsv_solver *s) {
@@ -604,7 +571,7 @@ extern "C" rsv_status rsv_solve_batched_ptr(rsv_solver *s, const double *b, doub
     if (!B->own) RSV_CUDA_TRY(cudaStreamCreateWithFlags(&B->own, cudaStreamNonBlocking));
     StreamSwap swap(s, B->own);
     if (!B->tuned) {
-        RSV_TRY(autotune_spmv(s));
+        RSV_CUDA_TRY(spmv_autotune(A));
         B->tuned = true;
     }
     const BatchDev d = B->dv;

@@ -95,6 +95,7 @@ struct Cpr {  // CPR pressure stage: quasi-IMPES weights and the GMG hierarchy (
     int *piv = nullptr;
     void *r = nullptr, *z = nullptr, *xp = nullptr;  // full-stage residual and ILU correction (T)
     void *apc = nullptr;          // pressure column of every block [nnzb][3] (T): CPR-PF's stage-two residual
+    void *amg = nullptr;          // algebraic hierarchy (amg.cu) when the pressure stage coarsens algebraically
 };
 
 struct Schedule {  // i+j+k wavefront hyperplanes
@@ -123,7 +124,9 @@ struct rsv_mat {
     std::vector<rsv::SysGrid> h_sys;
     rsv::SysGrid *d_sys = nullptr;  // per grid
     int32_t *d_sys_of_cell = nullptr;  // grid of each cell
-    int spmv_rows = 128;            // block rows per CTA of the SpMV (autotuned for batches)
+    int spmv_rows64 = 128;          // block rows per CTA of the FP64 SpMV (timed once per matrix)
+    int spmv_rows32 = 128;          // the same for the FP32 copy
+    bool spmv_tuned = false;
     int64_t nb, nnzb;
     cudaStream_t stream;
     std::vector<int32_t> h_rp, h_ci;
@@ -154,6 +157,9 @@ cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, dou
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
                             const int *done, int *status = nullptr, unsigned long long timeout_ns = 2000000000ull);
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b);
+// Time the SpMV's block-rows-per-CTA candidates (32, 64, 128) on A's pattern and keep the
+// fastest per precision; once per matrix (later calls return at once).
+cudaError_t spmv_autotune(rsv_mat *A);
 // r = f - A (p_c, 0, 0)_c from the blocks' pressure columns apc [nnzb][3] (T = double or float).
 template <typename T>
 cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p, const T *f, T *r, const int *done,
@@ -209,9 +215,16 @@ cudaError_t launch_bj_apply(cudaStream_t st, int64_t nb, const T *dinv, const T 
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status);
 
 // ---- implemented in cpr.cu
-// decoupling: 0 quasi-IMPES, 1 ABF, 2 true-IMPES from the accumulation blocks acc [nb][9] (rsv_pc_params)
+// decoupling: 0 quasi-IMPES, 1 ABF, 2 true-IMPES from the accumulation blocks acc [nb][9] (rsv_pc_params).
+// coarsening: 0 geometric hierarchy, 1 algebraic (amg_setup runs afterwards, from P->a7[0]).
 cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling,
-                      const double *acc, Cpr *P, int *status);
+                      const double *acc, int coarsening, Cpr *P, int *status);
+// ---- implemented in amg.cu
+rsv_status amg_setup(const rsv_mat *A, Cpr *P, int max_levels, int max_coarse, int sweeps);
+void amg_free(Cpr *P);
+rsv_status amg_info(const Cpr &P, int *nlev, int64_t *sizes);
+template <typename T>
+cudaError_t amg_vcycle(const Cpr &P, cudaStream_t st, const int *done);
 void free_cpr(Cpr *P);
 template <typename T>
 cudaError_t cpr_apply(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,

@@ -422,6 +422,7 @@ unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, 
 }  // namespace
 
 void free_cpr(Cpr *P) {
+    amg_free(P);
     for (int l = 0; l < kMaxLevels; ++l)
         for (void *p : {(void *)P->a7[l], P->a7f[l], P->a7s[l], P->x[l], P->b[l]})
             if (p) cudaFree(p);
@@ -432,9 +433,11 @@ void free_cpr(Cpr *P) {
 }
 
 cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coarse, int sweeps, int decoupling,
-                      const double *acc, Cpr *P, int *status) {
+                      const double *acc, int coarsening, Cpr *P, int *status) {
     cudaStream_t st = A->stream;
     const size_t es = mixed ? sizeof(float) : sizeof(double);
+    amg_free(P);
+    if (coarsening == 1) max_levels = 1;  // the geometric part keeps only the finest level
     // level sizes: halve (ceil) each dimension while the level has more than max_coarse cells
     int dims[kMaxLevels][3];
     G3 g{A->nx, A->ny, A->nz};
@@ -474,10 +477,11 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
         alloc(&P->x[l], es * n);
         alloc(&P->b[l], es * n);
     }
-    alloc((void **)&P->dense, sizeof(double) * nc * nc);
-    alloc((void **)&P->minv, sizeof(double) * nc * nc);
-    alloc((void **)&P->work, sizeof(double) * nc * nc);
-    alloc((void **)&P->piv, sizeof(int) * nc);
+    const int64_t ncd = coarsening == 1 ? 1 : nc;  // the algebraic hierarchy keeps its own coarsest inverse
+    alloc((void **)&P->dense, sizeof(double) * ncd * ncd);
+    alloc((void **)&P->minv, sizeof(double) * ncd * ncd);
+    alloc((void **)&P->work, sizeof(double) * ncd * ncd);
+    alloc((void **)&P->piv, sizeof(int) * ncd);
     alloc(&P->r, es * 3 * nb);
     alloc(&P->z, es * 3 * nb);
     alloc(&P->xp, es * 3 * nb);
@@ -496,11 +500,13 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
         count_launches(1);
         gmg_coarsen_kernel<<<blocks(c.n()), 256, 0, st>>>(f, P->a7[l], c, P->a7[l + 1]);
     }
-    G3 gc{P->dims[nl - 1][0], P->dims[nl - 1][1], P->dims[nl - 1][2]};
-    count_launches(3);
-    coarse_dense_kernel<<<blocks(nc), 256, 0, st>>>(gc, P->a7[nl - 1], P->dense);
-    coarse_lu_kernel<<<1, 1024, 0, st>>>(nc, P->dense, P->piv, status);
-    coarse_inverse_kernel<<<nc, 128, 0, st>>>(nc, P->dense, P->piv, P->minv, P->work);
+    if (coarsening != 1) {
+        G3 gc{P->dims[nl - 1][0], P->dims[nl - 1][1], P->dims[nl - 1][2]};
+        count_launches(3);
+        coarse_dense_kernel<<<blocks(nc), 256, 0, st>>>(gc, P->a7[nl - 1], P->dense);
+        coarse_lu_kernel<<<1, 1024, 0, st>>>(nc, P->dense, P->piv, status);
+        coarse_inverse_kernel<<<nc, 128, 0, st>>>(nc, P->dense, P->piv, P->minv, P->work);
+    }
     const unsigned pcb = (unsigned)std::min<int64_t>(blocks(A->nnzb), 152 * 32);
     count_launches(1);
     if (mixed)
@@ -532,6 +538,7 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
 // One V-cycle on level l from a zero initial guess: x[l] = V(b[l]).
 template <typename T>
 static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done) {
+    if (l == 0 && P.amg) return amg_vcycle<T>(P, st, done);
     const T *a7 = P.mixed ? (const T *)P.a7f[l] : (const T *)P.a7[l];
     const T *a7s = (const T *)P.a7s[l];  // colour-split copy for the smoother
     T *x = (T *)P.x[l], *b = (T *)P.b[l];
@@ -601,6 +608,8 @@ cudaError_t cpr_finish(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, co
     if (e != cudaSuccess) return e;
     e = launch_ilu_apply_tiles<T>(A, tiles, r, x, done, status, timeout_ns);
     if (e != cudaSuccess) return e;
+    // x_c[0] += p_c.  (Adding it in the backward sweep's store puts a scattered load of p on every
+    // step of the sweep's dependency chain: 0.34 ms slower per apply on 256x256x128.)
     count_launches(1);
     prolong_add_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, p, x, done);
     return cudaGetLastError();

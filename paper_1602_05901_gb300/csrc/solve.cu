@@ -584,7 +584,7 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     if (params) pcp = *params;
     if (pcp.gmg_max_levels < 1 || pcp.gmg_max_levels > kMaxLevels || pcp.gmg_max_coarse < 1 ||
         pcp.gmg_max_coarse > 1024 || pcp.gmg_sweeps < 0 || pcp.gmg_sweeps > 16 || pcp.decoupling < 0 ||
-        pcp.decoupling > 2)
+        pcp.decoupling > 2 || pcp.coarsening < 0 || pcp.coarsening > 1)
         return RSV_EINVAL;
     if (cpr && pcp.decoupling == 2 && !s->acc) return RSV_EINVAL;  // true-IMPES needs the accumulation blocks
     rsv_mat *A = s->A;
@@ -609,7 +609,13 @@ rsv_status rsv_precond_setup(rsv_solver *s, int pc_type, const rsv_pc_params *pa
     if (cpr && A->nsys > 1) return RSV_ENOTSUP;
     if (cpr)
         RSV_CUDA_TRY(cpr_setup(A, s->mixed, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps, pcp.decoupling,
-                               s->acc, &s->cpr, &s->ds->status));
+                               s->acc, pcp.coarsening, &s->cpr, &s->ds->status));
+    if (cpr && pcp.coarsening == 1) {
+        int status0 = 0;
+        RSV_TRY(read_status(s, &status0));  // the decoupling's pivots first
+        if (status0 != RSV_OK) return (rsv_status)status0;
+        RSV_TRY(amg_setup(A, &s->cpr, pcp.gmg_max_levels, pcp.gmg_max_coarse, pcp.gmg_sweeps));
+    }
     RSV_CUDA_TRY(cudaEventRecord(s->e1, s->st));
     int status = 0;
     RSV_TRY(read_status(s, &status));
@@ -686,6 +692,11 @@ rsv_status rsv_cpr_info(rsv_solver *s, int *nlev, int *dims, double *w_host, dou
     }
     RSV_CUDA_TRY(cudaStreamSynchronize(s->st));
     return RSV_OK;
+}
+
+rsv_status rsv_amg_info(rsv_solver *s, int *nlev, int64_t *sizes) {
+    if (!s || !is_cpr_type(s->pc_type) || !s->cpr.amg) return RSV_EINVAL;
+    return amg_info(s->cpr, nlev, sizes);
 }
 
 rsv_status rsv_cpr_vcycle(rsv_solver *s, const double *b, double *x) {

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
     for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t] - p0;
     __syncthreads();
     {
-        unsigned ok = 0, spins = 0;
+        unsigned ok = 0;
         const uint64_t deadline = global_timer() + timeout_ns;
         bool late = false;
         for (;;) {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
                 : "memory");
             if (ok) break;
             // the copy is plain memory traffic; the limit only guards against a stuck wait
-            if ((++spins & 7u) == 0 && global_timer() > deadline) {
+            if (global_timer() > deadline) {
                 late = true;
                 break;
             }
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(3 * R) pcol_residual_tma(int nb, const int32_t
     const T fr = t < nr * 3 ? f[row] : T(0);  // issued before the wait
     __syncthreads();
     {
-        unsigned ok = 0, spins = 0;
+        unsigned ok = 0;
         const uint64_t deadline = global_timer() + timeout_ns;
         bool late = false;
         for (;;) {
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(3 * R) pcol_residual_tma(int nb, const int32_t
                 : "r"(smem_u32(bar))
                 : "memory");
             if (ok) break;
-            if ((++spins & 7u) == 0 && global_timer() > deadline) {
+            if (global_timer() > deadline) {
                 late = true;
                 break;
             }
@@ -230,12 +230,12 @@ cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T bet
     return cudaGetLastError();
 }
 
-// Block rows per CTA: 128 by default; batches pick 32, 64 or 128 by timing.
+// Block rows per CTA: 32, 64 or 128, picked per matrix and precision by timing (spmv_autotune).
 template <typename T>
 cudaError_t spmv_dispatch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done,
                           int *status, unsigned long long timeout_ns) {
     if (A->nb == 0) return cudaSuccess;
-    switch (A->spmv_rows) {
+    switch (sizeof(T) == 8 ? A->spmv_rows64 : A->spmv_rows32) {
     case 32: return spmv_launch<T, 32>(A, v, alpha, x, beta, y, done, status, timeout_ns);
     case 64: return spmv_launch<T, 64>(A, v, alpha, x, beta, y, done, status, timeout_ns);
     default: return spmv_launch<T, kRows>(A, v, alpha, x, beta, y, done, status, timeout_ns);
@@ -286,6 +286,50 @@ cudaError_t launch_spmv_f64(const rsv_mat *A, double alpha, const double *x, dou
 cudaError_t launch_spmv_f32(const rsv_mat *A, float alpha, const float *x, float beta, float *y,
                             const int *done, int *status, unsigned long long timeout_ns) {
     return spmv_dispatch<float>(A, A->d_v32, alpha, x, beta, y, done, status, timeout_ns);
+}
+
+cudaError_t spmv_autotune(rsv_mat *A) {
+    if (A->spmv_tuned || A->nb == 0) return cudaSuccess;
+    cudaStream_t st = A->stream;
+    const int cands[3] = {32, 64, 128};
+    double *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&x, sizeof(double) * 3 * A->nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&y, sizeof(double) * 3 * A->nb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(double) * 3 * A->nb, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int prec = 0; prec < 2 && e == cudaSuccess; ++prec) {
+        if (prec == 1 && !A->d_v32) break;
+        int &rows = prec == 0 ? A->spmv_rows64 : A->spmv_rows32;
+        float best = 1e30f;
+        int pick = rows;
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+            rows = cands[q];
+            auto run = [&]() {
+                return prec == 0 ? launch_spmv_f64(A, 1.0, x, 0.0, y, nullptr)
+                                 : launch_spmv_f32(A, 1.0f, (const float *)x, 0.0f, (float *)y, nullptr);
+            };
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int w = 0; w < 5 && e == cudaSuccess; ++w) e = run();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                pick = cands[q];
+            }
+        }
+        rows = pick;
+    }
+    if (x) cudaFreeAsync(x, st);
+    if (y) cudaFreeAsync(y, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess) A->spmv_tuned = true;
+    return e;
 }
 
 cudaError_t launch_cast_f64_f32(cudaStream_t st, int64_t n, const double *a, float *b) {

@@ -344,3 +344,100 @@ def test_true_impes_needs_accumulation_blocks(rsv, torch):
     with pytest.raises(rsv.RsvError) as e:
         s.setup("cpr", decoupling="timpes")
     assert e.value.status == rsv.RSV_EINVAL
+
+
+# ---- algebraic coarsening of the pressure stage (rsv_pc_params.coarsening = 1)
+
+AMG_DIMS = [(20, 20, 10), (13, 7, 5), (33, 17, 9), (40, 24, 16)]
+
+
+def _amg_setup(rsv, p, precision="fp64", pc="cpr", coarse=64):
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, precision=precision)
+    s.setup(pc, coarsening="amg", gmg_max_levels=8, gmg_max_coarse=coarse)
+    return A, s
+
+
+@pytest.mark.parametrize("dims", AMG_DIMS)
+def test_amg_hierarchy_and_vcycle_match_oracle(rsv, torch, dims):
+    """The same PMIS splitting level by level (points and nonzeros equal), and one
+    V-cycle per entry against the oracle's."""
+    p = synth.make_problem(*dims, seed=66)
+    A, s = _amg_setup(rsv, p)
+    _, _, a7 = oracle.System.from_problem(p, pc="cpr").factors()
+    ref = oracle.amg_hierarchy(*dims, a7, max_levels=8, max_coarse=64)
+    assert s.amg_info() == ref and len(ref) >= 2
+    b = np.random.default_rng(67).standard_normal(p.nb)
+    st, e_or, nl = oracle.amg_vcycle(*dims, a7, b, max_levels=8, max_coarse=64, sweeps=2)
+    assert st == 0 and nl == len(ref)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    s.vcycle(bd, xd)
+    torch.cuda.synchronize()
+    ratio = report_ratio(f"amg_vcycle_{dims}", per_entry_ratio(xd.cpu().numpy(), e_or), 1e-9)
+    assert ratio <= 1e-9
+
+
+@pytest.mark.parametrize("dims", [(20, 20, 10), (40, 24, 16)])
+def test_cpr_amg_apply_matches_oracle(rsv, torch, dims):
+    p = synth.make_problem(*dims, seed=68)
+    A, s = _amg_setup(rsv, p)
+    o = oracle.System.from_problem(p, pc="cpr", coarsening="amg", gmg_levels=8, gmg_coarse=64)
+    assert o.setup_status == 0
+    f = np.random.default_rng(69).standard_normal(p.n)
+    st, z_or = o.pc_apply(f)
+    fd = torch.from_numpy(f).cuda()
+    zd = torch.zeros_like(fd)
+    s.apply(fd, zd)
+    torch.cuda.synchronize()
+    ratio = report_ratio(f"cpr_amg_apply_{dims}", per_entry_ratio(zd.cpu().numpy(), z_or), 1e-9)
+    assert ratio <= 1e-9
+    # FP32: the GPU applies the FP32-rounded hierarchy in FP32, the oracle the same rounded values in FP64
+    A32, s32 = _amg_setup(rsv, p, precision="mixed")
+    of = oracle.System.from_problem(p, pc="cpr", coarsening="amg", gmg_levels=8, gmg_coarse=64, float_round=True)
+    f32 = f.astype(np.float32)
+    _, z32_or = of.pc_apply(f32.astype(np.float64))
+    f32d = torch.from_numpy(f32).cuda()
+    z32d = torch.zeros_like(f32d)
+    s32.apply(f32d, z32d)
+    torch.cuda.synchronize()
+    ratio = report_ratio(f"cpr_amg_apply_fp32_{dims}", per_entry_ratio(z32d.cpu().numpy(), z32_or), 1e-3)
+    assert ratio <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cpr_amg_gmres_solve(rsv, torch, precision):
+    p = synth.make_problem(20, 20, 10, seed=0)
+    A = rsv.Matrix(p.nx, p.ny, p.nz)
+    A.set_values(p.vals)
+    s = rsv.Solver(A, solver="gmres", precision=precision, maxit=4000)
+    s.setup("cpr", coarsening="amg", gmg_max_levels=8, gmg_max_coarse=64)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    st, info = s.solve(b, x)
+    assert st == rsv.RSV_OK, (st, info)
+    relres = np.linalg.norm(p.b - oracle.spmv(p.row_ptr, p.col_idx, p.vals, x.cpu().numpy())) / np.linalg.norm(p.b)
+    assert relres <= 1e-8
+    if precision == "fp64":
+        o = oracle.System.from_problem(p, pc="cpr", coarsening="amg", gmg_levels=8, gmg_coarse=64)
+        ost, _, oinfo = o.gmres(p.b, maxit=4000)
+        assert ost == 0 and abs(info["iters"] - oinfo["iters"]) <= max(2, 0.1 * oinfo["iters"]), (info, oinfo)
+
+
+def test_amg_hierarchy_matches_oracle_at_100x100x50(rsv, torch):
+    """500,000 pressure points: six algebraic levels, equal to the oracle's, and the
+    V-cycle per entry."""
+    p = synth.workload("mid_100x100x50")
+    A, s = _amg_setup(rsv, p, coarse=512)
+    _, _, a7 = oracle.System.from_problem(p, pc="cpr").factors()
+    ref = oracle.amg_hierarchy(p.nx, p.ny, p.nz, a7, max_levels=8, max_coarse=512)
+    assert s.amg_info() == ref, (s.amg_info(), ref)
+    b = np.random.default_rng(70).standard_normal(p.nb)
+    st, e_or, _ = oracle.amg_vcycle(p.nx, p.ny, p.nz, a7, b, max_levels=8, max_coarse=512, sweeps=2)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    s.vcycle(bd, xd)
+    torch.cuda.synchronize()
+    ratio = report_ratio("amg_vcycle_mid", per_entry_ratio(xd.cpu().numpy(), e_or), 1e-9)
+    assert ratio <= 1e-9
