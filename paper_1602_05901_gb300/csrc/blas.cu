@@ -403,6 +403,72 @@ __global__ void __launch_bounds__(kRedThreads, 1) maxpy_mdot_kernel(int64_t n, T
     }
 }
 
+// The update pass of a delayed CGS2 step (GMRES): from one read of V_0..V_{k-1}, u and w,
+//   u <- cS[0] u - sum_i cB[i] V_i                    (the reorthogonalised, normalised v_k)
+//   w <- cS[0] w - cS[1] u_old - sum_i cA[i] V_i      (the next step's once-orthogonalised vector)
+// Both outputs are written over their inputs by the thread that read them.
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kRedThreads) dcgs2_update_kernel(int64_t n, T *u, T *w, const T *__restrict__ V,
+                                                                   int64_t ldv, int k, const double *cA,
+                                                                   const double *cB, const double *cS,
+                                                                   const int *done) {
+    if (is_done(done)) return;
+    using VT = Vec<T>;
+    __shared__ T sa[kMaxRestart], sb[kMaxRestart];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        sa[i] = (T)(-cA[i]);
+        sb[i] = (T)(-cB[i]);
+    }
+    __syncthreads();
+    const T cw = (T)cS[0], cu = (T)(-cS[1]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tail = 0;
+    if (VEC) {
+        const int64_t nv = n / VT::N;
+        for (int64_t r = tid; r < nv; r += stride) {
+            const typename VT::V ur = reinterpret_cast<const typename VT::V *>(u)[r];
+            const typename VT::V wr = reinterpret_cast<const typename VT::V *>(w)[r];
+            typename VT::V av, aw;
+#pragma unroll
+            for (int q = 0; q < VT::N; ++q) {
+                VT::set(av, q, VT::get(ur, q) * cw);
+                VT::set(aw, q, fma(cu, VT::get(ur, q), VT::get(wr, q) * cw));
+            }
+            constexpr int B = 8;  // loads issued together
+            for (int i0 = 0; i0 < k; i0 += B) {
+                typename VT::V vr[B];
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (i0 + i < k) vr[i] = reinterpret_cast<const typename VT::V *>(V + (int64_t)(i0 + i) * ldv)[r];
+#pragma unroll
+                for (int i = 0; i < B; ++i)
+                    if (i0 + i < k) {
+#pragma unroll
+                        for (int q = 0; q < VT::N; ++q) {
+                            VT::set(av, q, fma(sb[i0 + i], VT::get(vr[i], q), VT::get(av, q)));
+                            VT::set(aw, q, fma(sa[i0 + i], VT::get(vr[i], q), VT::get(aw, q)));
+                        }
+                    }
+            }
+            reinterpret_cast<typename VT::V *>(u)[r] = av;
+            reinterpret_cast<typename VT::V *>(w)[r] = aw;
+        }
+        tail = nv * VT::N;
+    }
+    for (int64_t r = tail + tid; r < n; r += stride) {
+        const T ur = u[r];
+        T av = ur * cw, aw = fma(cu, ur, w[r] * cw);
+        for (int i = 0; i < k; ++i) {
+            const T v = V[(int64_t)i * ldv + r];
+            av = fma(sb[i], v, av);
+            aw = fma(sa[i], v, aw);
+        }
+        u[r] = av;
+        w[r] = aw;
+    }
+}
+
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(kRedThreads) dot_kernel(int64_t n, const T *__restrict__ x,
                                                           const T *__restrict__ y, double *partial, double *out,
@@ -557,6 +623,18 @@ cudaError_t launch_maxpy_mdot(cudaStream_t st, int64_t n, T *w, const T *V, int6
 }
 
 template <typename T>
+cudaError_t launch_dcgs2_update(cudaStream_t st, int64_t n, T *u, T *w, const T *V, int64_t ldv, int k,
+                                const double *cA, const double *cB, const double *cS, const int *done) {
+    if (k < 0 || k > kMaxRestart) return cudaErrorInvalidValue;
+    rsv::count_launches(1);
+    if (vec_ok<T>(ldv, {u, w, V}))
+        dcgs2_update_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, u, w, V, ldv, k, cA, cB, cS, done);
+    else
+        dcgs2_update_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, u, w, V, ldv, k, cA, cB, cS, done);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_dot(cudaStream_t st, int64_t n, const T *x, const T *y, double *partial, double *out,
                        unsigned *counter, int sqrt_out, const int *done) {
     rsv::count_launches(1);
@@ -609,6 +687,8 @@ cudaError_t launch_add_f32_scaled(cudaStream_t st, int64_t n, const float *df, c
                                          double, T *, double *, double *, unsigned *, const int *, const int *);    \
     template cudaError_t launch_maxpy_mdot<T>(cudaStream_t, int64_t, T *, const T *, int64_t, int, const double *,  \
                                               double *, double *, double *, unsigned *, const int *);              \
+    template cudaError_t launch_dcgs2_update<T>(cudaStream_t, int64_t, T *, T *, const T *, int64_t, int,           \
+                                                const double *, const double *, const double *, const int *);      \
     template cudaError_t launch_dot<T>(cudaStream_t, int64_t, const T *, const T *, double *, double *, unsigned *, \
                                        int, const int *);                                                           \
     template cudaError_t launch_axpby<T>(cudaStream_t, int64_t, T, const T *, T, const T *, T *);                  \

@@ -45,6 +45,11 @@ struct DevState {
     double red[kMaxRestart + 1];                       // generic reduction outputs
     double G[(kMaxRestart + 1) * (kMaxRestart + 1)];   // Gram matrix of the current Arnoldi basis, row-major
     double gcol[kMaxRestart + 1];                      // <v_j, v_i>, i <= j: column j of G
+    // delayed CGS2 (FP32 GMRES): projections of the step's two vectors, the unrotated
+    // Hessenberg matrix and the update pass's coefficients
+    double ow[kMaxRestart + 1], ou[kMaxRestart + 1];
+    double Hu[(kMaxRestart + 1) * kMaxRestart];  // row-major (m+1) x m
+    double cA[kMaxRestart], cB[kMaxRestart], cS[2];
     double beta, hn, wnorm, tol;
     double rho, rho1, alpha, omega;
     double bnorm;
@@ -183,6 +188,12 @@ template <typename T>
 cudaError_t launch_maxpy(cudaStream_t st, int64_t n, const T *base, const T *V, int64_t ldv, int k, const double *c,
                          double sgn, T *out, double *partial, double *nrm, unsigned *counter, const int *done,
                          const int *skip = nullptr);
+// The update pass of a delayed CGS2 Arnoldi step, both outputs in place and elementwise:
+// u = cS[0] u - sum_{i<k} cB[i] V_i and w = cS[0] w - cS[1] u_old - sum_{i<k} cA[i] V_i,
+// with u and w outside V_0..V_{k-1}.  One read of the k basis vectors, u and w.
+template <typename T>
+cudaError_t launch_dcgs2_update(cudaStream_t st, int64_t n, T *u, T *w, const T *V, int64_t ldv, int k,
+                                const double *cA, const double *cB, const double *cS, const int *done);
 // Classical Gram-Schmidt, the first pass's update fused with the second pass's projections:
 // w -= sum_i c[i] V_i (in place, in the vector precision), then proj[i] = <w, V_i> for i < k
 // and *nrm = ||w||_2.  Each basis value is read once.  Returns cudaErrorInvalidValue (nothing

@@ -11,10 +11,13 @@
 // Arnoldi orthogonalisation is classical Gram-Schmidt with one reorthogonalisation
 // ("all projections, then one multi-vector update", twice).  FP64 bases take the
 // second pass's projections from the Gram matrix of the basis (see
-// gmres_gram_step), so a step reads the basis twice; FP32 bases run the second
-// pass explicitly when the first one cancelled more than 1 - 1/sqrt(2) of the
-// norm.  The Hessenberg columns, Givens rotations and the residual estimate are
-// FP64 scalars kept in device memory.
+// gmres_gram_step), so a step reads the basis twice.  FP32 bases (GMRES) delay
+// the second pass by one step and take it in the same read of the basis as the
+// next step's projections (gmres_dcgs2_step), which keeps the second pass acting
+// on the stored FP32 vector: two reads of the basis per step.  FP32 FGMRES runs
+// the second pass explicitly when the first one cancelled more than 1 - 1/sqrt(2)
+// of the norm.  The Hessenberg columns, Givens rotations and the residual estimate
+// are FP64 scalars kept in device memory.
 //
 // Mixed precision (precision = RSV_PREC_MIXED): an FP64 iterative-refinement
 // loop r = b - A x (FP64 SpMV, FP64 norm), inner solve A d = r / ||r|| with
@@ -44,22 +47,13 @@ __device__ __forceinline__ void raise_status(DevState *ds, int code) {
     ds->done = 1;
 }
 
-// Column j of the Hessenberg matrix from the two Gram-Schmidt passes, the
-// previous Givens rotations, a new rotation and the residual estimate |g_{j+1}|.
-// The block stages the column and the rotations in shared memory, so the serial
-// chain of rotations (thread 0) runs at shared-memory latency.
-__global__ void gmres_givens(DevState *ds, int j, int m) {
-    if (ds->done) return;
-    __shared__ double col[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart];
+// Givens step on column j of the Hessenberg matrix, staged in shared memory as col[0..j+1]
+// with the previous rotations in cs/sn: the previous rotations, a new rotation, the
+// residual estimate |g_{j+1}| and the stopping test.  Thread 0 runs the serial chain at
+// shared-memory latency; then the block stores the rotated column.  Called by the whole block.
+__device__ void rotate_column(DevState *ds, double *col, const double *cs, const double *sn, int j, int m) {
     double *H = ds->H;
     const int t = threadIdx.x;
-    for (int i = t; i <= j; i += blockDim.x) col[i] = ds->h1[i] + ds->h2[i];
-    for (int i = t; i < j; i += blockDim.x) {
-        cs[i] = ds->cs[i];
-        sn[i] = ds->sn[i];
-    }
-    if (t == 0) col[j + 1] = ds->hn;
-    __syncthreads();
     if (t == 0) {
         for (int i = 0; i < j; ++i) {
             const double a = col[i], b = col[i + 1];
@@ -68,7 +62,8 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
         }
         const double a = col[j], b = col[j + 1];
         const double rho = hypot(a, b);
-        if (!isfinite(rho) || !isfinite(ds->hn)) {
+        // b = col[j+1], the subdiagonal entry (a norm, >= 0): no earlier rotation touches it
+        if (!isfinite(rho) || !isfinite(b)) {
             raise_status(ds, RSV_ENAN);
         } else if (!(rho > 0.0)) {
             raise_status(ds, RSV_EBREAKDOWN);
@@ -81,13 +76,114 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
             ds->g[j] = ds->cs[j] * ds->g[j];
             ds->jend = j + 1;
             ds->iters += 1;
-            const bool lucky = !(ds->hn > 0.0);
+            const bool lucky = !(b > 0.0);
             const bool met = fabs(ds->g[j + 1]) <= ds->tol;
             if (met || lucky) ds->conv = 1;
             if (met || ds->iters >= ds->maxit || lucky || j + 1 == m) ds->done = 1;
         }
     }
+    __syncthreads();
     for (int i = t; i < j; i += blockDim.x) H[i * m + j] = col[i];
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes (h1 + h2, and
+// ||w|| after them as the subdiagonal entry), then its Givens step.
+__global__ void gmres_givens(DevState *ds, int j, int m) {
+    if (ds->done) return;
+    __shared__ double col[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart];
+    const int t = threadIdx.x;
+    for (int i = t; i <= j; i += blockDim.x) col[i] = ds->h1[i] + ds->h2[i];
+    for (int i = t; i < j; i += blockDim.x) {
+        cs[i] = ds->cs[i];
+        sn[i] = ds->sn[i];
+    }
+    if (t == 0) col[j + 1] = ds->hn;
+    __syncthreads();
+    rotate_column(ds, col, cs, sn, j, m);
+}
+
+// One step of GMRES's Arnoldi process by classical Gram-Schmidt with delayed
+// reorthogonalisation (the FP32 basis of the inner solves).  Step j holds the final
+// v_0..v_{j-1}, u_j (the once-orthogonalised, unnormalised vector of step j-1; u_0 = r)
+// and w = A M^{-1} u_j, and the multi-dot gave ou = V_{0..j}^T u_j and ow = V_{0..j}^T w
+// (V_j = u_j).  With s = ou[0..j-1] and rho^2 = <u_j,u_j> - s.s:
+//   v_j = (u_j - V s) / rho, so Hessenberg column j-1 becomes [h1 + s; rho]: its
+//   Givens step and stopping test run here (one step late; a step that finds its
+//   predecessor converged leaves its own product unused);
+//   A M^{-1} V_{0..j-1} = V_{0..j} Hbar (the Arnoldi relation) gives
+//   A M^{-1} v_j = (w - V_{0..j} Hbar s) / rho, whose projections on V_{0..j} are
+//   y = ([t; (c - s.t)/rho] - Hbar s) / rho (t = ow[0..j-1], c = ow[j]).  y is
+//   column j's first pass (h1), and the update pass forms v_j and
+//   u_{j+1} = A M^{-1} v_j - V_{0..j} y from the stored u_j and w with the
+//   coefficients cB, cS[0] (v_j) and cA, cS[1], cS[0] (u_{j+1}).
+// final: the cycle's last step finalises column j-1 only (no w).  Each step reads the
+// basis twice (multi-dot and update), against three times for two explicit passes.
+// One block of 128 threads.
+__global__ void gmres_dcgs2_step(DevState *ds, int j, int m, int final_only) {
+    if (ds->done) return;
+    constexpr int L = kMaxRestart + 1;
+    __shared__ double s[L], tv[L], col[L], cs[kMaxRestart], sn[kMaxRestart], hs[L], red[2];
+    __shared__ int stop;
+    const int t = threadIdx.x;
+    if (t < j) {
+        s[t] = ds->ou[t];
+        tv[t] = final_only ? 0.0 : ds->ow[t];
+    }
+    __syncthreads();
+    if (t == 0) {
+        double ss = 0.0, st = 0.0;
+        for (int q = 0; q < j; ++q) {
+            ss += s[q] * s[q];
+            st += s[q] * tv[q];
+        }
+        red[0] = ss;
+        red[1] = st;
+    }
+    __syncthreads();
+    const double rho2 = ds->ou[j] - red[0];
+    const double rho = rho2 > 0.0 ? sqrt(rho2) : (rho2 == rho2 ? 0.0 : rho2);  // NaN stays NaN
+    if (j == 0) {
+        if (t == 0) {
+            ds->g[0] = rho;  // u_0 = r: rho = ||r||
+            if (!isfinite(rho)) raise_status(ds, RSV_ENAN);
+            else if (!(rho > 0.0)) raise_status(ds, RSV_EBREAKDOWN);
+        }
+    } else {
+        if (t < j) col[t] = ds->h1[t] + s[t];
+        if (t < j - 1) {
+            cs[t] = ds->cs[t];
+            sn[t] = ds->sn[t];
+        }
+        if (t == 0) col[j] = rho;
+        __syncthreads();
+        if (t <= j) ds->Hu[t * m + (j - 1)] = col[t];
+        __syncthreads();
+        rotate_column(ds, col, cs, sn, j - 1, m);
+    }
+    __syncthreads();
+    if (t == 0) stop = ds->done;
+    __syncthreads();
+    if (final_only || stop) return;
+    const double ri = 1.0 / rho;
+    if (t <= j) {  // (Hbar s)_t over the finalised columns 0..j-1 (Hbar is upper Hessenberg)
+        double h = 0.0;
+        for (int c = t > 0 ? t - 1 : 0; c < j; ++c) h += ds->Hu[t * m + c] * s[c];
+        hs[t] = h;
+    }
+    __syncthreads();
+    const double yj = (ds->ow[j] - red[1]) * ri * ri - hs[j] * ri;
+    const double e = hs[j] * ri + yj;
+    if (t < j) {
+        const double yq = (tv[t] - hs[t]) * ri;
+        ds->h1[t] = yq;
+        ds->cA[t] = ri * hs[t] + yq - e * ri * s[t];
+        ds->cB[t] = s[t] * ri;
+    }
+    if (t == 0) {
+        ds->h1[j] = yj;
+        ds->cS[0] = ri;
+        ds->cS[1] = e * ri;
+    }
 }
 
 // Classical Gram-Schmidt with its second pass taken from the Gram matrix G = V^T V
@@ -293,6 +389,10 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
     const int64_t n = s->n, ldv = s->ldv;
     const int m = s->p.restart;
     const bool flex = s->p.solver == RSV_FGMRES;
+    // FP32 GMRES orthogonalises with delayed reorthogonalisation (gmres_dcgs2_step): the
+    // preconditioner runs on the not yet reorthogonalised u_j, which a flexible method
+    // would have to correct in Z as well, so FGMRES keeps the two explicit passes.
+    const bool delayed = !flex && sizeof(T) == 4;
     DevState *ds = s->ds;
     T *V = (T *)s->kw.V, *Z = (T *)s->kw.Z, *w = (T *)s->kw.w, *t = (T *)s->kw.t;
     HostState h{};
@@ -307,13 +407,23 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
         ++*cycles;
         rsv::count_launches(1);
         gmres_cycle_init<<<1, 1, 0, s->st>>>(ds);
-        RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, V, &ds->beta, nullptr));
+        if (!delayed) RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, V, &ds->beta, nullptr));  // else u_0 = r
         for (int j = 0; j < m; ++j) {
             T *vj = V + (size_t)j * ldv;
             T *wj = V + (size_t)(j + 1) * ldv;
             T *z = flex ? Z + (size_t)j * ldv : t;
             RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
+            if (delayed) {
+                // slot j holds u_j, slot j+1 w = A M^{-1} u_j: projections of both in one read
+                // of the basis, the step's scalars, then v_j and u_{j+1} in one more read
+                RSV_CUDA_TRY(launch_mdot2<T>(s->st, n, wj, vj, V, ldv, j + 1, s->partial, ds->ow, ds->ou,
+                                             &ds->counter[0], &ds->done));
+                rsv::count_launches(1);
+                gmres_dcgs2_step<<<1, 128, 0, s->st>>>(ds, j, m, 0);
+                RSV_CUDA_TRY(launch_dcgs2_update<T>(s->st, n, vj, wj, V, ldv, j, ds->cA, ds->cB, ds->cS, &ds->done));
+                continue;
+            }
             if (sizeof(T) == 8) {
                 // FP64: projections onto V and the Gram matrix's new column in one read of the
                 // basis, the second pass's projections from the Gram matrix, then one update
@@ -353,6 +463,13 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
             gmres_givens<<<1, kMaxRestart, 0, s->st>>>(ds, j, m);
             if (s->pc_type == RSV_PC_CPR_LEARNED) RSV_CUDA_TRY(learned_watch(s, j));
             RSV_CUDA_TRY(launch_scale_inv<T>(s->st, n, wj, &ds->hn, &ds->done));
+        }
+        if (delayed) {
+            // the cycle's last column waits for u_m's reorthogonalisation: <u_m, V_i> and <u_m, u_m>
+            RSV_CUDA_TRY(launch_mdot<T>(s->st, n, V + (size_t)m * ldv, V, ldv, m, s->partial, ds->ou,
+                                        &ds->counter[0], &ds->done, &ds->wnorm));
+            rsv::count_launches(1);
+            gmres_dcgs2_step<<<1, 128, 0, s->st>>>(ds, m, m, 1);
         }
         RSV_TRY(fetch(s, &h));
         if (h.status != RSV_OK && h.status != RSV_EBREAKDOWN) return (rsv_status)h.status;
