@@ -267,7 +267,8 @@ template <typename T>
 cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *T_);
 void free_tiles(IluTiles *T_);
 template <typename T>
+// add0 (optional): z_c[0] += add0[c] on output (carried through the sweeps in the vector's pad slot).
 cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &T_, const T *r, T *z, const int *done,
-                                   int *status, unsigned long long timeout_ns);
+                                   int *status, unsigned long long timeout_ns, const T *add0 = nullptr);
 
 }  // namespace rsv

@@ -485,7 +485,7 @@ cudaError_t cpr_setup(const rsv_mat *A, bool mixed, int max_levels, int max_coar
     alloc(&P->r, es * 3 * nb);
     alloc(&P->z, es * 3 * nb);
     alloc(&P->xp, es * 3 * nb);
-    alloc(&P->apc, es * 3 * (size_t)A->nnzb);
+    alloc(&P->apc, es * 3 * (size_t)A->nnzb + 64);  // tail room: the residual kernels stage whole 16-byte units
     if (e != cudaSuccess) return e;
     G3 g0{A->nx, A->ny, A->nz};
     count_launches(1);
@@ -595,24 +595,18 @@ cudaError_t cpr_pressure_vcycle(const rsv_mat *A, const Cpr &P, const int *gate)
 }
 
 // Stage one's prolongation x = Pi_p P.x[0], then stage two: x += ILU0^{-1}(f - A x).  Fused:
-// r = f - A Pi_p p from the pressure columns alone, x = ILU0^{-1} r, then x += Pi_p p (the same
+// r = f - A Pi_p p from the pressure columns alone, then x = ILU0^{-1} r + Pi_p p (the same
 // sums, in the same order, as forming x = Pi_p p, r = f - A x and x += ILU0^{-1} r).
 template <typename T>
 cudaError_t cpr_finish(const rsv_mat *A, const Cpr &P, const IluTiles &tiles, const T *f, T *x, const int *done,
                        int *status, unsigned long long timeout_ns) {
-    cudaStream_t st = A->stream;
-    const int64_t nb = A->nb;
     T *r = (T *)P.r;
     const T *p = (const T *)P.x[0];
     cudaError_t e = launch_pressure_residual<T>(A, (const T *)P.apc, p, f, r, done, status, timeout_ns);
     if (e != cudaSuccess) return e;
-    e = launch_ilu_apply_tiles<T>(A, tiles, r, x, done, status, timeout_ns);
-    if (e != cudaSuccess) return e;
-    // x_c[0] += p_c.  (Adding it in the backward sweep's store puts a scattered load of p on every
-    // step of the sweep's dependency chain: 0.34 ms slower per apply on 256x256x128.)
-    count_launches(1);
-    prolong_add_pressure_kernel<T><<<blocks(nb), 256, 0, st>>>(nb, p, x, done);
-    return cudaGetLastError();
+    // x = ILU0^{-1} r, and x_c[0] += p_c as the backward sweep stores x: p_c rides in the pad slot
+    // of the sweeps' tile-order vectors, so no step of the sweeps waits on a load of p
+    return launch_ilu_apply_tiles<T>(A, tiles, r, x, done, status, timeout_ns, p);
 }
 
 template <typename T>

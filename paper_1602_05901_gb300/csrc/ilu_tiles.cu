@@ -54,16 +54,18 @@ constexpr int TJ = 8, TK = 4;
 // look-ahead is a step of lag per tile hand-off on the sweep's critical path, so
 // the copies run one step ahead (measured on 100x100x50, FP32 apply: 379 us with
 // one step, 406 us with two, 462 us with three; per-lane relaxed register loads
-// instead of TMA: 595 us).  With four stages, the stage a step refills was last
-// read three steps earlier, long after its values were consumed, so the refill
-// needs no proxy fence (a fence there waits for the warp's outstanding stores:
-// 398 us with it).
-constexpr int NSE = 4, ELA = 1;
-// Steps per data group.  A tile's step count is padded to a multiple of GS (the
-// padded steps hold no valid cell), so every group is full and, GS being a
-// multiple of NSE, every edge stage is a constant of the unrolled step.
-constexpr int GS = 4;
-static_assert(GS % NSE == 0 && ELA >= 1 && ELA < NSE, "edge stages are fixed per unrolled step");
+// instead of TMA: 595 us).  The stage a step refills (NSE stages: 4 for FP32, 3 for
+// FP64) was last read NSE - 1 steps earlier, and its values fed that step's
+// results, so those reads are complete and the refill needs no proxy fence (a
+// fence there waits for the warp's outstanding stores: 5% slower with it).
+constexpr int ELA = 1;
+// Steps per data group, GS (Bits<T>).  A tile's step count is padded to a multiple
+// of GS (the padded steps hold no valid cell), so every group is full and, GS
+// being a multiple of NSE, every edge stage is a constant of the unrolled step.
+// FP64 takes three steps per group: 64.5 KB per tile, 3 tiles per SM instead of 2
+// (FP64 CPR solve on 256x256x128: 8.71 s against 9.58 s).  FP32 keeps four: three
+// would fit 7 tiles per SM instead of 5, but the apply on 256x256x128 then took
+// 1.081 ms against 1.061 ms (the wavefront, not residency, bounds it).
 
 template <typename T> struct Bits;
 template <> struct Bits<double> {
@@ -71,12 +73,14 @@ template <> struct Bits<double> {
     static constexpr U SENT = 0xFFF4C0DE5A17E7A1ull;  // signalling NaN
     static constexpr int NQP = 38;                    // padded factor row: conflict-free 16-byte reads
     static constexpr int NG = 2;                      // data ring groups (copies one group ahead)
+    static constexpr int GS = 3, NSE = 3;             // steps per data group, edge stages
 };
 template <> struct Bits<float> {
     using U = unsigned int;
     static constexpr U SENT = 0x7FA5C0DEu;
     static constexpr int NQP = 36;
     static constexpr int NG = 2;
+    static constexpr int GS = 4, NSE = 4;
 };
 
 // Data stage of one step: factor [32][NQP] and vector [32][4]; a data group holds
@@ -87,14 +91,16 @@ template <typename T> struct Stage {
     static constexpr int V = 32 * 4;
     static constexpr int EJ = TK * 4;
     static constexpr int EK = TJ * 4;
+    static constexpr int GS = Bits<T>::GS, NSE = Bits<T>::NSE;
+    static_assert(GS % NSE == 0 && ELA >= 1 && ELA < NSE, "edge stages are fixed per unrolled step");
     static constexpr int GSIZE = GS * (F + V);
     static constexpr int ESIZE = EJ + EK;
     static constexpr unsigned FB = F * sizeof(T), VB = V * sizeof(T), EJB = EJ * sizeof(T), EKB = EK * sizeof(T);
 };
 
 template <typename T> constexpr size_t sweep_smem() {
-    return (size_t)(Bits<T>::NG * Stage<T>::GSIZE + NSE * Stage<T>::ESIZE) * sizeof(T) +
-           (Bits<T>::NG + NSE) * sizeof(uint64_t);
+    return (size_t)(Bits<T>::NG * Stage<T>::GSIZE + Bits<T>::NSE * Stage<T>::ESIZE) * sizeof(T) +
+           (Bits<T>::NG + Bits<T>::NSE) * sizeof(uint64_t);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -184,13 +190,28 @@ __device__ __forceinline__ void lds3(const double *p, double v[3]) {
     v[1] = q.y;
     v[2] = p[2];
 }
-// y entry of the backward sweep's tile order (value, value, value, pad).
-__device__ __forceinline__ void st3pad(float *p, const float v[3]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], 0.f);
+// A tile-order vector entry: three values and the pad slot.
+__device__ __forceinline__ void lds4(const float *p, float v[3], float &pad) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    pad = q.w;
 }
-__device__ __forceinline__ void st3pad(double *p, const double v[3]) {
+__device__ __forceinline__ void lds4(const double *p, double v[3], double &pad) {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x;
+    v[1] = q0.y;
+    v[2] = q1.x;
+    pad = q1.y;
+}
+// y entry of the backward sweep's tile order (value, value, value, pad).
+__device__ __forceinline__ void st3pad(float *p, const float v[3], float pad) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], pad);
+}
+__device__ __forceinline__ void st3pad(double *p, const double v[3], double pad) {
     reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], 0.0);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], pad);
 }
 
 template <typename T>
@@ -218,6 +239,7 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
     using U = typename Bits<T>::U;
     constexpr int NQP = Bits<T>::NQP;
     constexpr int NG = Bits<T>::NG;
+    constexpr int GS = Bits<T>::GS, NSE = Bits<T>::NSE;
     if (P.done && *(volatile const int *)P.done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     T *ring = reinterpret_cast<T *>(smem);                                   // NG data groups
@@ -379,8 +401,8 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                         }
                     }
                 }
-                T vin[3];
-                lds3(grp + GS * St::F + u * St::V + lane * 4, vin);
+                T vin[3], vpad;  // vpad: the pad slot, carried from the forward input to the output
+                lds4(grp + GS * St::F + u * St::V + lane * 4, vin, vpad);
                 // neighbours from other tiles
                 T ej[3] = {T(0), T(0), T(0)}, ek[3] = {T(0), T(0), T(0)};
                 if (edges) {
@@ -438,10 +460,10 @@ __global__ void __launch_bounds__(32) ilu_sweep_tiles(SweepArgs<T> P) {
                 }
                 if (valid) {
                     if (FWD) {
-                        st3pad(yout + u * ystep, res);
+                        st3pad(yout + u * ystep, res, vpad);
                     } else {
                         T *zo = yout + u * ystep;
-                        zo[0] = res[0];
+                        zo[0] = res[0] + vpad;
                         zo[1] = res[1];
                         zo[2] = res[2];
                     }
@@ -524,11 +546,14 @@ __global__ void pack_tiles(const TileSys *__restrict__ tsys, const int *__restri
 }
 
 // Before a forward sweep: r into tile order, and the forward edge buffers to
-// the sentinel.  One thread per (tile, step, lane).
+// the sentinel.  One thread per (tile, step, lane).  The entry's pad slot takes
+// add[c] (or 0): the forward sweep carries it into y's entry and the backward
+// sweep adds it to the cell's first output component.
 template <typename T>
 __global__ void gather_tiles(const TileSys *__restrict__ tsys, const int *__restrict__ tile_sys,
                              const int64_t *__restrict__ tile_row0, const int2 *__restrict__ order,
-                             const T *__restrict__ r, T *__restrict__ Vt, T *__restrict__ EJ, T *__restrict__ EK) {
+                             const T *__restrict__ r, const T *__restrict__ add, T *__restrict__ Vt,
+                             T *__restrict__ EJ, T *__restrict__ EK) {
     using U = typename Bits<T>::U;
     const int t = blockIdx.y;
     const TileSys G = tsys[tile_sys[t]];
@@ -547,10 +572,10 @@ __global__ void gather_tiles(const TileSys *__restrict__ tsys, const int *__rest
         o[0] = r[3 * c];
         o[1] = r[3 * c + 1];
         o[2] = r[3 * c + 2];
+        o[3] = add ? add[c] : T(0);
     } else {
-        o[0] = o[1] = o[2] = T(0);
+        o[0] = o[1] = o[2] = o[3] = T(0);
     }
-    o[3] = T(0);
     // edge buffers [row][TK][4] and [row][TJ][4]: the 32 threads of a (t, s) row
     // cover its 16 + 32 entries
     if (lane < TK * 4) reinterpret_cast<U *>(EJ)[row * TK * 4 + lane] = Bits<T>::SENT;
@@ -581,7 +606,7 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
             ts.nTJ = (sg.ny + TJ - 1) / TJ;
             ts.nTK = (sg.nz + TK - 1) / TK;
             ts.S = sg.nx + TJ + TK - 2;
-            ts.Sp = (ts.S + GS - 1) / GS * GS;
+            ts.Sp = (ts.S + Bits<T>::GS - 1) / Bits<T>::GS * Bits<T>::GS;
             ts.cell0 = sg.cell0;
             ts.poff = (int)order.size();
             maxS = std::max(maxS, ts.Sp);
@@ -640,7 +665,11 @@ cudaError_t tiles_setup(const rsv_mat *A, const double *dinv, IluTiles *Tl) {
         if ((e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, true>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute((const void *)ilu_sweep_tiles<T, false>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess)
             return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, ilu_sweep_tiles<T, true>, 32, smem)) !=
                 cudaSuccess ||
@@ -670,10 +699,10 @@ void free_tiles(IluTiles *Tl) {
 
 template <typename T>
 cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &Tl, const T *r, T *z, const int *done,
-                                   int *status, unsigned long long timeout_ns) {
+                                   int *status, unsigned long long timeout_ns, const T *add0) {
     rsv::count_launches(3);
     const dim3 g((unsigned)((Tl.maxS * 32 + 255) / 256), (unsigned)Tl.nT);
-    gather_tiles<T><<<g, 256, 0, A->stream>>>(Tl.tsys, Tl.tile_sys, Tl.tile_row0, Tl.order, r, (T *)Tl.Vf,
+    gather_tiles<T><<<g, 256, 0, A->stream>>>(Tl.tsys, Tl.tile_sys, Tl.tile_row0, Tl.order, r, add0, (T *)Tl.Vf,
                                               (T *)Tl.EJf, (T *)Tl.EKf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -695,8 +724,8 @@ cudaError_t launch_ilu_apply_tiles(const rsv_mat *A, const IluTiles &Tl, const T
 template cudaError_t tiles_setup<double>(const rsv_mat *, const double *, IluTiles *);
 template cudaError_t tiles_setup<float>(const rsv_mat *, const double *, IluTiles *);
 template cudaError_t launch_ilu_apply_tiles<double>(const rsv_mat *, const IluTiles &, const double *, double *,
-                                                    const int *, int *, unsigned long long);
+                                                    const int *, int *, unsigned long long, const double *);
 template cudaError_t launch_ilu_apply_tiles<float>(const rsv_mat *, const IluTiles &, const float *, float *,
-                                                   const int *, int *, unsigned long long);
+                                                   const int *, int *, unsigned long long, const float *);
 
 }  // namespace rsv

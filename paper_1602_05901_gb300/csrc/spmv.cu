@@ -15,6 +15,53 @@ __device__ __forceinline__ uint64_t global_timer() {
     return t;
 }
 
+// The seven-point pattern of a single-grid matrix (grid dims; cells in natural order, a row's
+// columns ascending: -z, -y, -x, self, +x, +y, +z, absent faces skipped).  Its column indices
+// and row pointers follow from the cell index, so the stage-two residual reads neither array.
+//
+// Quotients by nx and ny use division by an invariant integer as a multiply and a shift
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l
+// for every 0 <= n < 2^31.
+struct Div32 {
+    unsigned m, l;
+    static Div32 of(unsigned d) {
+        unsigned l = 0;
+        while ((1ull << l) < d) ++l;
+        return {(unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
+    }
+    __device__ __forceinline__ int operator()(int n) const {
+        return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l);
+    }
+};
+struct Grid7 {
+    int nx, ny, nz;
+    Div32 dx, dy;
+    static Grid7 of(int nx, int ny, int nz) { return {nx, ny, nz, Div32::of(nx), Div32::of(ny)}; }
+};
+
+// Cell c's coordinates (q: pencils before c's; k: planes before c's).
+struct Cell7 {
+    int c, i, j, k, q;
+    __device__ __forceinline__ Cell7(int c_, const Grid7 &g) : c(c_) {
+        q = g.dx(c);
+        i = c - q * g.nx;
+        k = g.dy(q);
+        j = q - k * g.ny;
+    }
+    // First block of row c: 7 c less the faces absent from the cells before c (x: two per
+    // complete pencil, and the -x face of c's pencil start; y: 2 nx per complete plane, then the
+    // cells of the current plane on its j = 0 and j = ny - 1 rows; z: the cells before c on the
+    // k = 0 and k = nz - 1 planes).
+    __device__ __forceinline__ int64_t row_start(const Grid7 &g) const {
+        const int64_t nxy = (int64_t)g.nx * g.ny, m = (int64_t)j * g.nx + i;
+        const int64_t mx = 2 * (int64_t)q + (i > 0 ? 1 : 0);
+        const int64_t my = 2 * (int64_t)g.nx * k + min(m, (int64_t)g.nx) + max((int64_t)0, m - (int64_t)(g.ny - 1) * g.nx);
+        const int64_t mz = min((int64_t)c, nxy) + max((int64_t)0, (int64_t)c - (int64_t)(g.nz - 1) * nxy);
+        return 7 * (int64_t)c - mx - my - mz;
+    }
+};
+
 // Shared-memory layout of one CTA: block values | column indices | row pointers | mbarrier.
 template <typename T, int R> struct SpmvSmem {
     static constexpr int VALS = R * 7 * 9 + 32 / sizeof(T);  // + room for aligning both ends to 16 bytes
@@ -207,6 +254,99 @@ __global__ void __launch_bounds__(3 * R) pcol_residual_tma(int nb, const int32_t
     r[row] = T(-1) * acc + fr;
 }
 
+// The stage-two residual on a single-grid seven-point pattern: one thread per block row
+// forms its three entries, columns from the cell index, only the pressure columns staged.
+// Many small CTAs keep enough copies in flight per SM.  Same sums in the same order as
+// pcol_residual_tma.
+template <typename T, int R>
+__global__ void __launch_bounds__(R) pcol_residual_stencil(int nb, Grid7 g, const T *__restrict__ apc,
+                                                           const T *__restrict__ p, const T *__restrict__ f,
+                                                           T *__restrict__ r, const int *done, int *status,
+                                                           unsigned long long timeout_ns) {
+    if (done && *(volatile const int *)done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int VALS = R * 7 * 3 + 32 / sizeof(T);
+    T *sv = reinterpret_cast<T *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + ((size_t)VALS * sizeof(T) + 7) / 8 * 8);
+    const int r0 = blockIdx.x * R;
+    const int nr = min(R, nb - r0);
+    const int64_t p0 = Cell7(r0, g).row_start(g), p1 = Cell7(r0 + nr, g).row_start(g);
+    const uintptr_t vb0 = (uintptr_t)(apc + p0 * 3), vb1 = (uintptr_t)(apc + p1 * 3);
+    const uintptr_t va0 = vb0 & ~(uintptr_t)15, va1 = (vb1 + 15) & ~(uintptr_t)15;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"((unsigned)(va1 - va0))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sv)),
+            "l"(va0), "r"((unsigned)(va1 - va0)), "r"(smem_u32(bar))
+            : "memory");
+    }
+    const int t = threadIdx.x;
+    const int64_t row = 3 * (int64_t)(r0 + t);
+    T fr[3] = {T(0), T(0), T(0)};
+    if (t < nr)  // issued before the wait
+        for (int e = 0; e < 3; ++e) fr[e] = f[row + e];
+    __syncthreads();
+    {
+        unsigned ok = 0;
+        const uint64_t deadline = global_timer() + timeout_ns;
+        bool late = false;
+        for (;;) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(smem_u32(bar))
+                : "memory");
+            if (ok) break;
+            if (global_timer() > deadline) {
+                late = true;
+                break;
+            }
+        }
+        if (__syncthreads_or(late)) {
+            if (t == 0 && status) atomicCAS(status, 0, (int)RSV_ETIMEOUT);
+            if (t < nr)
+                for (int e = 0; e < 3; ++e) r[row + e] = T(__int_as_float(0x7fc00000));
+            if (t == 0) {
+                const uint64_t drain = global_timer() + 10000000ull;
+                do {
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, "
+                        "0, p;\n}"
+                        : "=r"(ok)
+                        : "r"(smem_u32(bar))
+                        : "memory");
+                } while (!ok && global_timer() < drain);
+            }
+            return;
+        }
+    }
+    if (t >= nr) return;
+    const Cell7 cl(r0 + t, g);
+    const T *a = sv + (int)((vb0 - va0) / sizeof(T)) + (int)(cl.row_start(g) - p0) * 3;
+    const int64_t c = cl.c, nxy = (int64_t)g.nx * g.ny;
+    T acc[3] = {T(0), T(0), T(0)};
+    auto blk = [&](int64_t col) {
+        const T pc = p[col];
+        acc[0] = fma(a[0], pc, acc[0]);
+        acc[1] = fma(a[1], pc, acc[1]);
+        acc[2] = fma(a[2], pc, acc[2]);
+        a += 3;
+    };
+    if (cl.k > 0) blk(c - nxy);
+    if (cl.j > 0) blk(c - g.nx);
+    if (cl.i > 0) blk(c - 1);
+    blk(c);
+    if (cl.i < g.nx - 1) blk(c + 1);
+    if (cl.j < g.ny - 1) blk(c + g.nx);
+    if (cl.k < g.nz - 1) blk(c + nxy);
+    for (int e = 0; e < 3; ++e) r[row + e] = T(-1) * acc[e] + fr[e];
+}
+
 __global__ void cast_f64_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
@@ -220,6 +360,9 @@ cudaError_t spmv_attr() {
                                 (int)SpmvSmem<T, R>::BYTES);
 }
 
+// The index-free form of the seven-point pattern (columns and row starts from the cell index)
+// reads 10% fewer bytes but measured slower on 256x256x128 (FP64 1.09 against 0.97 ms, FP32
+// 0.383 against 0.377 ms): the SpMV keeps the staged column indices.
 template <typename T, int R>
 cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T beta, T *y, const int *done,
                         int *status, unsigned long long timeout_ns) {
@@ -245,6 +388,9 @@ cudaError_t spmv_dispatch(const rsv_mat *A, const T *v, T alpha, const T *x, T b
 template <typename T, int R> constexpr size_t pcol_smem() {
     return (size_t)(R * 7 * 3 + 32 / sizeof(T)) * sizeof(T) + (R * 7 + 8) * 4 + (R + 4) * 4 + 16;
 }
+template <typename T, int R> constexpr size_t pcol_stencil_smem() {
+    return ((size_t)(R * 7 * 3 + 32 / sizeof(T)) * sizeof(T) + 7) / 8 * 8 + 16;
+}
 
 template <typename T>
 cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p, const T *f, T *r, const int *done,
@@ -253,8 +399,12 @@ cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p,
     constexpr int R = 128;
     const int grid = (int)((A->nb + R - 1) / R);
     rsv::count_launches(1);
-    pcol_residual_tma<T, R><<<grid, 3 * R, pcol_smem<T, R>(), A->stream>>>((int)A->nb, A->d_rp, A->d_ci, apc, p, f, r,
-                                                                          done, status, timeout_ns);
+    if (A->nsys == 1)  // 0.15 ms less per FP32 CPR apply on 256x256x128 than the indexed form
+        pcol_residual_stencil<T, R><<<grid, R, pcol_stencil_smem<T, R>(), A->stream>>>(
+            (int)A->nb, Grid7::of(A->nx, A->ny, A->nz), apc, p, f, r, done, status, timeout_ns);
+    else
+        pcol_residual_tma<T, R><<<grid, 3 * R, pcol_smem<T, R>(), A->stream>>>((int)A->nb, A->d_rp, A->d_ci, apc, p,
+                                                                              f, r, done, status, timeout_ns);
     return cudaGetLastError();
 }
 template cudaError_t launch_pressure_residual<double>(const rsv_mat *, const double *, const double *, const double *,
@@ -273,7 +423,13 @@ cudaError_t spmv_init() {
             cudaSuccess ||
         (e = cudaFuncSetAttribute((const void *)pcol_residual_tma<float, 128>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pcol_smem<float, 128>())) !=
-            cudaSuccess)
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute((const void *)pcol_residual_stencil<double, 128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pcol_stencil_smem<double, 128>())) != cudaSuccess ||
+        (e = cudaFuncSetAttribute((const void *)pcol_residual_stencil<float, 128>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pcol_stencil_smem<float, 128>())) != cudaSuccess)
         return e;
     return cudaSuccess;
 }
