@@ -25,6 +25,22 @@
 
 namespace rsv {
 
+// Division by an invariant integer as a multiply and a shift (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l for every 0 <= n < 2^31.
+// Built on the host for a grid dimension, used by index arithmetic in the kernels.
+struct Div32 {
+    unsigned m, l;
+    static Div32 of(unsigned d) {
+        unsigned l = 0;
+        while ((1ull << l) < d) ++l;
+        return {(unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
+    }
+    __device__ __forceinline__ int operator()(int n) const {
+        return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l);
+    }
+};
+
 constexpr int kMaxRestart = 64;
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs: grid of every reduction kernel
 constexpr int kRedThreads = 256;

@@ -18,22 +18,7 @@ __device__ __forceinline__ uint64_t global_timer() {
 // The seven-point pattern of a single-grid matrix (grid dims; cells in natural order, a row's
 // columns ascending: -z, -y, -x, self, +x, +y, +z, absent faces skipped).  Its column indices
 // and row pointers follow from the cell index, so the stage-two residual reads neither array.
-//
-// Quotients by nx and ny use division by an invariant integer as a multiply and a shift
-// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
-// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l
-// for every 0 <= n < 2^31.
-struct Div32 {
-    unsigned m, l;
-    static Div32 of(unsigned d) {
-        unsigned l = 0;
-        while ((1ull << l) < d) ++l;
-        return {(unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1), l};
-    }
-    __device__ __forceinline__ int operator()(int n) const {
-        return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l);
-    }
-};
+// Quotients by nx and ny use Div32 (a multiply and a shift).
 struct Grid7 {
     int nx, ny, nz;
     Div32 dx, dy;
