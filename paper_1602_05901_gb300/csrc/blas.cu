@@ -193,6 +193,8 @@ __global__ void __launch_bounds__(kRedThreads, 2) mdot2_kernel(int64_t n, const 
                                                             const T *__restrict__ u, const T *__restrict__ V,
                                                             int64_t ldv, int k, double *partial, double *ow,
                                                             double *ou, unsigned *counter, const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (is_done(done)) return;
     using VT = Vec<T>;
     constexpr int G2 = kGroup / 2;
@@ -412,6 +414,8 @@ __global__ void __launch_bounds__(kRedThreads) dcgs2_update_kernel(int64_t n, T 
                                                                    int64_t ldv, int k, const double *cA,
                                                                    const double *cB, const double *cS,
                                                                    const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (is_done(done)) return;
     using VT = Vec<T>;
     __shared__ T sa[kMaxRestart], sb[kMaxRestart];
@@ -586,11 +590,10 @@ cudaError_t launch_mdot2(cudaStream_t st, int64_t n, const T *w, const T *u, con
     if (k < 1 || k > kMaxRestart + 1) return cudaErrorInvalidValue;
     rsv::count_launches(1);
     if (vec_ok<T>(ldv, {w, u, V}))
-        mdot2_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, u, V, ldv, k, partial, ow, ou, counter, done);
-    else
-        mdot2_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, w, u, V, ldv, k, partial, ow, ou, counter,
-                                                                   done);
-    return cudaGetLastError();
+        return launch_pdl(mdot2_kernel<T, true>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, n, w, u, V, ldv, k,
+                          partial, ow, ou, counter, done);
+    return launch_pdl(mdot2_kernel<T, false>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, n, w, u, V, ldv, k, partial,
+                      ow, ou, counter, done);
 }
 
 template <typename T>
@@ -628,10 +631,10 @@ cudaError_t launch_dcgs2_update(cudaStream_t st, int64_t n, T *u, T *w, const T 
     if (k < 0 || k > kMaxRestart) return cudaErrorInvalidValue;
     rsv::count_launches(1);
     if (vec_ok<T>(ldv, {u, w, V}))
-        dcgs2_update_kernel<T, true><<<kRedBlocks, kRedThreads, 0, st>>>(n, u, w, V, ldv, k, cA, cB, cS, done);
-    else
-        dcgs2_update_kernel<T, false><<<kRedBlocks, kRedThreads, 0, st>>>(n, u, w, V, ldv, k, cA, cB, cS, done);
-    return cudaGetLastError();
+        return launch_pdl(dcgs2_update_kernel<T, true>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, n, u, w, V, ldv,
+                          k, cA, cB, cS, done);
+    return launch_pdl(dcgs2_update_kernel<T, false>, dim3(kRedBlocks), dim3(kRedThreads), 0, st, n, u, w, V, ldv, k,
+                      cA, cB, cS, done);
 }
 
 template <typename T>

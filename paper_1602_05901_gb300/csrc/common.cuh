@@ -41,6 +41,29 @@ struct Div32 {
     }
 };
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be scheduled while the
+// kernel before it on the stream is still running; it must call pdl_wait() before it touches
+// anything that kernel writes (pdl_wait returns once the previous grid has completed and its
+// memory is visible; in a kernel launched the ordinary way it returns at once).  pdl_trigger()
+// lets the next such kernel be scheduled as soon as every CTA of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 constexpr int kMaxRestart = 64;
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs: grid of every reduction kernel
 constexpr int kRedThreads = 256;

@@ -242,6 +242,8 @@ __global__ void coarse_inverse_kernel(int n, const double *__restrict__ LU, cons
 template <typename T>
 __global__ void coarse_apply_kernel(int n, const double *__restrict__ Minv, const T *__restrict__ b, T *__restrict__ x,
                                     const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (gated(done)) return;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -299,6 +301,8 @@ __global__ void split_stencil_kernel(G3 g, const double *__restrict__ a7, T *__r
 template <typename T, int MODE, int CELLS>
 __global__ void rbgs_kernel(G3 g, G3Div gd, const T *__restrict__ a7s, const T *__restrict__ b, T *__restrict__ x,
                             int colour, const T *__restrict__ xc, G3 cg, const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (gated(done)) return;
     const int64_t n = g.n();
     const int half = (g.nx + 1) >> 1;
@@ -345,6 +349,8 @@ __global__ void rbgs_kernel(G3 g, G3Div gd, const T *__restrict__ a7s, const T *
 template <typename T>
 __global__ void residual_restrict_kernel(G3 f, const T *__restrict__ a7, const T *__restrict__ b,
                                          const T *__restrict__ x, G3 cg, T *__restrict__ bc, const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (gated(done)) return;
     const int64_t nc = cg.n(), n = f.n();
     const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -394,6 +400,8 @@ __global__ void zero_kernel(int64_t n, T *x, const int *done) {
 template <typename T>
 __global__ void restrict_pressure_kernel(int64_t nb, const T *__restrict__ w, const T *__restrict__ f,
                                          T *__restrict__ p, const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (gated(done)) return;
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= nb) return;
@@ -405,6 +413,8 @@ __global__ void restrict_pressure_kernel(int64_t nb, const T *__restrict__ w, co
 // and 16-byte aligned w, f and p.
 __global__ void restrict_pressure_v4(int64_t nb4, const float4 *__restrict__ w, const float4 *__restrict__ f,
                                      float4 *__restrict__ p, const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (gated(done)) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nb4) return;
@@ -586,38 +596,47 @@ static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done)
     T *x = (T *)P.x[l], *b = (T *)P.b[l];
     G3 g{P.dims[l][0], P.dims[l][1], P.dims[l][2]};
     const int64_t n = g.n();
+    // The cycle's kernels are launched as programmatic dependents (launch_pdl): each waits for
+    // its predecessor on the device, so the launch latency of most levels' small kernels overlaps
+    // the kernel before.
     if (l == P.nlev - 1) {
         count_launches(1);
-        coarse_apply_kernel<T><<<blocks(n * 32), 256, 0, st>>>((int)n, P.minv, b, x, done);
-        return cudaGetLastError();
+        return launch_pdl(coarse_apply_kernel<T>, dim3(blocks(n * 32)), dim3(256), 0, st, (int)n, P.minv, b, x,
+                          done);
     }
     G3 c{P.dims[l + 1][0], P.dims[l + 1][1], P.dims[l + 1][2]};
     const T *xc = (const T *)P.x[l + 1];
     const int64_t slots = (int64_t)((g.nx + 1) / 2) * g.ny * g.nz;  // colour slots of a half sweep
     const bool wide = slots >= (1 << 20);                             // four cells per thread
-    const unsigned hb = blocks(slots), hb4 = blocks(slots, 256 * 4);
+    const dim3 hb(blocks(slots)), hb4(blocks(slots, 256 * 4)), t256(256);
     const G3Div gd = G3Div::of(g);
+    cudaError_t e = cudaSuccess;
+    auto sweep = [&](auto kern, dim3 grid, int colour) {
+        if (e == cudaSuccess) e = launch_pdl(kern, grid, t256, 0, st, g, gd, a7s, b, x, colour, xc, c, done);
+    };
+    auto half_sweep0 = [&](int colour) {
+        if (wide)
+            sweep(rbgs_kernel<T, 0, 4>, hb4, colour);
+        else
+            sweep(rbgs_kernel<T, 0, 1>, hb, colour);
+    };
     // pre-smoothing from x = 0: red, black, `sweeps` times (the first red half sweep reads no neighbour)
     count_launches(P.sweeps > 0 ? 2 * P.sweeps : 1);
     if (P.sweeps == 0) zero_kernel<T><<<blocks(n), 256, 0, st>>>(n, x, done);
-    auto half_sweep0 = [&](int colour) {
-        if (wide)
-            rbgs_kernel<T, 0, 4><<<hb4, 256, 0, st>>>(g, gd, a7s, b, x, colour, xc, c, done);
-        else
-            rbgs_kernel<T, 0, 1><<<hb, 256, 0, st>>>(g, gd, a7s, b, x, colour, xc, c, done);
-    };
     for (int s = 0; s < P.sweeps; ++s) {
         if (s > 0)
             half_sweep0(0);
         else if (wide)
-            rbgs_kernel<T, 1, 4><<<hb4, 256, 0, st>>>(g, gd, a7s, b, x, 0, xc, c, done);
+            sweep(rbgs_kernel<T, 1, 4>, hb4, 0);
         else
-            rbgs_kernel<T, 1, 1><<<hb, 256, 0, st>>>(g, gd, a7s, b, x, 0, xc, c, done);
+            sweep(rbgs_kernel<T, 1, 1>, hb, 0);
         half_sweep0(1);
     }
     count_launches(1);
-    residual_restrict_kernel<T><<<blocks(c.n()), 256, 0, st>>>(g, a7, b, x, c, (T *)P.b[l + 1], done);
-    cudaError_t e = vcycle<T>(P, l + 1, st, done);
+    if (e == cudaSuccess)
+        e = launch_pdl(residual_restrict_kernel<T>, dim3(blocks(c.n())), t256, 0, st, g, a7, b, x, c, (T *)P.b[l + 1],
+                       done);
+    if (e == cudaSuccess) e = vcycle<T>(P, l + 1, st, done);
     if (e != cudaSuccess) return e;
     // coarse correction x += P xc and post-smoothing black, red, `sweeps` times (the first black half
     // sweep applies the correction to the red values it reads)
@@ -625,11 +644,12 @@ static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done)
     if (P.sweeps == 0) prolong_add_kernel<T><<<blocks(n), 256, 0, st>>>(g, xc, c, x, done);
     for (int s = 0; s < P.sweeps; ++s) {
         if (s == 0)
-            rbgs_kernel<T, 2, 1><<<hb, 256, 0, st>>>(g, gd, a7s, b, x, 1, xc, c, done);
+            sweep(rbgs_kernel<T, 2, 1>, hb, 1);
         else
             half_sweep0(1);
         half_sweep0(0);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -639,12 +659,10 @@ cudaError_t cpr_restrict(const rsv_mat *A, const Cpr &P, const T *f, const int *
     count_launches(1);
     const bool v4 = sizeof(T) == 4 && A->nb % 4 == 0 && ((((uintptr_t)P.w) | ((uintptr_t)f) | ((uintptr_t)P.b[0])) & 15) == 0;
     if (v4)
-        restrict_pressure_v4<<<blocks(A->nb / 4), 256, 0, A->stream>>>(A->nb / 4, (const float4 *)P.w,
-                                                                     (const float4 *)f, (float4 *)P.b[0], done);
-    else
-        restrict_pressure_kernel<T><<<blocks(A->nb), 256, 0, A->stream>>>(A->nb, (const T *)P.w, f, (T *)P.b[0],
-                                                                          done);
-    return cudaGetLastError();
+        return launch_pdl(restrict_pressure_v4, dim3(blocks(A->nb / 4)), dim3(256), 0, A->stream, A->nb / 4,
+                          (const float4 *)P.w, (const float4 *)f, (float4 *)P.b[0], done);
+    return launch_pdl(restrict_pressure_kernel<T>, dim3(blocks(A->nb)), dim3(256), 0, A->stream, A->nb,
+                      (const T *)P.w, f, (T *)P.b[0], done);
 }
 
 // The pressure solve P.x[0] = V-cycle(P.b[0]); kernels skip when *gate != 0.

@@ -120,6 +120,8 @@ __global__ void gmres_givens(DevState *ds, int j, int m) {
 // basis twice (multi-dot and update), against three times for two explicit passes.
 // One block of 128 threads.
 __global__ void gmres_dcgs2_step(DevState *ds, int j, int m, int final_only) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (ds->done) return;
     constexpr int L = kMaxRestart + 1;
     __shared__ double s[L], tv[L], col[L], cs[kMaxRestart], sn[kMaxRestart], hs[L], red[2];
@@ -420,7 +422,7 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
                 RSV_CUDA_TRY(launch_mdot2<T>(s->st, n, wj, vj, V, ldv, j + 1, s->partial, ds->ow, ds->ou,
                                              &ds->counter[0], &ds->done));
                 rsv::count_launches(1);
-                gmres_dcgs2_step<<<1, 128, 0, s->st>>>(ds, j, m, 0);
+                RSV_CUDA_TRY(launch_pdl(gmres_dcgs2_step, dim3(1), dim3(128), 0, s->st, ds, j, m, 0));
                 RSV_CUDA_TRY(launch_dcgs2_update<T>(s->st, n, vj, wj, V, ldv, j, ds->cA, ds->cB, ds->cS, &ds->done));
                 continue;
             }

@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(3 * R) spmv_bsr3_tma(int nb, const int32_t *__
                                                        const int32_t *__restrict__ ci, const T *__restrict__ v,
                                                        T alpha, const T *__restrict__ x, T beta, T *__restrict__ y,
                                                        const int *done, int *status, unsigned long long timeout_ns) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (done && *(volatile const int *)done) return;
     using L = SpmvSmem<T, R>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -248,6 +250,8 @@ __global__ void __launch_bounds__(R) pcol_residual_stencil(int nb, Grid7 g, cons
                                                            const T *__restrict__ p, const T *__restrict__ f,
                                                            T *__restrict__ r, const int *done, int *status,
                                                            unsigned long long timeout_ns) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
     if (done && *(volatile const int *)done) return;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int VALS = R * 7 * 3 + 32 / sizeof(T);
@@ -353,9 +357,8 @@ cudaError_t spmv_launch(const rsv_mat *A, const T *v, T alpha, const T *x, T bet
                         int *status, unsigned long long timeout_ns) {
     const int grid = (int)((A->nb + R - 1) / R);
     rsv::count_launches(1);
-    spmv_bsr3_tma<T, R><<<grid, 3 * R, SpmvSmem<T, R>::BYTES, A->stream>>>((int)A->nb, A->d_rp, A->d_ci, v, alpha,
-                                                                           x, beta, y, done, status, timeout_ns);
-    return cudaGetLastError();
+    return launch_pdl(spmv_bsr3_tma<T, R>, dim3(grid), dim3(3 * R), SpmvSmem<T, R>::BYTES, A->stream, (int)A->nb,
+                      A->d_rp, A->d_ci, v, alpha, x, beta, y, done, status, timeout_ns);
 }
 
 // Block rows per CTA: 32, 64 or 128, picked per matrix and precision by timing (spmv_autotune).
@@ -385,8 +388,8 @@ cudaError_t launch_pressure_residual(const rsv_mat *A, const T *apc, const T *p,
     const int grid = (int)((A->nb + R - 1) / R);
     rsv::count_launches(1);
     if (A->nsys == 1)  // 0.15 ms less per FP32 CPR apply on 256x256x128 than the indexed form
-        pcol_residual_stencil<T, R><<<grid, R, pcol_stencil_smem<T, R>(), A->stream>>>(
-            (int)A->nb, Grid7::of(A->nx, A->ny, A->nz), apc, p, f, r, done, status, timeout_ns);
+        return launch_pdl(pcol_residual_stencil<T, R>, dim3(grid), dim3(R), pcol_stencil_smem<T, R>(), A->stream,
+                          (int)A->nb, Grid7::of(A->nx, A->ny, A->nz), apc, p, f, r, done, status, timeout_ns);
     else
         pcol_residual_tma<T, R><<<grid, 3 * R, pcol_smem<T, R>(), A->stream>>>((int)A->nb, A->d_rp, A->d_ci, apc, p,
                                                                               f, r, done, status, timeout_ns);
