@@ -395,6 +395,12 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
     // preconditioner runs on the not yet reorthogonalised u_j, which a flexible method
     // would have to correct in Z as well, so FGMRES keeps the two explicit passes.
     const bool delayed = !flex && sizeof(T) == 4;
+    // FP64 GMRES keeps z_j = M^{-1} v_j of every step and updates x += Z y, with no application
+    // of the preconditioner per restart (as FGMRES does).  FP32 forms M^{-1} (V y) instead:
+    // V is orthonormal, so V y has no cancellation, while an FP32 sum of the z_j can cancel;
+    // with the Z form the FP32 inner counts moved far from the oracle's refinement model
+    // (GMRES + block Jacobi on 33x17x9: 1008 against 1231).
+    const bool zupdate = flex || sizeof(T) == 8;
     DevState *ds = s->ds;
     T *V = (T *)s->kw.V, *Z = (T *)s->kw.Z, *w = (T *)s->kw.w, *t = (T *)s->kw.t;
     HostState h{};
@@ -413,7 +419,7 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
         for (int j = 0; j < m; ++j) {
             T *vj = V + (size_t)j * ldv;
             T *wj = V + (size_t)(j + 1) * ldv;
-            T *z = flex ? Z + (size_t)j * ldv : t;
+            T *z = zupdate ? Z + (size_t)j * ldv : t;
             RSV_CUDA_TRY(pc_apply<T>(s, vj, z, &ds->done));
             RSV_CUDA_TRY(spmv<T>(s, T(1), z, T(0), wj, &ds->done));
             if (delayed) {
@@ -478,7 +484,7 @@ rsv_status gmres_run(rsv_solver *s, const T *b, T *x, double tol, int *cycles, b
         if (h.jend > 0) {
             rsv::count_launches(1);
             gmres_backsolve<<<1, 1, 0, s->st>>>(ds, m);
-            if (flex) {
+            if (zupdate) {
                 RSV_CUDA_TRY(launch_maxpy<T>(s->st, n, x, Z, ldv, h.jend, ds->y, 1.0, x, s->partial, nullptr,
                                              &ds->counter[1], nullptr));
             } else {
@@ -668,7 +674,8 @@ rsv_status rsv_solver_create(rsv_mat *A, const rsv_solver_params *p, rsv_solver 
         alloc(&s->kw.V, 8 * n * es);
     } else {
         alloc(&s->kw.V, (size_t)(m + 1) * n * es);
-        if (p->solver == RSV_FGMRES) alloc(&s->kw.Z, (size_t)m * n * es);
+        // M^{-1} of every basis vector: FGMRES, and FP64 GMRES (its update from them needs no apply per restart)
+        if (p->solver == RSV_FGMRES || !s->mixed) alloc(&s->kw.Z, (size_t)m * n * es);
     }
     alloc(&s->kw.w, n * es);
     alloc(&s->kw.t, n * es);
