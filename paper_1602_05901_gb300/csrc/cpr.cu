@@ -389,6 +389,34 @@ __global__ void prolong_add_kernel(G3 f, const T *__restrict__ xc, G3 cg, T *__r
     x[c] += xc[(int64_t)(k / 2) * cg.nx * cg.ny + (int64_t)(j / 2) * cg.nx + i / 2];
 }
 
+// x += P xc on a large level, four consecutive cells of a grid row per thread (all loads
+// before the stores).  dq divides by the row's quads, ceil(nx / 4); dy by ny.  Each cell's
+// sum is the one prolong_add_kernel forms.
+template <typename T>
+__global__ void prolong_add_rows(G3 f, Div32 dq, Div32 dy, const T *__restrict__ xc, G3 cg, T *__restrict__ x,
+                                 const int *done) {
+    pdl_wait();  // launched with launch_pdl: the previous kernel may still be running
+    pdl_trigger();
+    if (gated(done)) return;
+    const int quads = (f.nx + 3) >> 2;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = dq(q);
+    if (row >= f.ny * f.nz) return;
+    const int k = dy(row), j = row - k * f.ny, i0 = 4 * (q - row * quads);
+    T *xr = x + (int64_t)row * f.nx;
+    const T *cr = xc + (int64_t)(k >> 1) * cg.nx * cg.ny + (int64_t)(j >> 1) * cg.nx;
+    T v[4], p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (i0 + u < f.nx) {
+            v[u] = xr[i0 + u];
+            p[u] = cr[(i0 + u) >> 1];
+        }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (i0 + u < f.nx) xr[i0 + u] = v[u] + p[u];
+}
+
 template <typename T>
 __global__ void zero_kernel(int64_t n, T *x, const int *done) {
     if (gated(done)) return;
@@ -643,10 +671,20 @@ static cudaError_t vcycle(const Cpr &P, int l, cudaStream_t st, const int *done)
     count_launches(P.sweeps > 0 ? 2 * P.sweeps : 1);
     if (P.sweeps == 0) prolong_add_kernel<T><<<blocks(n), 256, 0, st>>>(g, xc, c, x, done);
     for (int s = 0; s < P.sweeps; ++s) {
-        if (s == 0)
-            sweep(rbgs_kernel<T, 2, 1>, hb, 1);
-        else
+        if (s > 0) {
             half_sweep0(1);
+        } else if (wide) {
+            // on a large level the correction pass and a four-cell sweep beat the one-cell
+            // prolongating sweep (finest level of 256x256x128: 68 us for MODE 2)
+            count_launches(1);
+            const int64_t quads = (int64_t)((g.nx + 3) / 4) * g.ny * g.nz;
+            if (e == cudaSuccess)
+                e = launch_pdl(prolong_add_rows<T>, dim3(blocks(quads)), t256, 0, st, g, Div32::of((g.nx + 3) / 4),
+                               Div32::of(g.ny), xc, c, x, done);
+            half_sweep0(1);
+        } else {
+            sweep(rbgs_kernel<T, 2, 1>, hb, 1);
+        }
         half_sweep0(0);
     }
     if (e != cudaSuccess) return e;
