@@ -59,7 +59,11 @@ def spmv_bytes(nb, nnzb, val_bytes=8):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture, with the
 # kernel sources and their hash at capture time: a figure is reported only while the sources are unchanged.
-NCU_TRAFFIC = {}
+# The ILU(0) apply's figure sums its three launches (gather, forward sweep, backward sweep).
+NCU_TRAFFIC = {
+    "ilu_apply_f32_large_256x256x128": (3429493000, ("ilu_tiles.cu", "common.cuh"), "f2ec801b4cf68fdb"),
+    "spmv_f32_large_256x256x128": (2569320000, ("spmv.cu", "common.cuh"), "e5dfb24bef10827e"),
+}
 
 
 def spmv_flops(nnzb):

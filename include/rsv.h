@@ -249,11 +249,12 @@ RSV_API rsv_status rsv_axpby(void *stream, int64_t n, double alpha, const double
  * Its reduction scratch is one fixed file-scope device array (about 160 KB,
  * held by every GPU that loads the library until the process exits) instead
  * of memory from the allocator; no call to it allocates or frees.
- * Limits: 1 <= k <= 64 (RSV_EINVAL otherwise), ldv >= n.  The first call on
- * a device resolves the array's device address and keeps it for the life of
- * the process; make that first call before any stream capture.  A
- * cudaDeviceReset in the process invalidates the kept address: do not call
- * this entry point after resetting a device it has already been called on.
+ * Limits: 1 <= k <= 64 (RSV_EINVAL otherwise), ldv >= n.  Every call ends
+ * by synchronising its stream, so it cannot be made while the stream is being
+ * captured into a CUDA graph.  The first call on a device resolves the array's
+ * device address and keeps it for the life of the process: a cudaDeviceReset
+ * in the process invalidates the kept address, so do not call this entry
+ * point after resetting a device it has already been called on.
  * Every call reuses the same array, so calls whose GPU work overlaps (other
  * streams, other host threads) race: serialise them. */
 RSV_API rsv_status rsv_mdot_noalloc(void *stream, int64_t n, const double *w, const double *V, int64_t ldv, int k,

@@ -122,6 +122,8 @@ template <typename Tv>
 __global__ void ilu_factor_plane(const SysGrid *__restrict__ sys, const int32_t *__restrict__ sys_of_cell,
                                  const int32_t *__restrict__ rp, const Tv *__restrict__ v,
                                  const int32_t *__restrict__ cells, int p0, int p1, double *dinv, int *status) {
+    pdl_wait();  // launched with launch_pdl: the previous plane may still be running
+    pdl_trigger();
     const int t = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p1) return;
     const int c = cells[t];
@@ -209,19 +211,21 @@ template cudaError_t launch_bj_apply<double>(cudaStream_t, int64_t, const double
 template cudaError_t launch_bj_apply<float>(cudaStream_t, int64_t, const float *, const float *, float *,
                                             const int *);
 
+// One launch per hyperplane, each a programmatic dependent of the one before (its launch
+// overlaps the previous plane; it waits for it on the device before reading its factors).
 cudaError_t launch_ilu_setup(const rsv_mat *A, const Schedule &sch, bool from_f32, double *dinv, int *status) {
     for (int h = 0; h < sch.nplanes; ++h) {
         const int p0 = sch.plane_ptr[h], p1 = sch.plane_ptr[h + 1];
-        const int grid = (p1 - p0 + kPlaneThreads - 1) / kPlaneThreads;
+        const dim3 grid((p1 - p0 + kPlaneThreads - 1) / kPlaneThreads), block(kPlaneThreads);
         rsv::count_launches(1);
-        if (from_f32)
-            ilu_factor_plane<float><<<grid, kPlaneThreads, 0, A->stream>>>(A->d_sys, A->d_sys_of_cell, A->d_rp,
-                                                                           A->d_v32, sch.cells, p0, p1, dinv, status);
-        else
-            ilu_factor_plane<double><<<grid, kPlaneThreads, 0, A->stream>>>(A->d_sys, A->d_sys_of_cell, A->d_rp,
-                                                                            A->d_v, sch.cells, p0, p1, dinv, status);
+        const cudaError_t e =
+            from_f32 ? launch_pdl(ilu_factor_plane<float>, grid, block, 0, A->stream, A->d_sys, A->d_sys_of_cell,
+                                  A->d_rp, A->d_v32, sch.cells, p0, p1, dinv, status)
+                     : launch_pdl(ilu_factor_plane<double>, grid, block, 0, A->stream, A->d_sys, A->d_sys_of_cell,
+                                  A->d_rp, A->d_v, sch.cells, p0, p1, dinv, status);
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace rsv
