@@ -19,6 +19,8 @@ LIB = os.path.join(HERE, "librsv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
                 "--expt-relaxed-constexpr"]
+# Host loops parallelised with OpenMP: the algebraic-multigrid setup.
+OPENMP = {"amg.cu"}
 
 
 def nvcc() -> str:
@@ -47,7 +49,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            jobs.append([cc, *FLAGS, *extra_flags, "-c", src, "-o", obj])
+            omp = ["-Xcompiler", "-fopenmp"] if os.path.basename(src) in OPENMP else []
+            jobs.append([cc, *FLAGS, *omp, *extra_flags, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-Xlinker", "--no-undefined"])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lgomp", "-Xlinker", "--no-undefined"])
         os.replace(tmp, LIB)
     return LIB
 

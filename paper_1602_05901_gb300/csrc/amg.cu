@@ -24,7 +24,13 @@
 //     (at most 1024 points) is solved with its explicit inverse.
 // Every level holds its operator, P and R = P^T as CSR (columns ascending), so
 // restriction and prolongation are row-parallel products without atomics.
+//
+// The host setup runs its row loops on all host cores (OpenMP): each CSR is built
+// in two passes (row counts, then rows written at their offsets), and every row's
+// sums keep their order, so the hierarchy is the same as a one-thread run's.
 #include <algorithm>
+#include <omp.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -69,18 +75,34 @@ double unit_uniform(int64_t i) {
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// rp[i + 1] holds row i's count on entry; on return rp is the row-pointer array.
+void prefix_counts(std::vector<int> &rp) {
+    for (size_t i = 1; i < rp.size(); ++i) rp[i] += rp[i - 1];
+}
+
+// Row i's strong connections (columns ascending), written at out (nullptr: count only).
+inline int strong_row(const Csr &A, int i, int *out) {
+    double mx = 0.0;
+    for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
+        if (A.ci[p] != i && -A.v[p] > mx) mx = -A.v[p];
+    int m = 0;
+    if (mx > 0.0)
+        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
+            if (A.ci[p] != i && -A.v[p] >= 0.5 * mx) {
+                if (out) out[m] = A.ci[p];
+                ++m;
+            }
+    return m;
+}
+
 void strength(const Csr &A, std::vector<int> &srp, std::vector<int> &sci) {
     srp.assign(A.n + 1, 0);
-    sci.clear();
-    for (int i = 0; i < A.n; ++i) {
-        double mx = 0.0;
-        for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
-            if (A.ci[p] != i && -A.v[p] > mx) mx = -A.v[p];
-        if (mx > 0.0)
-            for (int p = A.rp[i]; p < A.rp[i + 1]; ++p)
-                if (A.ci[p] != i && -A.v[p] >= 0.5 * mx) sci.push_back(A.ci[p]);
-        srp[i + 1] = (int)sci.size();
-    }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < A.n; ++i) srp[i + 1] = strong_row(A, i, nullptr);
+    prefix_counts(srp);
+    sci.assign(srp[A.n], 0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < A.n; ++i) strong_row(A, i, sci.data() + srp[i]);
 }
 
 // cf: 1 C, -1 F.
@@ -100,11 +122,13 @@ void pmis(int n, const std::vector<int> &srp, const std::vector<int> &sci, std::
         lam[i] = cnt[i] + unit_uniform(i);
         if (lam[i] < 1.0) cf[i] = -1;
     }
-    std::vector<char> pick(n);
+    std::vector<char> pick(n), tof(n);
     for (;;) {
-        bool any = false;
-        for (int i = 0; i < n; ++i) any = any || cf[i] == 0;
+        int any = 0;
+#pragma omp parallel for schedule(static) reduction(| : any)
+        for (int i = 0; i < n; ++i) any |= cf[i] == 0;
         if (!any) break;
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) {
             pick[i] = 0;
             if (cf[i] != 0) continue;
@@ -115,56 +139,77 @@ void pmis(int n, const std::vector<int> &srp, const std::vector<int> &sci, std::
                 if (cf[tci[p]] == 0 && lam[tci[p]] >= lam[i]) top = false;
             pick[i] = top;
         }
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i)
             if (pick[i]) cf[i] = 1;
+        // undecided points that strongly depend on a C point become F (marked first, then set, so
+        // every test reads this round's C set only)
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) {
+            tof[i] = 0;
             if (cf[i] != 0) continue;
             for (int p = srp[i]; p < srp[i + 1]; ++p)
                 if (cf[sci[p]] == 1) {
-                    cf[i] = -1;
+                    tof[i] = 1;
                     break;
                 }
         }
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < n; ++i)
+            if (tof[i]) cf[i] = -1;
     }
+}
+
+// Row i of P (nullptr outputs: count only).
+inline int interp_row(const Csr &A, const std::vector<int> &srp, const std::vector<int> &sci,
+                      const std::vector<int> &cf, const std::vector<int> &cidx, int i, int *oc, double *ov) {
+    if (cf[i] == 1) {
+        if (oc) {
+            oc[0] = cidx[i];
+            ov[0] = 1.0;
+        }
+        return 1;
+    }
+    double aii = 0.0, sn = 0.0, sc = 0.0;
+    for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+        if (A.ci[p] == i) aii = A.v[p];
+        else sn += A.v[p];
+    }
+    for (int p = srp[i]; p < srp[i + 1]; ++p) {
+        const int j = sci[p];
+        if (cf[j] != 1) continue;
+        for (int r = A.rp[i]; r < A.rp[i + 1]; ++r)
+            if (A.ci[r] == j) sc += A.v[r];
+    }
+    if (!(sc != 0.0 && aii != 0.0)) return 0;
+    const double alpha = sn / sc;
+    int m = 0;
+    for (int p = srp[i]; p < srp[i + 1]; ++p) {
+        const int j = sci[p];
+        if (cf[j] != 1) continue;
+        for (int r = A.rp[i]; r < A.rp[i + 1]; ++r)
+            if (A.ci[r] == j) {
+                if (oc) {
+                    oc[m] = cidx[j];
+                    ov[m] = -alpha * A.v[r] / aii;
+                }
+                ++m;
+            }
+    }
+    return m;
 }
 
 void interpolation(const Csr &A, const std::vector<int> &srp, const std::vector<int> &sci, const std::vector<int> &cf,
                    const std::vector<int> &cidx, Csr &P) {
     P.n = A.n;
     P.rp.assign(A.n + 1, 0);
-    P.ci.clear();
-    P.v.clear();
-    for (int i = 0; i < A.n; ++i) {
-        if (cf[i] == 1) {
-            P.ci.push_back(cidx[i]);
-            P.v.push_back(1.0);
-        } else {
-            double aii = 0.0, sn = 0.0, sc = 0.0;
-            for (int p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-                if (A.ci[p] == i) aii = A.v[p];
-                else sn += A.v[p];
-            }
-            for (int p = srp[i]; p < srp[i + 1]; ++p) {
-                const int j = sci[p];
-                if (cf[j] != 1) continue;
-                for (int r = A.rp[i]; r < A.rp[i + 1]; ++r)
-                    if (A.ci[r] == j) sc += A.v[r];
-            }
-            if (sc != 0.0 && aii != 0.0) {
-                const double alpha = sn / sc;
-                for (int p = srp[i]; p < srp[i + 1]; ++p) {
-                    const int j = sci[p];
-                    if (cf[j] != 1) continue;
-                    for (int r = A.rp[i]; r < A.rp[i + 1]; ++r)
-                        if (A.ci[r] == j) {
-                            P.ci.push_back(cidx[j]);
-                            P.v.push_back(-alpha * A.v[r] / aii);
-                        }
-                }
-            }
-        }
-        P.rp[i + 1] = (int)P.ci.size();
-    }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < A.n; ++i) P.rp[i + 1] = interp_row(A, srp, sci, cf, cidx, i, nullptr, nullptr);
+    prefix_counts(P.rp);
+    P.ci.assign(P.rp[A.n], 0);
+    P.v.assign(P.rp[A.n], 0.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < A.n; ++i) interp_row(A, srp, sci, cf, cidx, i, P.ci.data() + P.rp[i], P.v.data() + P.rp[i]);
 }
 
 void transpose(const Csr &P, int ncols, Csr &R) {
@@ -184,38 +229,56 @@ void transpose(const Csr &P, int ncols, Csr &R) {
 }
 
 // Ac = R A P: entry (I, J) sums R_If a_fk P_kJ over R's row I (f ascending), A's row f and P's row k, in order.
+// The coarse rows are cut into contiguous chunks; each chunk runs with its own dense accumulator and
+// writes to its own arrays, and the chunks are then copied into place.
 void galerkin(const Csr &A, const Csr &P, const Csr &R, Csr &Ac) {
     const int nc = R.n;
     Ac.n = nc;
     Ac.rp.assign(nc + 1, 0);
-    Ac.ci.clear();
-    Ac.v.clear();
-    std::vector<double> acc(nc, 0.0);
-    std::vector<int> mark(nc, -1), cols;
-    for (int I = 0; I < nc; ++I) {
-        cols.clear();
-        for (int t = R.rp[I]; t < R.rp[I + 1]; ++t) {
-            const int f = R.ci[t];
-            const double pf = R.v[t];
-            for (int a = A.rp[f]; a < A.rp[f + 1]; ++a) {
-                const int k = A.ci[a];
-                for (int b = P.rp[k]; b < P.rp[k + 1]; ++b) {
-                    const int J = P.ci[b];
-                    if (mark[J] != I) {
-                        mark[J] = I;
-                        acc[J] = 0.0;
-                        cols.push_back(J);
+    const int nt = std::max(1, std::min(omp_get_max_threads(), nc / 1024 + 1));  // chunks
+    std::vector<std::vector<int>> tci(nt);
+    std::vector<std::vector<double>> tv(nt);
+    std::vector<int> row0(nt + 1);
+    for (int t = 0; t <= nt; ++t) row0[t] = (int)((int64_t)nc * t / nt);
+#pragma omp parallel for schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        std::vector<double> acc(nc, 0.0);
+        std::vector<int> mark(nc, -1), cols;
+        std::vector<int> &oc = tci[t];
+        std::vector<double> &ov = tv[t];
+        for (int I = row0[t]; I < row0[t + 1]; ++I) {
+            cols.clear();
+            for (int q = R.rp[I]; q < R.rp[I + 1]; ++q) {
+                const int f = R.ci[q];
+                const double pf = R.v[q];
+                for (int a = A.rp[f]; a < A.rp[f + 1]; ++a) {
+                    const int k = A.ci[a];
+                    for (int b = P.rp[k]; b < P.rp[k + 1]; ++b) {
+                        const int J = P.ci[b];
+                        if (mark[J] != I) {
+                            mark[J] = I;
+                            acc[J] = 0.0;
+                            cols.push_back(J);
+                        }
+                        acc[J] += pf * A.v[a] * P.v[b];
                     }
-                    acc[J] += pf * A.v[a] * P.v[b];
                 }
             }
+            std::sort(cols.begin(), cols.end());
+            for (int J : cols) {
+                oc.push_back(J);
+                ov.push_back(acc[J]);
+            }
+            Ac.rp[I + 1] = (int)cols.size();
         }
-        std::sort(cols.begin(), cols.end());
-        for (int J : cols) {
-            Ac.ci.push_back(J);
-            Ac.v.push_back(acc[J]);
-        }
-        Ac.rp[I + 1] = (int)Ac.ci.size();
+    }
+    prefix_counts(Ac.rp);
+    Ac.ci.assign(Ac.rp[nc], 0);
+    Ac.v.assign(Ac.rp[nc], 0.0);
+#pragma omp parallel for schedule(static, 1)
+    for (int t = 0; t < nt; ++t) {
+        std::copy(tci[t].begin(), tci[t].end(), Ac.ci.begin() + Ac.rp[row0[t]]);
+        std::copy(tv[t].begin(), tv[t].end(), Ac.v.begin() + Ac.rp[row0[t]]);
     }
 }
 
@@ -295,6 +358,7 @@ bool dense_inverse(int n, std::vector<double> M, std::vector<double> &inv) {
             M[(size_t)k * n + q] /= d;
             inv[(size_t)k * n + q] /= d;
         }
+#pragma omp parallel for schedule(static)
         for (int i = 0; i < n; ++i) {
             if (i == k) continue;
             const double f = M[(size_t)i * n + k];
@@ -343,19 +407,23 @@ rsv_status amg_setup(const rsv_mat *A, Cpr *P, int max_levels, int max_coarse, i
     RSV_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<Csr> As(1), Ps, Rs;
     {
+        // the pressure operator has the matrix's own seven-point pattern (slots -z, -y, -x, self, +x,
+        // +y, +z; absent faces skipped): take its row pointers and columns, fill the values per row
         Csr &A0 = As[0];
         A0.n = (int)nb;
-        A0.rp.assign(nb + 1, 0);
+        A0.rp.assign(A->h_rp.begin(), A->h_rp.end());
+        A0.ci.assign(A->h_ci.begin(), A->h_ci.end());
+        A0.v.assign(A0.ci.size(), 0.0);
         static const int DI[7] = {0, 0, -1, 0, 1, 0, 0}, DJ[7] = {0, -1, 0, 0, 0, 1, 0}, DK[7] = {-1, 0, 0, 0, 0, 0, 1};
+#pragma omp parallel for schedule(static)
         for (int64_t c = 0; c < nb; ++c) {
             const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
+            int p = A0.rp[c];
             for (int s = 0; s < 7; ++s) {
                 const int ii = i + DI[s], jj = j + DJ[s], kk = k + DK[s];
                 if (ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz) continue;
-                A0.ci.push_back((int)((int64_t)nx * ny * kk + (int64_t)nx * jj + ii));
-                A0.v.push_back(a7[(size_t)s * nb + c]);
+                A0.v[p++] = a7[(size_t)s * nb + c];
             }
-            A0.rp[c + 1] = (int)A0.ci.size();
         }
     }
     max_levels = std::min(std::max(max_levels, 1), kMaxLevels);

@@ -405,6 +405,18 @@ __global__ void prolong_add_rows(G3 f, Div32 dq, Div32 dy, const T *__restrict__
     const int k = dy(row), j = row - k * f.ny, i0 = 4 * (q - row * quads);
     T *xr = x + (int64_t)row * f.nx;
     const T *cr = xc + (int64_t)(k >> 1) * cg.nx * cg.ny + (int64_t)(j >> 1) * cg.nx;
+    if constexpr (sizeof(T) == 4) {
+        if ((f.nx & 3) == 0 && (((uintptr_t)x) & 15) == 0) {  // one 16-byte access per quad
+            float4 v = *reinterpret_cast<const float4 *>(xr + i0);
+            const T p0 = cr[i0 >> 1], p1 = cr[(i0 >> 1) + 1];
+            v.x += p0;
+            v.y += p0;
+            v.z += p1;
+            v.w += p1;
+            *reinterpret_cast<float4 *>(xr + i0) = v;
+            return;
+        }
+    }
     T v[4], p[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
