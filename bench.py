@@ -736,15 +736,22 @@ def run_bench(args, rank, ws, local, dist):
     vals_h = torch.from_numpy(p.vals).pin_memory()
     b_h = torch.from_numpy(p.b).pin_memory()
     x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
+
+    def e2e_step():
         A.set_values(vals_h.numpy())
         s.setup(args.pc, **pc_kwargs(args))
         x_h.zero_()
         st, einfo = s.solve(b_h.numpy(), x_h.numpy())
         assert st == rsv.RSV_OK, rsv.status_string(st)
+
+    # one untimed step first: the first transfers from freshly pinned buffers pay a one-time
+    # mapping cost (measured ~0.2 s on the 4.2 GB of values) that later steps do not
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
