@@ -744,9 +744,6 @@ def run_bench(args, rank, ws, local, dist):
         st, einfo = s.solve(b_h.numpy(), x_h.numpy())
         assert st == rsv.RSV_OK, rsv.status_string(st)
 
-    # one untimed step first: the first transfers from freshly pinned buffers pay a one-time
-    # mapping cost (measured ~0.2 s on the 4.2 GB of values) that later steps do not
-    e2e_step()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     e0.record(stream)
